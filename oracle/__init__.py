@@ -1,0 +1,167 @@
+"""FP64 CPU oracle of the DUGKS step (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It wraps ``dugks_oracle.c`` (plain C,
+built with gcc, ``-O2 -ffp-contract=off``, OpenMP over rows) through ctypes
+and shares no code with the CUDA library.
+
+Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
+  equilibrium           moment identities of Eq. 2.7 (quadrature for C)
+  cell_transforms       Eqs. 2.11, 2.13, 2.15, 2.17 composed independently
+  face_original         Eq. 2.22 derived from Eqs. 2.15 / 2.11
+  step / run            exact rational stepper on tiny grids, Gaussian-hill
+                        and Cole-Hopf closed forms with second-order
+                        convergence, plane-wave decay, conservation,
+                        Dirichlet steady states, symmetry
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dugks_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+Q = 9
+
+
+def build(force: bool = False) -> str:
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("xf", ctypes.POINTER(ctypes.c_double)), ("yf", ctypes.POINTER(ctypes.c_double)),
+        ("bc", ctypes.c_int * 4), ("bc_value", ctypes.c_double * 4),
+        ("c", ctypes.c_double), ("u", ctypes.c_double * 2),
+        ("nb", ctypes.c_int), ("b", ctypes.c_double * 8),
+        ("alpha", ctypes.c_double),
+        ("nd", ctypes.c_int), ("d", ctypes.c_double * 8),
+        ("c_zero", ctypes.c_int), ("dt", ctypes.c_double),
+    ]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        P = ctypes.POINTER(_Problem)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.oracle_equilibrium.argtypes = [P, ctypes.c_double, dp]
+        L.oracle_cell_transforms.argtypes = [P, dp, dp, dp, dp]
+        L.oracle_face_original.argtypes = [P, dp, dp]
+        L.oracle_face_original.restype = ctypes.c_double
+        L.oracle_init.argtypes = [P, dp, dp]
+        L.oracle_phi.argtypes = [P, dp, dp]
+        L.oracle_mass.argtypes = [P, dp]
+        L.oracle_mass.restype = ctypes.c_double
+        L.oracle_step.argtypes = [P, dp, dp, ctypes.c_int]
+        L.oracle_run.argtypes = [P, dp, ctypes.c_long, ctypes.c_int]
+        L.oracle_max_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Oracle:
+    """Holds a problem (see ``paper_1906_11036_gb300.inputs.Problem``) in the
+    C struct layout; arrays are [Q][ny][nx] float64."""
+
+    def __init__(self, problem):
+        self.p = problem
+        self._xf = np.ascontiguousarray(problem.xf, dtype=np.float64)
+        self._yf = np.ascontiguousarray(problem.yf, dtype=np.float64)
+        s = _Problem()
+        s.nx, s.ny = len(self._xf) - 1, len(self._yf) - 1
+        s.xf, s.yf = _ptr(self._xf), _ptr(self._yf)
+        for i in range(4):
+            s.bc[i] = int(problem.bc[i])
+            s.bc_value[i] = float(problem.bc_value[i])
+        s.c = float(problem.c)
+        s.u[0], s.u[1] = float(problem.u[0]), float(problem.u[1])
+        if len(problem.b) > 8 or len(problem.d) > 8:
+            raise ValueError("at most 8 polynomial coefficients")
+        s.nb = len(problem.b)
+        for k, v in enumerate(problem.b):
+            s.b[k] = float(v)
+        s.alpha = float(problem.alpha)
+        s.nd = len(problem.d)
+        for k, v in enumerate(problem.d):
+            s.d[k] = float(v)
+        s.c_zero = int(bool(problem.c_zero))
+        s.dt = float(problem.dt)
+        self.s = s
+        self.L = lib()
+        self.nx, self.ny = s.nx, s.ny
+
+    # pointwise helpers --------------------------------------------------
+    def equilibrium(self, phi: float) -> np.ndarray:
+        out = np.zeros(Q)
+        self.L.oracle_equilibrium(ctypes.byref(self.s), float(phi), _ptr(out))
+        return out
+
+    def cell_transforms(self, ft, feq):
+        ft = np.ascontiguousarray(ft, dtype=np.float64)
+        feq = np.ascontiguousarray(feq, dtype=np.float64)
+        fbp, ftp = np.zeros(Q), np.zeros(Q)
+        self.L.oracle_cell_transforms(ctypes.byref(self.s), _ptr(ft), _ptr(feq), _ptr(fbp), _ptr(ftp))
+        return fbp, ftp
+
+    def face_original(self, fbar):
+        fbar = np.ascontiguousarray(fbar, dtype=np.float64)
+        f = np.zeros(Q)
+        phib = self.L.oracle_face_original(ctypes.byref(self.s), _ptr(fbar), _ptr(f))
+        return phib, f
+
+    # fields --------------------------------------------------------------
+    def init(self, phi0: np.ndarray) -> np.ndarray:
+        phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
+        assert phi0.shape == (self.ny, self.nx)
+        f = np.zeros((Q, self.ny, self.nx))
+        self.L.oracle_init(ctypes.byref(self.s), _ptr(phi0), _ptr(f))
+        return f
+
+    def step(self, f: np.ndarray, threads: int = 0) -> np.ndarray:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        out = np.empty_like(f)
+        rc = self.L.oracle_step(ctypes.byref(self.s), _ptr(f), _ptr(out), int(threads))
+        if rc != 0:
+            raise RuntimeError(f"oracle_step failed ({rc})")
+        return out
+
+    def run(self, f: np.ndarray, nsteps: int, threads: int = 0) -> np.ndarray:
+        f = np.array(f, dtype=np.float64, order="C", copy=True)
+        rc = self.L.oracle_run(ctypes.byref(self.s), _ptr(f), int(nsteps), int(threads))
+        if rc != 0:
+            raise RuntimeError(f"oracle_run failed ({rc})")
+        return f
+
+    def phi(self, f: np.ndarray) -> np.ndarray:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        out = np.zeros((self.ny, self.nx))
+        self.L.oracle_phi(ctypes.byref(self.s), _ptr(f), _ptr(out))
+        return out
+
+    def mass(self, f: np.ndarray) -> float:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        return float(self.L.oracle_mass(ctypes.byref(self.s), _ptr(f)))
+
+
+def max_threads() -> int:
+    return int(lib().oracle_max_threads())

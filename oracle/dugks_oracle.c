@@ -1,0 +1,453 @@
+/*
+ * dugks_oracle.c -- plain, slow, FP64 CPU implementation of the DUGKS time
+ * step for the two-dimensional nonlinear convection-diffusion equation
+ * (NCDE) with the D2Q9 velocity set, written from the paper's Section 2.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the parity oracle: only the test
+ * suite, the smoke check and the CPU-baseline leg of the benchmark may load
+ * it.  It shares no code, header, table or helper with the CUDA library and
+ * must never be reached from the product path.
+ *
+ * It follows the step summary at the end of Section 2 in the paper's order,
+ * with explicit intermediate arrays:
+ *   1. phi = sum_i ft_i                                   (text after Eq. 2.13)
+ *   2. feq_i(phi)                                         (Eq. 2.3)
+ *   3. fbp = fbar^+ (Eq. 2.21) and ftp = ftilde^+ (Eq. 2.13)
+ *   4. ghost / halo cells (periodic wrap, or the Dirichlet reading below)
+ *   5. x-faces: value and slopes (Eqs. 2.19, 2.20), fbar at x_b (Eq. 2.26),
+ *      phi_b = sum_i fbar_i, feq(phi_b), f at the face (Eq. 2.22), flux (Eq. 2.9)
+ *   6. y-faces likewise
+ *   7. cell update ft^{n+1} = ftp - dt/|V| J (Eq. 2.12 without sources)
+ *
+ * Readings of points the paper leaves open (all shared with the CUDA path,
+ * never its code):
+ *   - Eq. 2.15 lost its f_i; read fbar = (2l+h)/(2l) f - h/(2l) feq.
+ *   - Eq. 2.5 prints the diagonal weights with a garbled index; read
+ *     w_5..w_8 = 1/36.
+ *   - lambda = alpha / c_s^2 (Chapman-Enskog result, Section 3), h = dt/2.
+ *   - The auxiliary moment C = u u * int_0^phi b'(s)^2 ds (Remark 3) for
+ *     B = u b(phi), or C = 0 when requested; D = d(phi) I.
+ *   - 2-D reconstruction at an x-face between cells j and j+1 (Eq. 2.20 is
+ *     only given in 1-D): normal slope g_n = (P_{j+1}-P_j)/(x_{j+1}-x_j),
+ *     value P_j + (x_b-x_j) g_n, tangential slope g_t = (1-w) G_j + w G_{j+1}
+ *     with w = (x_b-x_j)/(x_{j+1}-x_j) and G the cell central difference
+ *     (P_{k+1}-P_{k-1})/(y_{k+1}-y_{k-1}).  y-faces are symmetric.
+ *   - Dirichlet walls (the paper cites a non-equilibrium extrapolation
+ *     scheme without defining it): one ghost cell mirrored across the wall,
+ *     x_g = 2 x_w - x_1, phi_g = 2 phi_w - phi_1, and
+ *     fbp_g = feq(phi_g) + (fbp_1 - feq(phi_1)); at a wall face the
+ *     tangential slope is the interior cell's G alone.
+ *   - Periodic directions wrap the cell index and shift the coordinate by
+ *     the domain length.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define Q 9
+#define BC_PERIODIC 0
+#define BC_DIRICHLET 1
+#define WALL_W 0
+#define WALL_E 1
+#define WALL_S 2
+#define WALL_N 3
+
+/* D2Q9 (Eq. 2.5): directions in units of c, and weights. */
+static const int CX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int CY[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double WT[Q] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
+                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+
+typedef struct {
+    int nx, ny;
+    const double *xf; /* nx+1 x-face coordinates, increasing */
+    const double *yf; /* ny+1 y-face coordinates, increasing */
+    int bc[4];        /* W, E, S, N: 0 periodic, 1 Dirichlet */
+    double bc_value[4];
+    double c;         /* lattice speed */
+    double u[2];      /* B(phi) = u * b(phi) */
+    int nb;
+    double b[8];      /* b(phi) = sum_k b[k] phi^k */
+    double alpha;     /* diffusion coefficient */
+    int nd;
+    double d[8];      /* D(phi) = d(phi) I, d(phi) = sum_k d[k] phi^k */
+    int c_zero;       /* 1: C = 0 instead of u u int b'^2 */
+    double dt;
+} oracle_problem;
+
+/* ------------------------------------------------------------------ */
+/* Coefficient functions                                               */
+/* ------------------------------------------------------------------ */
+
+static double poly(int n, const double *a, double x) {
+    double s = 0.0, p = 1.0;
+    for (int k = 0; k < n; k++) {
+        s += a[k] * p;
+        p *= x;
+    }
+    return s;
+}
+
+/* int_0^phi b'(s)^2 ds with b'(s) = sum_k k b_k s^{k-1}:
+ * b'^2 = sum_{k,l>=1} k l b_k b_l s^{k+l-2}, integrated term by term. */
+static double aux_moment_scalar(const oracle_problem *p, double phi) {
+    double s = 0.0;
+    for (int k = 1; k < p->nb; k++)
+        for (int l = 1; l < p->nb; l++) {
+            int e = k + l - 1;
+            s += (double)k * (double)l * p->b[k] * p->b[l] * pow(phi, (double)e) / (double)e;
+        }
+    return s;
+}
+
+/* Eq. 2.3: feq_i = w_i [phi + c_i.B/cs^2 + (cs^2 D + C - cs^2 phi I):(c_i c_i - cs^2 I)/(2 cs^4)] */
+void oracle_equilibrium(const oracle_problem *p, double phi, double *feq) {
+    const double cs2 = p->c * p->c / 3.0;
+    const double bv = poly(p->nb, p->b, phi);
+    const double dv = poly(p->nd, p->d, phi);
+    const double cv = p->c_zero ? 0.0 : aux_moment_scalar(p, phi);
+    double B[2], T[2][2];
+    for (int a = 0; a < 2; a++) B[a] = p->u[a] * bv;
+    for (int a = 0; a < 2; a++)
+        for (int e = 0; e < 2; e++) {
+            double delta = (a == e) ? 1.0 : 0.0;
+            T[a][e] = cs2 * dv * delta + p->u[a] * p->u[e] * cv - cs2 * phi * delta;
+        }
+    for (int i = 0; i < Q; i++) {
+        double ci[2] = {CX[i] * p->c, CY[i] * p->c};
+        double cB = ci[0] * B[0] + ci[1] * B[1];
+        double contr = 0.0;
+        for (int a = 0; a < 2; a++)
+            for (int e = 0; e < 2; e++) {
+                double delta = (a == e) ? 1.0 : 0.0;
+                contr += T[a][e] * (ci[a] * ci[e] - cs2 * delta);
+            }
+        feq[i] = WT[i] * (phi + cB / cs2 + contr / (2.0 * cs2 * cs2));
+    }
+}
+
+static double relax_time(const oracle_problem *p) { return p->alpha / (p->c * p->c / 3.0); }
+
+/* Eqs. 2.21 and 2.13 for one cell: fbar^+ and ftilde^+ from ftilde and feq. */
+void oracle_cell_transforms(const oracle_problem *p, const double *ft, const double *feq,
+                            double *fbp, double *ftp) {
+    const double lam = relax_time(p), dt = p->dt, h = 0.5 * p->dt;
+    for (int i = 0; i < Q; i++) {
+        fbp[i] = (2.0 * lam - h) / (2.0 * lam + dt) * ft[i] + 3.0 * h / (2.0 * lam + dt) * feq[i];
+        ftp[i] = (2.0 * lam - dt) / (2.0 * lam + dt) * ft[i] + 2.0 * dt / (2.0 * lam + dt) * feq[i];
+    }
+}
+
+/* Interface phi (text after Eq. 2.20) and Eq. 2.22 at one face: phi_b = sum fbar, then f = 2l/(2l+h) fbar + h/(2l+h) feq(phi_b). */
+double oracle_face_original(const oracle_problem *p, const double *fbar, double *f) {
+    const double lam = relax_time(p), h = 0.5 * p->dt;
+    double phib = 0.0, feqb[Q];
+    for (int i = 0; i < Q; i++) phib += fbar[i];
+    oracle_equilibrium(p, phib, feqb);
+    for (int i = 0; i < Q; i++)
+        f[i] = 2.0 * lam / (2.0 * lam + h) * fbar[i] + h / (2.0 * lam + h) * feqb[i];
+    return phib;
+}
+
+/* ------------------------------------------------------------------ */
+/* Initialisation and moments                                          */
+/* ------------------------------------------------------------------ */
+
+/* Section 4 opening: ft(x, 0) = feq(phi0) at each cell. f layout [Q][ny][nx]. */
+void oracle_init(const oracle_problem *p, const double *phi0, double *f) {
+    const size_t n = (size_t)p->nx * p->ny;
+    for (size_t c = 0; c < n; c++) {
+        double feq[Q];
+        oracle_equilibrium(p, phi0[c], feq);
+        for (int i = 0; i < Q; i++) f[i * n + c] = feq[i];
+    }
+}
+
+void oracle_phi(const oracle_problem *p, const double *f, double *phi) {
+    const size_t n = (size_t)p->nx * p->ny;
+    for (size_t c = 0; c < n; c++) {
+        double s = 0.0;
+        for (int i = 0; i < Q; i++) s += f[i * n + c];
+        phi[c] = s;
+    }
+}
+
+/* M = sum_jk |V_jk| phi_jk, summed in a fixed serial order. */
+double oracle_mass(const oracle_problem *p, const double *f) {
+    const size_t n = (size_t)p->nx * p->ny;
+    double m = 0.0;
+    for (int k = 0; k < p->ny; k++)
+        for (int j = 0; j < p->nx; j++) {
+            size_t c = (size_t)k * p->nx + j;
+            double s = 0.0;
+            for (int i = 0; i < Q; i++) s += f[i * n + c];
+            m += (p->xf[j + 1] - p->xf[j]) * (p->yf[k + 1] - p->yf[k]) * s;
+        }
+    return m;
+}
+
+/* ------------------------------------------------------------------ */
+/* One time step                                                        */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int nx, ny, ex, ey;   /* interior size and extended (1-cell halo) size */
+    double *xc, *yc;      /* extended centre coordinates, index j+1 / k+1 */
+    double *phi;          /* [ny][nx] */
+    double *feq;          /* [Q][ny][nx] */
+    double *fbp;          /* [Q][ey][ex] with halo */
+    double *ftp;          /* [Q][ny][nx] */
+    double *fx;           /* x-face flux c_ix f_i: [Q][ny][nx+1] */
+    double *fy;           /* y-face flux c_iy f_i: [Q][ny+1][nx] */
+} workspace;
+
+static int ws_alloc(workspace *w, const oracle_problem *p) {
+    memset(w, 0, sizeof(*w));
+    w->nx = p->nx;
+    w->ny = p->ny;
+    w->ex = p->nx + 2;
+    w->ey = p->ny + 2;
+    size_t n = (size_t)p->nx * p->ny, ne = (size_t)w->ex * w->ey;
+    w->xc = malloc(sizeof(double) * w->ex);
+    w->yc = malloc(sizeof(double) * w->ey);
+    w->phi = malloc(sizeof(double) * n);
+    w->feq = malloc(sizeof(double) * Q * n);
+    w->fbp = malloc(sizeof(double) * Q * ne);
+    w->ftp = malloc(sizeof(double) * Q * n);
+    w->fx = malloc(sizeof(double) * Q * (size_t)p->ny * (p->nx + 1));
+    w->fy = malloc(sizeof(double) * Q * (size_t)(p->ny + 1) * p->nx);
+    if (!w->xc || !w->yc || !w->phi || !w->feq || !w->fbp || !w->ftp || !w->fx || !w->fy) return -1;
+    /* extended centre coordinates: interior centres are face midpoints; ghost
+     * centres are periodic images or mirror images across the wall. */
+    const double Lx = p->xf[p->nx] - p->xf[0], Ly = p->yf[p->ny] - p->yf[0];
+    for (int j = 0; j < p->nx; j++) w->xc[j + 1] = 0.5 * (p->xf[j] + p->xf[j + 1]);
+    for (int k = 0; k < p->ny; k++) w->yc[k + 1] = 0.5 * (p->yf[k] + p->yf[k + 1]);
+    if (p->bc[WALL_W] == BC_PERIODIC) {
+        w->xc[0] = w->xc[p->nx] - Lx;
+        w->xc[p->nx + 1] = w->xc[1] + Lx;
+    } else {
+        w->xc[0] = 2.0 * p->xf[0] - w->xc[1];
+        w->xc[p->nx + 1] = 2.0 * p->xf[p->nx] - w->xc[p->nx];
+    }
+    if (p->bc[WALL_S] == BC_PERIODIC) {
+        w->yc[0] = w->yc[p->ny] - Ly;
+        w->yc[p->ny + 1] = w->yc[1] + Ly;
+    } else {
+        w->yc[0] = 2.0 * p->yf[0] - w->yc[1];
+        w->yc[p->ny + 1] = 2.0 * p->yf[p->ny] - w->yc[p->ny];
+    }
+    return 0;
+}
+
+static void ws_free(workspace *w) {
+    free(w->xc); free(w->yc); free(w->phi); free(w->feq);
+    free(w->fbp); free(w->ftp); free(w->fx); free(w->fy);
+}
+
+#define EXT(w, i, k, j) ((w)->fbp[((size_t)(i) * (w)->ey + (size_t)(k)) * (w)->ex + (size_t)(j)])
+
+/* NEE ghost of the reading above: interior cell (ji, ki) in extended
+ * indices, ghost at (jg, kg), wall value phiw. */
+static void nee_ghost(const oracle_problem *p, workspace *w, int jg, int kg, int ji, int ki, double phiw) {
+    const size_t n = (size_t)p->nx * p->ny;
+    size_t c = (size_t)(ki - 1) * p->nx + (size_t)(ji - 1);
+    double phi1 = w->phi[c];
+    double phig = 2.0 * phiw - phi1;
+    double feqg[Q];
+    oracle_equilibrium(p, phig, feqg);
+    for (int i = 0; i < Q; i++)
+        EXT(w, i, kg, jg) = feqg[i] + (EXT(w, i, ki, ji) - w->feq[i * n + c]);
+}
+
+static void fill_halo(const oracle_problem *p, workspace *w) {
+    const int nx = p->nx, ny = p->ny;
+    const int xper = p->bc[WALL_W] == BC_PERIODIC, yper = p->bc[WALL_S] == BC_PERIODIC;
+    /* Dirichlet rows first (interior columns), then periodic x-wrap over all
+     * rows including ghost rows (gives the corners when y is Dirichlet). */
+    if (!yper)
+        for (int j = 1; j <= nx; j++) {
+            nee_ghost(p, w, j, 0, j, 1, p->bc_value[WALL_S]);
+            nee_ghost(p, w, j, ny + 1, j, ny, p->bc_value[WALL_N]);
+        }
+    if (!xper)
+        for (int k = 1; k <= ny; k++) {
+            nee_ghost(p, w, 0, k, 1, k, p->bc_value[WALL_W]);
+            nee_ghost(p, w, nx + 1, k, nx, k, p->bc_value[WALL_E]);
+        }
+    if (xper)
+        for (int i = 0; i < Q; i++)
+            for (int k = 0; k <= ny + 1; k++) {
+                EXT(w, i, k, 0) = EXT(w, i, k, nx);
+                EXT(w, i, k, nx + 1) = EXT(w, i, k, 1);
+            }
+    if (yper)
+        for (int i = 0; i < Q; i++)
+            for (int j = 0; j <= nx + 1; j++) {
+                EXT(w, i, 0, j) = EXT(w, i, ny, j);
+                EXT(w, i, ny + 1, j) = EXT(w, i, 1, j);
+            }
+    if (!xper && !yper) /* corners are never read with two walls: poison them */
+        for (int i = 0; i < Q; i++) {
+            EXT(w, i, 0, 0) = NAN;
+            EXT(w, i, 0, nx + 1) = NAN;
+            EXT(w, i, ny + 1, 0) = NAN;
+            EXT(w, i, ny + 1, nx + 1) = NAN;
+        }
+}
+
+/* Central difference of fbar^+ in y at extended cell (j, k), velocity i. */
+static double grad_y(const workspace *w, int i, int k, int j) {
+    return (EXT(w, i, k + 1, j) - EXT(w, i, k - 1, j)) / (w->yc[k + 1] - w->yc[k - 1]);
+}
+static double grad_x(const workspace *w, int i, int k, int j) {
+    return (EXT(w, i, k, j + 1) - EXT(w, i, k, j - 1)) / (w->xc[j + 1] - w->xc[j - 1]);
+}
+
+static void step_ws(const oracle_problem *p, workspace *w, const double *f_in, double *f_out,
+                    int nthreads) {
+    const int nx = p->nx, ny = p->ny;
+    const size_t n = (size_t)nx * ny;
+    const double h = 0.5 * p->dt;
+    const double lam = relax_time(p);
+    (void)lam;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+
+    /* 1-3: phi, feq, fbar^+, ftilde^+ per cell */
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < ny; k++)
+        for (int j = 0; j < nx; j++) {
+            size_t c = (size_t)k * nx + j;
+            double ft[Q], feq[Q], fbp[Q], ftp[Q], phi = 0.0;
+            for (int i = 0; i < Q; i++) { ft[i] = f_in[i * n + c]; phi += ft[i]; }
+            oracle_equilibrium(p, phi, feq);
+            oracle_cell_transforms(p, ft, feq, fbp, ftp);
+            w->phi[c] = phi;
+            for (int i = 0; i < Q; i++) {
+                w->feq[i * n + c] = feq[i];
+                w->ftp[i * n + c] = ftp[i];
+                EXT(w, i, k + 1, j + 1) = fbp[i];
+            }
+        }
+    /* 4: ghosts */
+    fill_halo(p, w);
+    const int xper = p->bc[WALL_W] == BC_PERIODIC, yper = p->bc[WALL_S] == BC_PERIODIC;
+
+    /* 5: x-faces jf = 0..nx between extended cells jf (left) and jf+1 (right) */
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < ny; k++)
+        for (int jf = 0; jf <= nx; jf++) {
+            const int jl = jf, jr = jf + 1, ke = k + 1;
+            const double xb = p->xf[jf];
+            const double dxc = w->xc[jr] - w->xc[jl];
+            const double wgt = (xb - w->xc[jl]) / dxc;
+            double fbar[Q], f[Q];
+            for (int i = 0; i < Q; i++) {
+                double gn = (EXT(w, i, ke, jr) - EXT(w, i, ke, jl)) / dxc;     /* Eq. 2.20 slope */
+                double val = EXT(w, i, ke, jl) + (xb - w->xc[jl]) * gn;        /* Eq. 2.20 value */
+                double gt;
+                if (!xper && jf == 0)
+                    gt = grad_y(w, i, ke, jr);           /* west wall: interior cell only */
+                else if (!xper && jf == nx)
+                    gt = grad_y(w, i, ke, jl);           /* east wall */
+                else
+                    gt = (1.0 - wgt) * grad_y(w, i, ke, jl) + wgt * grad_y(w, i, ke, jr);
+                /* Eq. 2.19 + Eq. 2.26: fbar(x_b, t+h) = fbar^+(x_b) - h c_i . grad fbar^+(x_b) */
+                fbar[i] = val - h * (CX[i] * p->c * gn + CY[i] * p->c * gt);
+            }
+            oracle_face_original(p, fbar, f);
+            for (int i = 0; i < Q; i++)
+                w->fx[((size_t)i * ny + k) * (nx + 1) + jf] = CX[i] * p->c * f[i];
+        }
+
+    /* 6: y-faces kf = 0..ny */
+#pragma omp parallel for schedule(static)
+    for (int kf = 0; kf <= ny; kf++)
+        for (int j = 0; j < nx; j++) {
+            const int kl = kf, kr = kf + 1, je = j + 1;
+            const double yb = p->yf[kf];
+            const double dyc = w->yc[kr] - w->yc[kl];
+            const double wgt = (yb - w->yc[kl]) / dyc;
+            double fbar[Q], f[Q];
+            for (int i = 0; i < Q; i++) {
+                double gn = (EXT(w, i, kr, je) - EXT(w, i, kl, je)) / dyc;
+                double val = EXT(w, i, kl, je) + (yb - w->yc[kl]) * gn;
+                double gt;
+                if (!yper && kf == 0)
+                    gt = grad_x(w, i, kr, je);
+                else if (!yper && kf == ny)
+                    gt = grad_x(w, i, kl, je);
+                else
+                    gt = (1.0 - wgt) * grad_x(w, i, kl, je) + wgt * grad_x(w, i, kr, je);
+                fbar[i] = val - h * (CX[i] * p->c * gt + CY[i] * p->c * gn);
+            }
+            oracle_face_original(p, fbar, f);
+            for (int i = 0; i < Q; i++)
+                w->fy[((size_t)i * (ny + 1) + kf) * nx + j] = CY[i] * p->c * f[i];
+        }
+
+    /* 7: cell update, Eq. 2.12 with J = sum over faces of (c_i . n) f_i |S| */
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < ny; k++)
+        for (int j = 0; j < nx; j++) {
+            size_t c = (size_t)k * nx + j;
+            double dxj = p->xf[j + 1] - p->xf[j], dyk = p->yf[k + 1] - p->yf[k];
+            double area = dxj * dyk;
+            for (int i = 0; i < Q; i++) {
+                double fe = w->fx[((size_t)i * ny + k) * (nx + 1) + j + 1];
+                double fw = w->fx[((size_t)i * ny + k) * (nx + 1) + j];
+                double fn = w->fy[((size_t)i * (ny + 1) + k + 1) * nx + j];
+                double fs = w->fy[((size_t)i * (ny + 1) + k) * nx + j];
+                double J = (fe - fw) * dyk + (fn - fs) * dxj;
+                f_out[i * n + c] = w->ftp[i * n + c] - p->dt / area * J;
+            }
+        }
+}
+
+static int valid(const oracle_problem *p) {
+    if (p->nx <= 0 || p->ny <= 0 || p->nb > 8 || p->nd > 8 || p->nb < 0 || p->nd < 0) return 0;
+    if ((p->bc[WALL_W] == BC_PERIODIC) != (p->bc[WALL_E] == BC_PERIODIC)) return 0;
+    if ((p->bc[WALL_S] == BC_PERIODIC) != (p->bc[WALL_N] == BC_PERIODIC)) return 0;
+    return p->alpha > 0.0 && p->c > 0.0 && p->dt > 0.0;
+}
+
+int oracle_step(const oracle_problem *p, const double *f_in, double *f_out, int nthreads) {
+    workspace ws;
+    if (!valid(p)) return -2;
+    if (ws_alloc(&ws, p) != 0) { ws_free(&ws); return -1; }
+    step_ws(p, &ws, f_in, f_out, nthreads);
+    ws_free(&ws);
+    return 0;
+}
+
+/* n steps in place on f (ping-pong through a scratch copy). */
+int oracle_run(const oracle_problem *p, double *f, long nsteps, int nthreads) {
+    const size_t sz = sizeof(double) * Q * (size_t)p->nx * p->ny;
+    workspace ws;
+    if (!valid(p)) return -2;
+    double *tmp = malloc(sz);
+    if (!tmp || ws_alloc(&ws, p) != 0) { free(tmp); ws_free(&ws); return -1; }
+    for (long s = 0; s < nsteps; s++) {
+        step_ws(p, &ws, f, tmp, nthreads);
+        memcpy(f, tmp, sz);
+    }
+    ws_free(&ws);
+    free(tmp);
+    return 0;
+}
+
+int oracle_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
