@@ -1,0 +1,341 @@
+"""Benchmark of the fused DUGKS step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload nonuniform|burgers] [--substeps S]
+
+A bench step is one output interval of S DUGKS time steps (default 50) on
+the workload's full grid; every DUGKS time step is one launch of the fused
+step kernel, i.e. one pass of the whole method over the grid.
+
+* value      : cell-velocity updates per second with the state resident in
+               HBM (K intervals timed with CUDA events on the solver's stream).
+* e2e        : the same metric through the C ABI with host buffers: each
+               interval uploads phi0 from pinned host memory
+               (dugks_init_phi_host), steps S times, and reads phi back to
+               host memory (dugks_get_phi_host).
+* roofline   : the fused step kernel against the measured HBM copy
+               bandwidth; algorithmic bytes = read ftilde once + write once
+               = 2 * 9 * sizeof(T) per cell.
+* cpu_baseline (rank 0, N = 1): the FP64 CPU oracle on a bounded sample.
+
+--impl reference times that oracle as it stands on the host cores.
+Multi-GPU runs are independent replicas (one per rank, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DUGKS cell-velocity updates/sec and % HBM roofline (FP32, 1 GB300); adjoint/step ratio"
+UNIT = "cell-velocity updates/s"
+Q = 9
+PROFILE = os.path.join(ROOT, "profiles", "fused_step_nonuniform_2048.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1906_11036_gb300", "csrc", f)
+                  for f in ("dugks_kernels.cuh", "dugks_device.cuh")]
+
+
+def workload(name: str):
+    from paper_1906_11036_gb300 import inputs as I
+
+    if name == "nonuniform":
+        return I.nonuniform()
+    if name == "burgers":
+        return I.burgers()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(workload_name: str):
+    """dram bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source and this workload; else None."""
+    if not os.path.exists(PROFILE):
+        return None
+    kv = {}
+    for line in open(PROFILE):
+        if ":" in line and not line.startswith(" "):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_hash") != kernel_source_hash() or kv.get("workload") != workload_name:
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_full_grid"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path))["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.p is not None:
+            time.sleep(0.2)
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out, _ = self.p.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for _, _, flags in rows for n, f in zip(names, flags) if f.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_rate(p, phi0, seconds: float, threads: int, max_rows: int | None = None):
+    """Time the FP64 oracle as it stands on a horizontal band of the workload
+    (all columns, the first `rows` rows, walls as in the workload) for about
+    `seconds`; returns (CVU/s, sample description, threads)."""
+    from oracle import Oracle
+
+    rows = p.ny if max_rows is None else min(p.ny, max_rows)
+    band = p.with_(yf=p.yf[: rows + 1])
+    o = Oracle(band)
+    f = o.init(np.ascontiguousarray(phi0[:rows]))
+    t0 = time.perf_counter()
+    f = o.run(f, 1, threads)  # calibration step (also first-touch of the workspace)
+    one = time.perf_counter() - t0
+    n = max(1, int(seconds / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    o.run(f, n, threads)
+    el = time.perf_counter() - t0
+    cvu = band.nx * rows * Q * n
+    return cvu / el, f"{n} oracle steps on a {band.nx}x{rows} band of the {p.nx}x{p.ny} workload", threads
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    p, phi0 = workload(args.workload)
+    threads = os.cpu_count() or 1
+    # each bench step: one oracle time step on a band sized so that warmup+steps take ~2 minutes
+    from oracle import Oracle
+
+    rows = min(p.ny, 64)
+    band = p.with_(yf=p.yf[: rows + 1])
+    o = Oracle(band)
+    f = o.init(np.ascontiguousarray(phi0[:rows]))
+    t0 = time.perf_counter()
+    f = o.run(f, 1, threads)
+    per_row = (time.perf_counter() - t0) / rows
+    total = args.steps + args.warmup
+    rows = int(max(4, min(p.ny, 120.0 / max(total, 1) / max(per_row, 1e-9))))
+    band = p.with_(yf=p.yf[: rows + 1])
+    o = Oracle(band)
+    f = o.init(np.ascontiguousarray(phi0[:rows]))
+    f = o.run(f, args.warmup, threads)
+    t0 = time.perf_counter()
+    o.run(f, args.steps, threads)
+    el = time.perf_counter() - t0
+    value = band.nx * rows * Q * args.steps / el
+    sample = f"each step: one FP64 oracle time step on a {band.nx}x{rows} band of the {p.nx}x{p.ny} {args.workload} workload"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(args, p),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(args, p):
+    return {"workload": f"{args.workload}_{p.nx}x{p.ny}", "nx": p.nx, "ny": p.ny, "velocity_set": "D2Q9",
+            "mesh": "tanh-stretched k=2, Dirichlet walls" if args.workload == "nonuniform" else "uniform periodic",
+            "dt": p.dt, "c": p.c, "step": f"{args.substeps} DUGKS time steps (one output interval)",
+            "l2": "state larger than L2 (two 9-plane FP32 buffers)", "parallelism": "replicas"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="nonuniform", choices=["nonuniform", "burgers"])
+    ap.add_argument("--substeps", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+        __graft_entry__.build()
+    from paper_1906_11036_gb300.dugks import Solver
+
+    p, phi0 = workload(args.workload)
+    S = args.substeps
+    cells = p.nx * p.ny
+    cvu_per_step = cells * Q * S
+    stream = torch.cuda.Stream()
+    solver = Solver(p, precision=32, stream=stream)
+    info = solver.info()
+    with torch.cuda.stream(stream):
+        solver.init_phi(torch.tensor(phi0, device="cuda"))
+        for _ in range(args.warmup):
+            solver.step(S)
+    stream.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident throughput --------------------------------------------
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            solver.step(S)
+        ev1.record(stream)
+        ev1.synchronize()
+    barrier()
+    t_dev = ev0.elapsed_time(ev1) / 1e3
+    solver.sync()
+    # ---- per-launch kernel duration (events around each launch) ------------------
+    nl = min(200, max(20, args.steps * S // 4))
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nl)]
+    for a, b in evs:
+        a.record(stream)
+        solver.step(1)
+        b.record(stream)
+    stream.synchronize()
+    launch_s = statistics.median(a.elapsed_time(b) for a, b in evs) / 1e3
+    # ---- end to end through host buffers ------------------------------------------
+    phi_host = torch.tensor(phi0, dtype=torch.float64).pin_memory()
+    out_host = torch.empty((p.ny, p.nx), dtype=torch.float64).pin_memory()
+    phi_np, out_np = phi_host.numpy(), out_host.numpy()
+    e2e_steps = max(1, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.init_phi(phi_np)
+        solver.step(S)
+        solver.get_phi_host(out_np)
+    barrier()
+    t_e2e = time.perf_counter() - t0
+    solver.close()
+
+    times = torch.tensor([t_dev, t_e2e], device="cuda", dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
+    t_dev, t_e2e = times.tolist()
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    value = world * cvu_per_step * args.steps / t_dev
+    e2e = world * cvu_per_step * e2e_steps / t_e2e
+    peak, peak_kind = measured_peak()
+    alg_bytes = 2 * Q * 4 * cells
+    achieved = alg_bytes / launch_s / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(args, p),
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * cells, "d2h_bytes_per_step": 8 * cells + 8},
+        "gpu_launches": args.steps * S,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": profile_traffic(args.workload), "peak_kind": peak_kind,
+                     "kernel": "fused_step", "kernel_ms": launch_s * 1e3,
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "clocks": clk.summary(),
+        "launch": {"block": info["block_threads"], "grid": info["grid_blocks"]},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        rate, sample, thr = oracle_rate(p, phi0, args.cpu_seconds, os.cpu_count() or 1, max_rows=256)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

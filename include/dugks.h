@@ -1,0 +1,186 @@
+/*
+ * dugks.h -- C ABI of the GB300 DUGKS library: the discrete unified gas
+ * kinetic scheme time step for the two-dimensional nonlinear
+ * convection-diffusion equation (NCDE)
+ *
+ *     d_t phi + div B(phi) = div( alpha div D(phi) )                  (Eq. 2.1, F = 0)
+ *
+ * on a rectilinear (uniform or stretched) mesh with the D2Q9 velocity set
+ * (Eq. 2.5), following Section 2 of arXiv:1906.11036.
+ *
+ * Conventions for every entry point:
+ *   - No C++ exception crosses this boundary; every call returns a
+ *     dugks_status.  CUDA failures map to DUGKS_ERR_CUDA and the CUDA error
+ *     text is kept for dugks_last_error().
+ *   - "device pointer" arguments must be device (or managed) memory of the
+ *     GPU the context was created on, owned by the caller, aligned to the
+ *     element size; "host pointer" arguments are ordinary (pageable or
+ *     pinned) host memory owned by the caller.
+ *   - All device work is enqueued on the context's CUDA stream (set at
+ *     creation or by dugks_set_stream) and is asynchronous unless the entry
+ *     point says that it synchronises.
+ *   - Field layout: phi is [ny][nx] row-major (x fastest), contiguous.
+ *     A distribution state is 9 planes [9][ny][nx], contiguous, velocity i
+ *     ordered as in Eq. 2.5: (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1)
+ *     (-1,-1) (1,-1), times the lattice speed c.
+ *   - Element type is float for precision 32 and double for precision 64,
+ *     except where a signature says double.
+ */
+#ifndef DUGKS_H
+#define DUGKS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dugks_ctx dugks_ctx; /* opaque, library-owned */
+
+typedef enum {
+    DUGKS_OK = 0,
+    DUGKS_ERR_ARG = 1,         /* null pointer, bad size, bad enum value */
+    DUGKS_ERR_CONFIG = 2,      /* physically invalid setup (CFL >= 1, alpha <= 0, faces not increasing) */
+    DUGKS_ERR_CUDA = 3,        /* a CUDA runtime or driver call failed */
+    DUGKS_ERR_NONFINITE = 4,   /* NaN or Inf detected in phi */
+    DUGKS_ERR_UNSUPPORTED = 5, /* valid request that this build does not implement */
+    DUGKS_ERR_NOMEM = 6,       /* device or host allocation failed */
+    DUGKS_ERR_TIMEOUT = 7      /* a bounded device-side wait expired; the step result is invalid */
+} dugks_status;
+
+enum { DUGKS_BC_PERIODIC = 0, DUGKS_BC_DIRICHLET = 1 };
+enum { DUGKS_WALL_W = 0, DUGKS_WALL_E = 1, DUGKS_WALL_S = 2, DUGKS_WALL_N = 3 };
+enum { DUGKS_D2Q9 = 9 };
+enum { DUGKS_FP32 = 32, DUGKS_FP64 = 64 };
+enum {
+    DUGKS_KERNEL_AUTO = 0,  /* the fused streaming kernel */
+    DUGKS_KERNEL_FUSED = 1, /* fused streaming kernel: TMA row pipeline, one read and one write of ftilde */
+    DUGKS_KERNEL_NAIVE = 2  /* one thread per cell, everything recomputed from global memory (cross-check) */
+};
+
+/* Rectilinear mesh (Section 2: finite-volume cells V_j; Section 4, Example 4.3
+ * for stretched meshes).  xf/yf are HOST arrays of nx+1 / ny+1 strictly
+ * increasing face coordinates, copied at creation.  Cell centres are face
+ * midpoints.  bc[] per wall W, E, S, N: DUGKS_BC_PERIODIC (must be set on both
+ * walls of a direction) or DUGKS_BC_DIRICHLET with phi = bc_value[] on the
+ * wall, imposed by a mirrored ghost cell with non-equilibrium extrapolation
+ * (Section 4 opening; reading recorded in the design notes). */
+typedef struct {
+    int nx, ny;
+    const double *xf;
+    const double *yf;
+    int bc[4];
+    double bc_value[4];
+} dugks_mesh;
+
+/* Velocity set (Eq. 2.5): kind = DUGKS_D2Q9; c = lattice speed > 0, c_s^2 = c^2/3. */
+typedef struct {
+    int kind;
+    double c;
+} dugks_vset;
+
+/* Coefficients (Eqs. 2.1, 2.3, Remark 3): B(phi) = u * b(phi),
+ * D(phi) = d(phi) I, with b(phi) = sum_{k<nb} b[k] phi^k and
+ * d(phi) = sum_{k<nd} d[k] phi^k; alpha > 0 is the diffusion coefficient and
+ * fixes the relaxation time lambda = alpha / c_s^2 (Section 3).  The
+ * auxiliary moment is C = u u * int_0^phi b'(s)^2 ds, or C = 0 if c_zero. */
+typedef struct {
+    double u[2];
+    int nb;
+    double b[8];
+    double alpha;
+    int nd;
+    double d[8];
+    int c_zero;
+} dugks_coef;
+
+typedef struct {
+    int precision; /* DUGKS_FP32 or DUGKS_FP64: storage and arithmetic type */
+    int kernel;    /* DUGKS_KERNEL_* */
+    void *stream;  /* cudaStream_t for all work; NULL = the legacy default stream */
+    int device;    /* CUDA device ordinal; -1 = the current device */
+} dugks_options;
+
+typedef struct {
+    int nx, ny, precision, kernel;
+    long long pitch;        /* elements per row of one plane in the library's buffers */
+    long long steps_done;   /* time steps taken since the last init/load */
+    double dt, lambda, cfl; /* time step, relaxation time alpha/c_s^2, c dt / min cell width */
+    int block_threads;      /* threads per block of the step kernel */
+    int grid_blocks;        /* blocks per launch of the step kernel */
+    long long state_bytes;  /* bytes of one ftilde buffer (two are held) */
+} dugks_info_t;
+
+/* Validate a setup on the host only (no CUDA call).  Returns DUGKS_OK,
+ * DUGKS_ERR_ARG (null pointers, nx or ny < 1, nb/nd outside 0..8, periodic set
+ * on one wall of a direction only, unknown velocity set) or DUGKS_ERR_CONFIG
+ * (non-finite values, faces not strictly increasing, c <= 0, alpha <= 0,
+ * dt <= 0, or CFL = c dt / min cell width >= 1, the stability bound stated
+ * in the opening of Section 4). */
+dugks_status dugks_check_config(const dugks_mesh *mesh, const dugks_vset *vset,
+                                const dugks_coef *coef, double dt);
+
+/* Create a context (Section 2, one time step of size dt per dugks_step).
+ * Copies mesh and coefficients, precomputes per-row and per-column metrics
+ * and the equilibrium polynomials, and allocates two ftilde buffers on the
+ * device (library-owned; see dugks_info_t.state_bytes).  opts may be NULL
+ * (FP32, fused kernel, default stream, current device).  On error *out is
+ * set to NULL and nothing is leaked. */
+dugks_status dugks_create(const dugks_mesh *mesh, const dugks_vset *vset, const dugks_coef *coef,
+                          double dt, const dugks_options *opts, dugks_ctx **out);
+
+/* Release the context and its device memory.  Synchronises the context's
+ * stream first.  NULL is accepted and ignored. */
+dugks_status dugks_destroy(dugks_ctx *ctx);
+
+/* Initialise ftilde = feq(phi0) per cell (opening of Section 4), phi0 taken as
+ * point values at cell centres.  phi0_dev: device pointer, [ny][nx], element
+ * type of the context's precision.  Resets steps_done. */
+dugks_status dugks_init_phi(dugks_ctx *ctx, const void *phi0_dev);
+
+/* Same from a HOST array of doubles [ny][nx]; the copy goes through a
+ * library-owned staging buffer on the context's stream.  Returns after the
+ * host array may be reused (synchronises the stream). */
+dugks_status dugks_init_phi_host(dugks_ctx *ctx, const double *phi0_host);
+
+/* Advance n >= 0 time steps (Eq. 2.12 with the interface flux of Eqs.
+ * 2.19-2.22 and Eq. 2.9), asynchronously on the context's stream.  One kernel
+ * launch per step; the two ftilde buffers alternate. */
+dugks_status dugks_step(dugks_ctx *ctx, long long n);
+
+/* phi = sum_i ftilde_i (text after Eq. 2.13) into phi_dev_out (device,
+ * [ny][nx], precision's element type; may be NULL) and, if mass_out is not
+ * NULL, the mass M = sum |V_jk| phi_jk accumulated in double into *mass_out
+ * (host).  With mass_out != NULL the call synchronises the stream and returns
+ * DUGKS_ERR_NONFINITE if M is not finite. */
+dugks_status dugks_get_phi(dugks_ctx *ctx, void *phi_dev_out, double *mass_out);
+
+/* Same into a HOST array of doubles [ny][nx] (phi_host_out may be NULL);
+ * synchronises the stream. */
+dugks_status dugks_get_phi_host(dugks_ctx *ctx, double *phi_host_out, double *mass_out);
+
+/* Copy the current ftilde state out to / in from a caller device buffer laid
+ * out [9][ny][nx] (precision's element type).  Checkpoint and restart: a run
+ * of n steps, save, load, m steps equals n + m steps bit for bit.  Loading
+ * resets steps_done to 0. */
+dugks_status dugks_save_state(dugks_ctx *ctx, void *f_dev_out);
+dugks_status dugks_load_state(dugks_ctx *ctx, const void *f_dev_in);
+
+/* Replace the stream used for subsequent work (NULL = legacy default). */
+dugks_status dugks_set_stream(dugks_ctx *ctx, void *stream);
+
+/* Synchronise the stream and report a pending device-side error flag
+ * (DUGKS_ERR_TIMEOUT) or a CUDA error. */
+dugks_status dugks_sync(dugks_ctx *ctx);
+
+/* Sizes and launch shape of a context. */
+dugks_status dugks_info(const dugks_ctx *ctx, dugks_info_t *out);
+
+/* Static text for a status code; never NULL. */
+const char *dugks_status_string(dugks_status s);
+
+/* Text of the last error recorded on ctx (empty string if none; never NULL). */
+const char *dugks_last_error(const dugks_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DUGKS_H */

@@ -1,0 +1,674 @@
+// dugks_api.cu -- host side of the C ABI declared in include/dugks.h.
+//
+// Owns the context (two ftilde buffers, mesh metrics, TMA descriptors, the
+// staging and reduction buffers), validates setups, precomputes the
+// per-velocity equilibrium polynomials (Eq. 2.3 with B = u b(phi),
+// D = d(phi) I, C = u u int_0^phi b'^2, Remark 3) and the relaxation
+// coefficients of Eqs. 2.13, 2.21 and 2.22, and launches the kernels.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/dugks.h"
+#include "dugks_kernels.cuh"
+
+using namespace dugks;
+
+namespace {
+
+constexpr int NC_SMALL = 4;   // equilibrium polynomials of degree <= 3
+constexpr int NC_LARGE = 16;  // up to degree 15 (nb, nd <= 8)
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+}  // namespace
+
+struct dugks_ctx {
+    int device = 0;
+    int nx = 0, ny = 0, precision = 32, kernel = DUGKS_KERNEL_FUSED;
+    int xper = 1, yper = 1;
+    double bcv[4] = {0, 0, 0, 0};
+    double c = 1, dt = 0, lambda = 0, cfl = 0;
+    int nc = NC_SMALL;
+    double feq_coef[Q][NC_LARGE];
+    double a_bp = 0, b_bp = 0, a_tp = 0, b_tp = 0, a_f = 0, b_f = 0, hc = 0;
+    std::vector<double> xf, yf;
+    long long pitch = 0, plane = 0;
+    size_t elem = 4;
+    cudaStream_t stream = nullptr;
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    void* fxm = nullptr;  // FaceM<T>[nx+3]
+    void* fym = nullptr;  // FaceM<T>[ny+3]
+    void* cxm = nullptr;  // CellM<T>[nx+2]
+    void* cym = nullptr;  // CellM<T>[ny+2]
+    double* dxv = nullptr;  // cell widths (double) for the mass
+    double* dyv = nullptr;
+    double* staging = nullptr;  // nx*ny doubles for host transfers
+    double* partial = nullptr;  // reduction partials
+    double* mass_dev = nullptr;
+    int* err_dev = nullptr;
+    int red_blocks = 0;
+    CUtensorMap tmap[2];
+    int nt = 128, stages = 6, seg_rows = 0, nstrips = 0, nseg = 0;
+    long long steps_done = 0;
+    std::string last_error;
+};
+
+namespace {
+
+dugks_status cuda_fail(dugks_ctx* ctx, cudaError_t e, const char* what) {
+    if (ctx) {
+        char buf[256];
+        snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+        ctx->last_error = buf;
+    }
+    return e == cudaErrorMemoryAllocation ? DUGKS_ERR_NOMEM : DUGKS_ERR_CUDA;
+}
+
+#define CK(call)                                                  \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
+    } while (0)
+
+bool finite_all(const double* v, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+// int_0^phi b'(s)^2 ds as polynomial coefficients: sum_{k,l>=1} k l b_k b_l phi^{k+l-1}/(k+l-1)
+void aux_moment_poly(const dugks_coef* cf, double* out /* NC_LARGE */) {
+    for (int m = 0; m < NC_LARGE; ++m) out[m] = 0.0;
+    if (cf->c_zero) return;
+    for (int k = 1; k < cf->nb; ++k)
+        for (int l = 1; l < cf->nb; ++l) {
+            const int m = k + l - 1;
+            out[m] += double(k) * double(l) * cf->b[k] * cf->b[l] / double(m);
+        }
+}
+
+template <typename T>
+void build_metrics(const std::vector<double>& f, bool per, double hcv, double dt, double c, std::vector<FaceM<T>>& fm,
+                   std::vector<CellM<T>>& cm, std::vector<double>& width) {
+    const int n = int(f.size()) - 1;
+    std::vector<double> xc(n + 2);  // centres j = -1..n at index j+1
+    for (int j = 0; j < n; ++j) xc[j + 1] = 0.5 * (f[j] + f[j + 1]);
+    const double L = f[n] - f[0];
+    if (per) {
+        xc[0] = xc[n] - L;
+        xc[n + 1] = xc[1] + L;
+    } else {  // mirror images across the walls
+        xc[0] = 2.0 * f[0] - xc[1];
+        xc[n + 1] = 2.0 * f[n] - xc[n];
+    }
+    fm.assign(n + 3, FaceM<T>{T(0.5), T(0), T(0), T(0)});
+    for (int q = 0; q <= n; ++q) {  // face q between columns q-1 and q
+        const double xl = xc[q], xr = xc[q + 1];
+        const double dxc = xr - xl, w = (f[q] - xl) / dxc;
+        double tl = 1.0 - w, tr = w;
+        if (!per && q == 0) { tl = 0.0; tr = 1.0; }
+        if (!per && q == n) { tl = 1.0; tr = 0.0; }
+        fm[q + 1] = FaceM<T>{T(w), T(hcv / dxc), T(tl), T(tr)};
+    }
+    cm.assign(n + 2, CellM<T>{T(0), T(0)});
+    width.assign(n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        cm[j + 1] = CellM<T>{T(1.0 / (xc[j + 2] - xc[j])), T(dt * c / (f[j + 1] - f[j]))};
+        width[j] = f[j + 1] - f[j];
+    }
+}
+
+template <typename T, int NC>
+Consts<T, NC> make_consts(const dugks_ctx* ctx) {
+    Consts<T, NC> k;
+    for (int i = 0; i < Q; ++i)
+        for (int m = 0; m < NC; ++m) k.feq[i][m] = T(ctx->feq_coef[i][m]);
+    k.a_bp = T(ctx->a_bp); k.b_bp = T(ctx->b_bp);
+    k.a_tp = T(ctx->a_tp); k.b_tp = T(ctx->b_tp);
+    k.a_f = T(ctx->a_f); k.b_f = T(ctx->b_f);
+    k.hc = T(ctx->hc);
+    for (int w = 0; w < 4; ++w) k.bcv[w] = T(ctx->bcv[w]);
+    return k;
+}
+
+template <typename T, int NC>
+StepArgs<T, NC> make_args(const dugks_ctx* ctx, int from) {
+    StepArgs<T, NC> a;
+    a.fin = static_cast<const T*>(ctx->buf[from]);
+    a.fout = static_cast<T*>(ctx->buf[1 - from]);
+    a.nx = ctx->nx; a.ny = ctx->ny;
+    a.pitch = ctx->pitch; a.plane = ctx->plane;
+    a.xper = ctx->xper; a.yper = ctx->yper;
+    a.fx = static_cast<const FaceM<T>*>(ctx->fxm);
+    a.fy = static_cast<const FaceM<T>*>(ctx->fym);
+    a.cx = static_cast<const CellM<T>*>(ctx->cxm);
+    a.cy = static_cast<const CellM<T>*>(ctx->cym);
+    a.err = ctx->err_dev;
+    return a;
+}
+
+template <typename T, int NC, int NT>
+void* fused_ptr() { return reinterpret_cast<void*>(&fused_step<T, NC, NT>); }
+
+// The fused kernel variants this build instantiates.
+template <typename T, int NC>
+bool fused_variant(int nt, void** fn) {
+    switch (nt) {
+        case 96: *fn = fused_ptr<T, NC, 96>(); return true;
+        case 128: *fn = fused_ptr<T, NC, 128>(); return true;
+        case 160: *fn = fused_ptr<T, NC, 160>(); return true;
+        case 192: *fn = fused_ptr<T, NC, 192>(); return true;
+        default: return false;
+    }
+}
+
+size_t fused_smem(int elem, int nt, int stages) {
+    if (elem == 4) {
+        switch (nt) {
+            case 96: return FusedLayout<float, 96>::bytes(stages);
+            case 128: return FusedLayout<float, 128>::bytes(stages);
+            case 160: return FusedLayout<float, 160>::bytes(stages);
+            default: return FusedLayout<float, 192>::bytes(stages);
+        }
+    }
+    switch (nt) {
+        case 96: return FusedLayout<double, 96>::bytes(stages);
+        case 128: return FusedLayout<double, 128>::bytes(stages);
+        case 160: return FusedLayout<double, 160>::bytes(stages);
+        default: return FusedLayout<double, 192>::bytes(stages);
+    }
+}
+
+void* fused_fn(const dugks_ctx* ctx) {
+    void* fn = nullptr;
+    if (ctx->precision == 32)
+        (ctx->nc == NC_SMALL ? fused_variant<float, NC_SMALL>(ctx->nt, &fn) : fused_variant<float, NC_LARGE>(ctx->nt, &fn));
+    else
+        (ctx->nc == NC_SMALL ? fused_variant<double, NC_SMALL>(ctx->nt, &fn) : fused_variant<double, NC_LARGE>(ctx->nt, &fn));
+    return fn;
+}
+
+dugks_status make_tensor_maps(dugks_ctx* ctx) {
+    static EncodeTiledFn encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+            ctx->last_error = "cuTensorMapEncodeTiled is not available from the driver";
+            return DUGKS_ERR_CUDA;
+        }
+        encode = reinterpret_cast<EncodeTiledFn>(fn);
+    }
+    const int align = 16 / int(ctx->elem);
+    const cuuint64_t dims[3] = {cuuint64_t(ctx->nx), cuuint64_t(ctx->ny), cuuint64_t(Q)};
+    const cuuint64_t strides[2] = {cuuint64_t(ctx->pitch) * ctx->elem, cuuint64_t(ctx->plane) * ctx->elem};
+    const cuuint32_t box[3] = {cuuint32_t(ctx->nt + align), 1u, cuuint32_t(Q)};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    for (int b = 0; b < 2; ++b) {
+        CUresult r = encode(&ctx->tmap[b], ctx->precision == 32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                            3, ctx->buf[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            char buf[128];
+            snprintf(buf, sizeof(buf), "cuTensorMapEncodeTiled failed (%d)", int(r));
+            ctx->last_error = buf;
+            return DUGKS_ERR_CUDA;
+        }
+    }
+    return DUGKS_OK;
+}
+
+// Strip width and segment count of the fused kernel for this grid.
+dugks_status plan_fused(dugks_ctx* ctx) {
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaDeviceGetAttribute");
+    // block width: the variant that wastes the fewest thread columns
+    const int cands[] = {160, 128, 192, 96};
+    int best = 128;
+    double best_eff = -1.0;
+    for (int nt : cands) {
+        const int w = nt - 2;
+        const int strips = (ctx->nx + w - 1) / w;
+        const double eff = double(ctx->nx) / double(strips * nt);
+        if (eff > best_eff + 1e-9) { best_eff = eff; best = nt; }
+    }
+    ctx->nt = best;
+    ctx->stages = ctx->precision == 32 ? 8 : 4;
+    void* fn = fused_fn(ctx);
+    const size_t smem = fused_smem(int(ctx->elem), ctx->nt, ctx->stages);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, ctx->nt, smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (occ < 1) {
+        ctx->last_error = "fused kernel does not fit on an SM";
+        return DUGKS_ERR_UNSUPPORTED;
+    }
+    ctx->nstrips = (ctx->nx + ctx->nt - 3) / (ctx->nt - 2);
+    const long long slots = (long long)sms * occ;
+    long long nseg = std::max<long long>(1, slots / ctx->nstrips);
+    // at least 16 rows per segment so the two pipeline-fill rows stay cheap
+    nseg = std::min<long long>(nseg, std::max(1, ctx->ny / 16));
+    ctx->seg_rows = int((ctx->ny + nseg - 1) / nseg);
+    ctx->nseg = (ctx->ny + ctx->seg_rows - 1) / ctx->seg_rows;
+    return DUGKS_OK;
+}
+
+template <typename T, int NC>
+cudaError_t launch_step(dugks_ctx* ctx) {
+    const StepArgs<T, NC> a = make_args<T, NC>(ctx, ctx->cur);
+    const Consts<T, NC> k = make_consts<T, NC>(ctx);
+    if (ctx->kernel == DUGKS_KERNEL_NAIVE) {
+        dim3 grid((ctx->nx + 127) / 128, std::min(ctx->ny, 65535));
+        naive_step<T, NC><<<grid, 128, 0, ctx->stream>>>(a, k);
+    } else {
+        const size_t smem = fused_smem(int(ctx->elem), ctx->nt, ctx->stages);
+        dim3 grid(ctx->nstrips, ctx->nseg);
+        const CUtensorMap& tm = ctx->tmap[ctx->cur];
+        switch (ctx->nt) {
+            case 96: fused_step<T, NC, 96><<<grid, 96, smem, ctx->stream>>>(tm, a, k, ctx->seg_rows, ctx->stages); break;
+            case 128: fused_step<T, NC, 128><<<grid, 128, smem, ctx->stream>>>(tm, a, k, ctx->seg_rows, ctx->stages); break;
+            case 160: fused_step<T, NC, 160><<<grid, 160, smem, ctx->stream>>>(tm, a, k, ctx->seg_rows, ctx->stages); break;
+            default: fused_step<T, NC, 192><<<grid, 192, smem, ctx->stream>>>(tm, a, k, ctx->seg_rows, ctx->stages); break;
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_any(dugks_ctx* ctx) {
+    if (ctx->precision == 32)
+        return ctx->nc == NC_SMALL ? launch_step<float, NC_SMALL>(ctx) : launch_step<float, NC_LARGE>(ctx);
+    return ctx->nc == NC_SMALL ? launch_step<double, NC_SMALL>(ctx) : launch_step<double, NC_LARGE>(ctx);
+}
+
+template <typename T, typename Tin>
+cudaError_t launch_init(dugks_ctx* ctx, const Tin* phi0) {
+    const long long n = (long long)ctx->nx * ctx->ny;
+    const int blocks = int(std::min<long long>((n + 255) / 256, 65535));
+    T* f = static_cast<T*>(ctx->buf[ctx->cur]);
+    if (ctx->nc == NC_SMALL)
+        init_kernel<T, NC_SMALL, Tin><<<blocks, 256, 0, ctx->stream>>>(phi0, f, ctx->nx, ctx->ny, ctx->pitch, ctx->plane,
+                                                                      make_consts<T, NC_SMALL>(ctx));
+    else
+        init_kernel<T, NC_LARGE, Tin><<<blocks, 256, 0, ctx->stream>>>(phi0, f, ctx->nx, ctx->ny, ctx->pitch, ctx->plane,
+                                                                      make_consts<T, NC_LARGE>(ctx));
+    return cudaGetLastError();
+}
+
+template <typename T, typename Tout>
+cudaError_t launch_phi(dugks_ctx* ctx, Tout* phi) {
+    const T* f = static_cast<const T*>(ctx->buf[ctx->cur]);
+    phi_mass_kernel<T, Tout><<<ctx->red_blocks, 256, 0, ctx->stream>>>(f, phi, ctx->nx, ctx->ny, ctx->pitch, ctx->plane,
+                                                                       ctx->dxv, ctx->dyv, ctx->partial);
+    sum_partials_kernel<<<1, 256, 0, ctx->stream>>>(ctx->partial, ctx->red_blocks, ctx->mass_dev);
+    return cudaGetLastError();
+}
+
+void free_ctx(dugks_ctx* ctx) {
+    if (!ctx) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
+    for (void* p : {ctx->buf[0], ctx->buf[1], ctx->fxm, ctx->fym, ctx->cxm, ctx->cym}) if (p) cudaFree(p);
+    for (void* p : {static_cast<void*>(ctx->dxv), static_cast<void*>(ctx->dyv), static_cast<void*>(ctx->staging),
+                    static_cast<void*>(ctx->partial), static_cast<void*>(ctx->mass_dev),
+                    static_cast<void*>(ctx->err_dev)})
+        if (p) cudaFree(p);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete ctx;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int now = -1;
+        if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* dugks_status_string(dugks_status s) {
+    switch (s) {
+        case DUGKS_OK: return "ok";
+        case DUGKS_ERR_ARG: return "invalid argument";
+        case DUGKS_ERR_CONFIG: return "invalid configuration";
+        case DUGKS_ERR_CUDA: return "CUDA error";
+        case DUGKS_ERR_NONFINITE: return "non-finite value in phi";
+        case DUGKS_ERR_UNSUPPORTED: return "unsupported";
+        case DUGKS_ERR_NOMEM: return "out of memory";
+        case DUGKS_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+const char* dugks_last_error(const dugks_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+dugks_status dugks_check_config(const dugks_mesh* mesh, const dugks_vset* vset, const dugks_coef* coef, double dt) {
+    if (!mesh || !vset || !coef || !mesh->xf || !mesh->yf) return DUGKS_ERR_ARG;
+    if (mesh->nx < 1 || mesh->ny < 1) return DUGKS_ERR_ARG;
+    if (mesh->nx > (1 << 30) || mesh->ny > (1 << 30)) return DUGKS_ERR_ARG;
+    if (vset->kind != DUGKS_D2Q9) return DUGKS_ERR_ARG;
+    if (coef->nb < 0 || coef->nb > 8 || coef->nd < 0 || coef->nd > 8) return DUGKS_ERR_ARG;
+    for (int w = 0; w < 4; ++w)
+        if (mesh->bc[w] != DUGKS_BC_PERIODIC && mesh->bc[w] != DUGKS_BC_DIRICHLET) return DUGKS_ERR_ARG;
+    if ((mesh->bc[0] == DUGKS_BC_PERIODIC) != (mesh->bc[1] == DUGKS_BC_PERIODIC)) return DUGKS_ERR_ARG;
+    if ((mesh->bc[2] == DUGKS_BC_PERIODIC) != (mesh->bc[3] == DUGKS_BC_PERIODIC)) return DUGKS_ERR_ARG;
+    if (!finite_all(mesh->xf, mesh->nx + 1) || !finite_all(mesh->yf, mesh->ny + 1)) return DUGKS_ERR_CONFIG;
+    if (!finite_all(mesh->bc_value, 4) || !finite_all(coef->u, 2) || !finite_all(coef->b, coef->nb) ||
+        !finite_all(coef->d, coef->nd) || !std::isfinite(coef->alpha) || !std::isfinite(vset->c) || !std::isfinite(dt))
+        return DUGKS_ERR_CONFIG;
+    double hmin = INFINITY;
+    for (int j = 0; j < mesh->nx; ++j) {
+        const double w = mesh->xf[j + 1] - mesh->xf[j];
+        if (!(w > 0.0)) return DUGKS_ERR_CONFIG;
+        hmin = std::min(hmin, w);
+    }
+    for (int k = 0; k < mesh->ny; ++k) {
+        const double w = mesh->yf[k + 1] - mesh->yf[k];
+        if (!(w > 0.0)) return DUGKS_ERR_CONFIG;
+        hmin = std::min(hmin, w);
+    }
+    if (!(vset->c > 0.0) || !(coef->alpha > 0.0) || !(dt > 0.0)) return DUGKS_ERR_CONFIG;
+    if (!(vset->c * dt / hmin < 1.0)) return DUGKS_ERR_CONFIG;
+    return DUGKS_OK;
+}
+
+dugks_status dugks_create(const dugks_mesh* mesh, const dugks_vset* vset, const dugks_coef* coef, double dt,
+                          const dugks_options* opts, dugks_ctx** out) {
+    if (!out) return DUGKS_ERR_ARG;
+    *out = nullptr;
+    dugks_status st = dugks_check_config(mesh, vset, coef, dt);
+    if (st != DUGKS_OK) return st;
+    dugks_options o = {DUGKS_FP32, DUGKS_KERNEL_AUTO, nullptr, -1};
+    if (opts) o = *opts;
+    if (o.precision != DUGKS_FP32 && o.precision != DUGKS_FP64) return DUGKS_ERR_ARG;
+    if (o.kernel != DUGKS_KERNEL_AUTO && o.kernel != DUGKS_KERNEL_FUSED && o.kernel != DUGKS_KERNEL_NAIVE)
+        return DUGKS_ERR_ARG;
+
+    dugks_ctx* ctx = new (std::nothrow) dugks_ctx();
+    if (!ctx) return DUGKS_ERR_NOMEM;
+    if (o.device < 0) {
+        if (cudaGetDevice(&ctx->device) != cudaSuccess) { delete ctx; return DUGKS_ERR_CUDA; }
+    } else {
+        ctx->device = o.device;
+    }
+    DeviceGuard guard(ctx->device);
+    ctx->nx = mesh->nx;
+    ctx->ny = mesh->ny;
+    ctx->precision = o.precision;
+    ctx->kernel = o.kernel == DUGKS_KERNEL_NAIVE ? DUGKS_KERNEL_NAIVE : DUGKS_KERNEL_FUSED;
+    ctx->xper = mesh->bc[0] == DUGKS_BC_PERIODIC;
+    ctx->yper = mesh->bc[2] == DUGKS_BC_PERIODIC;
+    for (int w = 0; w < 4; ++w) ctx->bcv[w] = mesh->bc_value[w];
+    ctx->xf.assign(mesh->xf, mesh->xf + mesh->nx + 1);
+    ctx->yf.assign(mesh->yf, mesh->yf + mesh->ny + 1);
+    ctx->c = vset->c;
+    ctx->dt = dt;
+    ctx->stream = static_cast<cudaStream_t>(o.stream);
+    ctx->elem = ctx->precision == 32 ? sizeof(float) : sizeof(double);
+
+    // relaxation time from the Chapman-Enskog result alpha = c_s^2 lambda (Section 3)
+    const double cs2 = vset->c * vset->c / 3.0;
+    const double lam = coef->alpha / cs2, h = 0.5 * dt;
+    ctx->lambda = lam;
+    double hmin = INFINITY;
+    for (int j = 0; j < ctx->nx; ++j) hmin = std::min(hmin, ctx->xf[j + 1] - ctx->xf[j]);
+    for (int k = 0; k < ctx->ny; ++k) hmin = std::min(hmin, ctx->yf[k + 1] - ctx->yf[k]);
+    ctx->cfl = vset->c * dt / hmin;
+    ctx->a_bp = (2.0 * lam - h) / (2.0 * lam + dt);  // Eq. 2.21
+    ctx->b_bp = 3.0 * h / (2.0 * lam + dt);
+    ctx->a_tp = (2.0 * lam - dt) / (2.0 * lam + dt);  // Eq. 2.13
+    ctx->b_tp = 2.0 * dt / (2.0 * lam + dt);
+    ctx->a_f = 2.0 * lam / (2.0 * lam + h);  // Eq. 2.22
+    ctx->b_f = h / (2.0 * lam + h);
+    ctx->hc = h * vset->c;
+
+    // Equilibrium (Eq. 2.3) per velocity as a polynomial in phi, with
+    // e_i the unit direction, c_s^2 = c^2/3:
+    //   feq_i = w_i [ phi + 3 (e_i.u)/c b + (3|e_i|^2 - 2)/2 (d - phi)
+    //                 + (9 (e_i.u)^2 - 3 |u|^2) / (2 c^2) Cint ]
+    double cint[NC_LARGE];
+    aux_moment_poly(coef, cint);
+    const double wts[Q] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    const double ux = coef->u[0], uy = coef->u[1], c = vset->c;
+    int maxdeg = 1;
+    for (int i = 0; i < Q; ++i) {
+        const double eu = EX(i) * ux + EY(i) * uy;
+        const double e2 = double(EX(i) * EX(i) + EY(i) * EY(i));
+        const double kb = 3.0 * eu / c, kd = (3.0 * e2 - 2.0) / 2.0;
+        const double kc = (9.0 * eu * eu - 3.0 * (ux * ux + uy * uy)) / (2.0 * c * c);
+        for (int m = 0; m < NC_LARGE; ++m) {
+            const double bm = m < coef->nb ? coef->b[m] : 0.0;
+            const double dm = m < coef->nd ? coef->d[m] : 0.0;
+            const double one = m == 1 ? 1.0 : 0.0;
+            const double v = wts[i] * (one + kb * bm + kd * (dm - one) + kc * cint[m]);
+            ctx->feq_coef[i][m] = v;
+            if (v != 0.0) maxdeg = std::max(maxdeg, m);
+        }
+    }
+    ctx->nc = maxdeg < NC_SMALL ? NC_SMALL : NC_LARGE;
+
+    const int lane = 128 / int(ctx->elem);  // rows padded to 128 bytes
+    ctx->pitch = ((long long)ctx->nx + lane - 1) / lane * lane;
+    ctx->plane = ctx->pitch * ctx->ny;
+    const size_t bytes = size_t(Q) * size_t(ctx->plane) * ctx->elem;
+
+    auto fail = [&](dugks_status s) {
+        dugks_status r = s;
+        free_ctx(ctx);
+        return r;
+    };
+    cudaError_t e;
+    for (int b = 0; b < 2; ++b) {
+        e = cudaMalloc(&ctx->buf[b], bytes);
+        if (e != cudaSuccess) { cuda_fail(ctx, e, "cudaMalloc(state)"); return fail(DUGKS_ERR_NOMEM); }
+        e = cudaMemsetAsync(ctx->buf[b], 0, bytes, ctx->stream);
+        if (e != cudaSuccess) return fail(cuda_fail(ctx, e, "cudaMemsetAsync"));
+    }
+    // metrics
+    std::vector<double> dxw, dyw;
+    auto upload = [&](void** dst, const void* src, size_t n) -> cudaError_t {
+        cudaError_t r = cudaMalloc(dst, n);
+        if (r != cudaSuccess) return r;
+        return cudaMemcpy(*dst, src, n, cudaMemcpyHostToDevice);
+    };
+    if (ctx->precision == 32) {
+        std::vector<FaceM<float>> fx, fy;
+        std::vector<CellM<float>> cx, cy;
+        build_metrics<float>(ctx->xf, ctx->xper, ctx->hc, dt, c, fx, cx, dxw);
+        build_metrics<float>(ctx->yf, ctx->yper, ctx->hc, dt, c, fy, cy, dyw);
+        if ((e = upload(&ctx->fxm, fx.data(), fx.size() * sizeof(fx[0]))) != cudaSuccess ||
+            (e = upload(&ctx->fym, fy.data(), fy.size() * sizeof(fy[0]))) != cudaSuccess ||
+            (e = upload(&ctx->cxm, cx.data(), cx.size() * sizeof(cx[0]))) != cudaSuccess ||
+            (e = upload(&ctx->cym, cy.data(), cy.size() * sizeof(cy[0]))) != cudaSuccess)
+            return fail(cuda_fail(ctx, e, "metrics upload"));
+    } else {
+        std::vector<FaceM<double>> fx, fy;
+        std::vector<CellM<double>> cx, cy;
+        build_metrics<double>(ctx->xf, ctx->xper, ctx->hc, dt, c, fx, cx, dxw);
+        build_metrics<double>(ctx->yf, ctx->yper, ctx->hc, dt, c, fy, cy, dyw);
+        if ((e = upload(&ctx->fxm, fx.data(), fx.size() * sizeof(fx[0]))) != cudaSuccess ||
+            (e = upload(&ctx->fym, fy.data(), fy.size() * sizeof(fy[0]))) != cudaSuccess ||
+            (e = upload(&ctx->cxm, cx.data(), cx.size() * sizeof(cx[0]))) != cudaSuccess ||
+            (e = upload(&ctx->cym, cy.data(), cy.size() * sizeof(cy[0]))) != cudaSuccess)
+            return fail(cuda_fail(ctx, e, "metrics upload"));
+    }
+    void* p = nullptr;
+    if ((e = upload(&p, dxw.data(), dxw.size() * sizeof(double))) != cudaSuccess) { ctx->dxv = (double*)p; return fail(cuda_fail(ctx, e, "dx upload")); }
+    ctx->dxv = static_cast<double*>(p);
+    p = nullptr;
+    if ((e = upload(&p, dyw.data(), dyw.size() * sizeof(double))) != cudaSuccess) { ctx->dyv = (double*)p; return fail(cuda_fail(ctx, e, "dy upload")); }
+    ctx->dyv = static_cast<double*>(p);
+    const long long ncell = (long long)ctx->nx * ctx->ny;
+    ctx->red_blocks = int(std::min<long long>((ncell + 255) / 256, 4096));
+    if ((e = cudaMalloc(&ctx->staging, sizeof(double) * size_t(ncell))) != cudaSuccess)
+        return fail(cuda_fail(ctx, e, "cudaMalloc(staging)"));
+    if ((e = cudaMalloc(&ctx->partial, sizeof(double) * size_t(ctx->red_blocks))) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->mass_dev, sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->err_dev, sizeof(int))) != cudaSuccess)
+        return fail(cuda_fail(ctx, e, "cudaMalloc(scalars)"));
+    if ((e = cudaMemsetAsync(ctx->err_dev, 0, sizeof(int), ctx->stream)) != cudaSuccess)
+        return fail(cuda_fail(ctx, e, "cudaMemsetAsync(err)"));
+    if (ctx->kernel == DUGKS_KERNEL_FUSED) {
+        st = plan_fused(ctx);
+        if (st != DUGKS_OK) return fail(st);
+        st = make_tensor_maps(ctx);
+        if (st != DUGKS_OK) return fail(st);
+    }
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return fail(cuda_fail(ctx, e, "cudaStreamSynchronize"));
+    *out = ctx;
+    return DUGKS_OK;
+}
+
+dugks_status dugks_destroy(dugks_ctx* ctx) {
+    if (!ctx) return DUGKS_OK;
+    {
+        DeviceGuard guard(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+    }
+    free_ctx(ctx);
+    return DUGKS_OK;
+}
+
+dugks_status dugks_init_phi(dugks_ctx* ctx, const void* phi0_dev) {
+    if (!ctx || !phi0_dev) return DUGKS_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    cudaError_t e = ctx->precision == 32 ? launch_init<float, float>(ctx, static_cast<const float*>(phi0_dev))
+                                         : launch_init<double, double>(ctx, static_cast<const double*>(phi0_dev));
+    CK(e);
+    ctx->steps_done = 0;
+    return DUGKS_OK;
+}
+
+dugks_status dugks_init_phi_host(dugks_ctx* ctx, const double* phi0_host) {
+    if (!ctx || !phi0_host) return DUGKS_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    const size_t n = size_t(ctx->nx) * ctx->ny;
+    CK(cudaMemcpyAsync(ctx->staging, phi0_host, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    cudaError_t e = ctx->precision == 32 ? launch_init<float, double>(ctx, ctx->staging)
+                                         : launch_init<double, double>(ctx, ctx->staging);
+    CK(e);
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->steps_done = 0;
+    return DUGKS_OK;
+}
+
+dugks_status dugks_step(dugks_ctx* ctx, long long n) {
+    if (!ctx || n < 0) return DUGKS_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    for (long long s = 0; s < n; ++s) {
+        CK(launch_step_any(ctx));
+        ctx->cur ^= 1;
+        ++ctx->steps_done;
+    }
+    return DUGKS_OK;
+}
+
+dugks_status dugks_get_phi(dugks_ctx* ctx, void* phi_dev_out, double* mass_out) {
+    if (!ctx) return DUGKS_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    cudaError_t e = ctx->precision == 32 ? launch_phi<float, float>(ctx, static_cast<float*>(phi_dev_out))
+                                         : launch_phi<double, double>(ctx, static_cast<double*>(phi_dev_out));
+    CK(e);
+    if (mass_out) {
+        CK(cudaMemcpyAsync(mass_out, ctx->mass_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (!std::isfinite(*mass_out)) return DUGKS_ERR_NONFINITE;
+    }
+    return DUGKS_OK;
+}
+
+dugks_status dugks_get_phi_host(dugks_ctx* ctx, double* phi_host_out, double* mass_out) {
+    if (!ctx) return DUGKS_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    cudaError_t e = ctx->precision == 32 ? launch_phi<float, double>(ctx, ctx->staging)
+                                         : launch_phi<double, double>(ctx, ctx->staging);
+    CK(e);
+    const size_t n = size_t(ctx->nx) * ctx->ny;
+    if (phi_host_out)
+        CK(cudaMemcpyAsync(phi_host_out, ctx->staging, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    double m = 0.0;
+    CK(cudaMemcpyAsync(&m, ctx->mass_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (mass_out) *mass_out = m;
+    if (!std::isfinite(m)) return DUGKS_ERR_NONFINITE;
+    return DUGKS_OK;
+}
+
+dugks_status dugks_save_state(dugks_ctx* ctx, void* f_dev_out) {
+    if (!ctx || !f_dev_out) return DUGKS_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    CK(cudaMemcpy2DAsync(f_dev_out, size_t(ctx->nx) * ctx->elem, ctx->buf[ctx->cur], size_t(ctx->pitch) * ctx->elem,
+                         size_t(ctx->nx) * ctx->elem, size_t(Q) * ctx->ny, cudaMemcpyDeviceToDevice, ctx->stream));
+    return DUGKS_OK;
+}
+
+dugks_status dugks_load_state(dugks_ctx* ctx, const void* f_dev_in) {
+    if (!ctx || !f_dev_in) return DUGKS_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    CK(cudaMemcpy2DAsync(ctx->buf[ctx->cur], size_t(ctx->pitch) * ctx->elem, f_dev_in, size_t(ctx->nx) * ctx->elem,
+                         size_t(ctx->nx) * ctx->elem, size_t(Q) * ctx->ny, cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->steps_done = 0;
+    return DUGKS_OK;
+}
+
+dugks_status dugks_set_stream(dugks_ctx* ctx, void* stream) {
+    if (!ctx) return DUGKS_ERR_ARG;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    return DUGKS_OK;
+}
+
+dugks_status dugks_sync(dugks_ctx* ctx) {
+    if (!ctx) return DUGKS_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream));
+    int err = 0;
+    CK(cudaMemcpy(&err, ctx->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        ctx->last_error = "a bounded TMA wait in the step kernel expired";
+        return DUGKS_ERR_TIMEOUT;
+    }
+    return DUGKS_OK;
+}
+
+dugks_status dugks_info(const dugks_ctx* ctx, dugks_info_t* out) {
+    if (!ctx || !out) return DUGKS_ERR_ARG;
+    out->nx = ctx->nx;
+    out->ny = ctx->ny;
+    out->precision = ctx->precision;
+    out->kernel = ctx->kernel;
+    out->pitch = ctx->pitch;
+    out->steps_done = ctx->steps_done;
+    out->dt = ctx->dt;
+    out->lambda = ctx->lambda;
+    out->cfl = ctx->cfl;
+    out->block_threads = ctx->kernel == DUGKS_KERNEL_NAIVE ? 128 : ctx->nt;
+    out->grid_blocks = ctx->kernel == DUGKS_KERNEL_NAIVE ? ((ctx->nx + 127) / 128) * std::min(ctx->ny, 65535)
+                                                         : ctx->nstrips * ctx->nseg;
+    out->state_bytes = (long long)Q * ctx->plane * (long long)ctx->elem;
+    return DUGKS_OK;
+}
+
+}  // extern "C"

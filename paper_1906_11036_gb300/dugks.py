@@ -1,0 +1,244 @@
+"""Thin Python binding of the C ABI in ``include/dugks.h`` (ctypes).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  PyTorch provides device memory (phi and state tensors) and the
+stream.  If the library is missing the import fails loudly; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import inputs
+from .build import LIB
+
+OK = 0
+STATUS = {0: "ok", 1: "invalid argument", 2: "invalid configuration", 3: "CUDA error",
+          4: "non-finite value in phi", 5: "unsupported", 6: "out of memory", 7: "device wait timed out"}
+KERNELS = {"auto": 0, "fused": 1, "naive": 2}
+
+
+class DugksError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}" + (f" ({detail})" if detail else ""))
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("xf", ctypes.POINTER(ctypes.c_double)), ("yf", ctypes.POINTER(ctypes.c_double)),
+                ("bc", ctypes.c_int * 4), ("bc_value", ctypes.c_double * 4)]
+
+
+class VSet(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("c", ctypes.c_double)]
+
+
+class Coef(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_double * 2), ("nb", ctypes.c_int), ("b", ctypes.c_double * 8),
+                ("alpha", ctypes.c_double), ("nd", ctypes.c_int), ("d", ctypes.c_double * 8),
+                ("c_zero", ctypes.c_int)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("kernel", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("device", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("pitch", ctypes.c_longlong), ("steps_done", ctypes.c_longlong), ("dt", ctypes.c_double),
+                ("lam", ctypes.c_double), ("cfl", ctypes.c_double), ("block_threads", ctypes.c_int),
+                ("grid_blocks", ctypes.c_int), ("state_bytes", ctypes.c_longlong)]
+
+
+_lib = None
+
+
+def library():
+    """Load ``libdugks.so`` (build it with ``paper_1906_11036_gb300.build.build()`` first)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise ImportError(f"CUDA library not built: {LIB} (run paper_1906_11036_gb300.build.build())")
+        L = ctypes.CDLL(LIB)
+        vp, P = ctypes.c_void_p, ctypes.POINTER
+        L.dugks_check_config.argtypes = [P(Mesh), P(VSet), P(Coef), ctypes.c_double]
+        L.dugks_create.argtypes = [P(Mesh), P(VSet), P(Coef), ctypes.c_double, P(Options), P(vp)]
+        L.dugks_destroy.argtypes = [vp]
+        L.dugks_init_phi.argtypes = [vp, vp]
+        L.dugks_init_phi_host.argtypes = [vp, P(ctypes.c_double)]
+        L.dugks_step.argtypes = [vp, ctypes.c_longlong]
+        L.dugks_get_phi.argtypes = [vp, vp, P(ctypes.c_double)]
+        L.dugks_get_phi_host.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_double)]
+        L.dugks_save_state.argtypes = [vp, vp]
+        L.dugks_load_state.argtypes = [vp, vp]
+        L.dugks_set_stream.argtypes = [vp, vp]
+        L.dugks_sync.argtypes = [vp]
+        L.dugks_info.argtypes = [vp, P(Info)]
+        L.dugks_status_string.argtypes = [ctypes.c_int]
+        L.dugks_status_string.restype = ctypes.c_char_p
+        L.dugks_last_error.argtypes = [vp]
+        L.dugks_last_error.restype = ctypes.c_char_p
+        for name in ("dugks_check_config", "dugks_create", "dugks_destroy", "dugks_init_phi", "dugks_init_phi_host",
+                     "dugks_step", "dugks_get_phi", "dugks_get_phi_host", "dugks_save_state", "dugks_load_state",
+                     "dugks_set_stream", "dugks_sync", "dugks_info"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def marshal(problem: inputs.Problem):
+    """Problem -> (Mesh, VSet, Coef, keepalive arrays)."""
+    xf = np.ascontiguousarray(problem.xf, dtype=np.float64)
+    yf = np.ascontiguousarray(problem.yf, dtype=np.float64)
+    m = Mesh()
+    m.nx, m.ny = len(xf) - 1, len(yf) - 1
+    m.xf, m.yf = _dptr(xf), _dptr(yf)
+    for i in range(4):
+        m.bc[i] = int(problem.bc[i])
+        m.bc_value[i] = float(problem.bc_value[i])
+    v = VSet()
+    v.kind, v.c = 9, float(problem.c)
+    c = Coef()
+    c.u[0], c.u[1] = float(problem.u[0]), float(problem.u[1])
+    if len(problem.b) > 8 or len(problem.d) > 8:
+        raise ValueError("at most 8 polynomial coefficients")
+    c.nb = len(problem.b)
+    for k, x in enumerate(problem.b):
+        c.b[k] = float(x)
+    c.alpha = float(problem.alpha)
+    c.nd = len(problem.d)
+    for k, x in enumerate(problem.d):
+        c.d[k] = float(x)
+    c.c_zero = int(bool(problem.c_zero))
+    return m, v, c, (xf, yf)
+
+
+def check_config(problem: inputs.Problem) -> int:
+    """Host-only validation (no CUDA call); returns the status code."""
+    m, v, c, keep = marshal(problem)
+    return int(library().dugks_check_config(ctypes.byref(m), ctypes.byref(v), ctypes.byref(c), float(problem.dt)))
+
+
+class Solver:
+    """One NCDE instance advanced by the CUDA DUGKS step."""
+
+    def __init__(self, problem: inputs.Problem, precision: int = 32, kernel: str = "auto", stream=None,
+                 device: int | None = None):
+        import torch
+
+        self.torch = torch
+        self.problem = problem
+        self.precision = int(precision)
+        self.dtype = torch.float32 if self.precision == 32 else torch.float64
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        L = library()
+        m, v, c, keep = marshal(problem)
+        o = Options()
+        o.precision = self.precision
+        o.kernel = KERNELS[kernel]
+        o.stream = ctypes.c_void_p(stream.cuda_stream)
+        o.device = self.device.index
+        h = ctypes.c_void_p()
+        st = L.dugks_create(ctypes.byref(m), ctypes.byref(v), ctypes.byref(c), float(problem.dt), ctypes.byref(o),
+                            ctypes.byref(h))
+        if st != OK:
+            raise DugksError(st, "dugks_create")
+        self.h = h
+        self.L = L
+        self.nx, self.ny = m.nx, m.ny
+
+    # -- helpers --------------------------------------------------------------
+    def _check(self, st, where):
+        if st != OK:
+            raise DugksError(st, where, self.L.dugks_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.dugks_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- API ------------------------------------------------------------------
+    def init_phi(self, phi0):
+        """phi0: CUDA tensor [ny, nx] (converted to the solver's dtype) or a numpy array (host path)."""
+        if isinstance(phi0, np.ndarray):
+            a = np.ascontiguousarray(phi0, dtype=np.float64)
+            assert a.shape == (self.ny, self.nx)
+            self._check(self.L.dugks_init_phi_host(self.h, _dptr(a)), "dugks_init_phi_host")
+            return
+        t = phi0.to(device=self.device, dtype=self.dtype).contiguous()
+        assert tuple(t.shape) == (self.ny, self.nx)
+        self._keep = t
+        self._check(self.L.dugks_init_phi(self.h, ctypes.c_void_p(t.data_ptr())), "dugks_init_phi")
+
+    def step(self, n: int = 1):
+        self._check(self.L.dugks_step(self.h, int(n)), "dugks_step")
+
+    def get_phi(self, out=None, mass: bool = False):
+        """phi as a CUDA tensor [ny, nx]; with mass=True also returns M (synchronises)."""
+        if out is None:
+            out = self.torch.empty((self.ny, self.nx), dtype=self.dtype, device=self.device)
+        m = ctypes.c_double(0.0)
+        self._check(self.L.dugks_get_phi(self.h, ctypes.c_void_p(out.data_ptr()), ctypes.byref(m) if mass else None),
+                    "dugks_get_phi")
+        return (out, m.value) if mass else out
+
+    def get_phi_host(self, out: np.ndarray | None = None):
+        """(phi as float64 numpy [ny, nx], mass); synchronises."""
+        if out is None:
+            out = np.empty((self.ny, self.nx), dtype=np.float64)
+        m = ctypes.c_double(0.0)
+        self._check(self.L.dugks_get_phi_host(self.h, _dptr(out), ctypes.byref(m)), "dugks_get_phi_host")
+        return out, m.value
+
+    def mass(self) -> float:
+        m = ctypes.c_double(0.0)
+        self._check(self.L.dugks_get_phi(self.h, None, ctypes.byref(m)), "dugks_get_phi")
+        return m.value
+
+    def save_state(self, out=None):
+        if out is None:
+            out = self.torch.empty((9, self.ny, self.nx), dtype=self.dtype, device=self.device)
+        self._check(self.L.dugks_save_state(self.h, ctypes.c_void_p(out.data_ptr())), "dugks_save_state")
+        return out
+
+    def load_state(self, f):
+        t = f.to(device=self.device, dtype=self.dtype).contiguous()
+        assert tuple(t.shape) == (9, self.ny, self.nx)
+        self._keep_state = t
+        self._check(self.L.dugks_load_state(self.h, ctypes.c_void_p(t.data_ptr())), "dugks_load_state")
+
+    def set_stream(self, stream):
+        self.stream = stream
+        self._check(self.L.dugks_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream)), "dugks_set_stream")
+
+    def sync(self):
+        self._check(self.L.dugks_sync(self.h), "dugks_sync")
+
+    def info(self) -> dict:
+        i = Info()
+        self._check(self.L.dugks_info(self.h, ctypes.byref(i)), "dugks_info")
+        return {f: getattr(i, f) for f, _ in Info._fields_}
