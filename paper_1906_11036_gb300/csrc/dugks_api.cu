@@ -135,7 +135,9 @@ Consts<T, NC> make_consts(const dugks_ctx* ctx) {
     for (int i = 0; i < Q; ++i)
         for (int m = 0; m < NC; ++m) k.feq[i][m] = T(ctx->feq_coef[i][m]);
     k.a_bp = T(ctx->a_bp); k.b_bp = T(ctx->b_bp);
-    k.a_tp = T(ctx->a_tp); k.b_tp = T(ctx->b_tp);
+    // Eq. 2.13 weights sum to one; keep that exact in the stored precision
+    k.a_tp = T(ctx->a_tp);
+    k.b_tp = T(1.0 - double(k.a_tp));
     k.a_f = T(ctx->a_f); k.b_f = T(ctx->b_f);
     k.hc = T(ctx->hc);
     for (int w = 0; w < 4; ++w) k.bcv[w] = T(ctx->bcv[w]);

@@ -64,10 +64,18 @@ __device__ __forceinline__ T feq_i(const Consts<T, NC>& k, int i, T phi) {
     return s;
 }
 
+// All nine equilibria.  The rest velocity takes feq_0 = phi - sum_{i>0} feq_i
+// (zeroth moment of Eq. 2.7), so that rounded weights cannot bias the
+// discrete mass in single precision.
 template <typename T, int NC>
 __device__ __forceinline__ void feq_all(const Consts<T, NC>& k, T phi, T (&out)[Q]) {
+    T s = T(0);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) out[i] = feq_i(k, i, phi);
+    for (int i = 1; i < Q; ++i) {
+        out[i] = feq_i(k, i, phi);
+        s += out[i];
+    }
+    out[0] = phi - s;
 }
 
 // fbar at a face -> original f for the velocities that cross it

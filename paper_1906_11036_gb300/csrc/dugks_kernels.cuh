@@ -370,9 +370,10 @@ __global__ void init_kernel(const Tin* __restrict__ phi0, T* __restrict__ f, int
     const long long n = (long long)nx * ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int kr = int(c / nx), j = int(c % nx);
-        const T phi = T(phi0[c]);
+        T fe[Q];
+        feq_all(k, T(phi0[c]), fe);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) f[i * plane + kr * pitch + j] = feq_i(k, i, phi);
+        for (int i = 0; i < Q; ++i) f[i * plane + kr * pitch + j] = fe[i];
     }
 }
 
