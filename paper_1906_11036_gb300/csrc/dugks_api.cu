@@ -23,7 +23,6 @@ using namespace dugks;
 
 namespace {
 
-constexpr int NC_SMALL = 4;   // equilibrium polynomials of degree <= 3
 constexpr int NC_LARGE = 16;  // up to degree 15 (nb, nd <= 8)
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -38,7 +37,7 @@ struct dugks_ctx {
     int xper = 1, yper = 1;
     double bcv[4] = {0, 0, 0, 0};
     double c = 1, dt = 0, lambda = 0, cfl = 0;
-    int nc = NC_SMALL;
+    int nc = NC_LARGE;  // equilibrium polynomial coefficients used by the step (3, 4 or 16)
     double feq_coef[Q][NC_LARGE];
     double a_bp = 0, b_bp = 0, a_tp = 0, b_tp = 0, a_f = 0, b_f = 0, hc = 0;
     std::vector<double> xf, yf;
@@ -59,7 +58,7 @@ struct dugks_ctx {
     int* err_dev = nullptr;
     int red_blocks = 0;
     CUtensorMap tmap[2];
-    int nt = 128, stages = 6, seg_rows = 0, nstrips = 0, nseg = 0;
+    int nt = 32, stages = 8, seg_rows = 0, nstrips = 0, nseg = 0, occupancy = 0;
     long long steps_done = 0;
     std::string last_error;
 };
@@ -160,45 +159,23 @@ StepArgs<T, NC> make_args(const dugks_ctx* ctx, int from) {
     return a;
 }
 
-template <typename T, int NC, int NT>
-void* fused_ptr() { return reinterpret_cast<void*>(&fused_step<T, NC, NT>); }
-
-// The fused kernel variants this build instantiates.
-template <typename T, int NC>
-bool fused_variant(int nt, void** fn) {
-    switch (nt) {
-        case 96: *fn = fused_ptr<T, NC, 96>(); return true;
-        case 128: *fn = fused_ptr<T, NC, 128>(); return true;
-        case 160: *fn = fused_ptr<T, NC, 160>(); return true;
-        case 192: *fn = fused_ptr<T, NC, 192>(); return true;
-        default: return false;
-    }
-}
-
-size_t fused_smem(int elem, int nt, int stages) {
-    if (elem == 4) {
-        switch (nt) {
-            case 96: return FusedLayout<float, 96>::bytes(stages);
-            case 128: return FusedLayout<float, 128>::bytes(stages);
-            case 160: return FusedLayout<float, 160>::bytes(stages);
-            default: return FusedLayout<float, 192>::bytes(stages);
+void* fused_fn(const dugks_ctx* ctx) {
+    if (ctx->precision == 32) {
+        switch (ctx->nc) {
+            case 3: return reinterpret_cast<void*>(&fused_step<float, 3>);
+            case 4: return reinterpret_cast<void*>(&fused_step<float, 4>);
+            default: return reinterpret_cast<void*>(&fused_step<float, NC_LARGE>);
         }
     }
-    switch (nt) {
-        case 96: return FusedLayout<double, 96>::bytes(stages);
-        case 128: return FusedLayout<double, 128>::bytes(stages);
-        case 160: return FusedLayout<double, 160>::bytes(stages);
-        default: return FusedLayout<double, 192>::bytes(stages);
+    switch (ctx->nc) {
+        case 3: return reinterpret_cast<void*>(&fused_step<double, 3>);
+        case 4: return reinterpret_cast<void*>(&fused_step<double, 4>);
+        default: return reinterpret_cast<void*>(&fused_step<double, NC_LARGE>);
     }
 }
 
-void* fused_fn(const dugks_ctx* ctx) {
-    void* fn = nullptr;
-    if (ctx->precision == 32)
-        (ctx->nc == NC_SMALL ? fused_variant<float, NC_SMALL>(ctx->nt, &fn) : fused_variant<float, NC_LARGE>(ctx->nt, &fn));
-    else
-        (ctx->nc == NC_SMALL ? fused_variant<double, NC_SMALL>(ctx->nt, &fn) : fused_variant<double, NC_LARGE>(ctx->nt, &fn));
-    return fn;
+size_t fused_smem(const dugks_ctx* ctx) {
+    return ctx->precision == 32 ? WarpLayout<float>::bytes(ctx->stages) : WarpLayout<double>::bytes(ctx->stages);
 }
 
 dugks_status make_tensor_maps(dugks_ctx* ctx) {
@@ -216,7 +193,7 @@ dugks_status make_tensor_maps(dugks_ctx* ctx) {
     const int align = 16 / int(ctx->elem);
     const cuuint64_t dims[3] = {cuuint64_t(ctx->nx), cuuint64_t(ctx->ny), cuuint64_t(Q)};
     const cuuint64_t strides[2] = {cuuint64_t(ctx->pitch) * ctx->elem, cuuint64_t(ctx->plane) * ctx->elem};
-    const cuuint32_t box[3] = {cuuint32_t(ctx->nt + align), 1u, cuuint32_t(Q)};
+    const cuuint32_t box[3] = {cuuint32_t(32 + align), 1u, cuuint32_t(Q)};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     for (int b = 0; b < 2; ++b) {
         CUresult r = encode(&ctx->tmap[b], ctx->precision == 32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
@@ -233,35 +210,27 @@ dugks_status make_tensor_maps(dugks_ctx* ctx) {
     return DUGKS_OK;
 }
 
-// Strip width and segment count of the fused kernel for this grid.
+// Strip and segment counts of the fused kernel for this grid: one warp per
+// (30-column strip, row segment), enough segments to fill every SM.
 dugks_status plan_fused(dugks_ctx* ctx) {
     int sms = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaDeviceGetAttribute");
-    // block width: the variant that wastes the fewest thread columns
-    const int cands[] = {160, 128, 192, 96};
-    int best = 128;
-    double best_eff = -1.0;
-    for (int nt : cands) {
-        const int w = nt - 2;
-        const int strips = (ctx->nx + w - 1) / w;
-        const double eff = double(ctx->nx) / double(strips * nt);
-        if (eff > best_eff + 1e-9) { best_eff = eff; best = nt; }
-    }
-    ctx->nt = best;
-    ctx->stages = ctx->precision == 32 ? 8 : 4;
+    ctx->nt = 32;
+    ctx->stages = ctx->precision == 32 ? 8 : 6;
     void* fn = fused_fn(ctx);
-    const size_t smem = fused_smem(int(ctx->elem), ctx->nt, ctx->stages);
+    const size_t smem = fused_smem(ctx);
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, ctx->nt, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32, smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (occ < 1) {
         ctx->last_error = "fused kernel does not fit on an SM";
         return DUGKS_ERR_UNSUPPORTED;
     }
-    ctx->nstrips = (ctx->nx + ctx->nt - 3) / (ctx->nt - 2);
+    ctx->occupancy = occ;
+    ctx->nstrips = (ctx->nx + WarpLayout<float>::WI - 1) / WarpLayout<float>::WI;
     const long long slots = (long long)sms * occ;
     long long nseg = std::max<long long>(1, slots / ctx->nstrips);
     // at least 16 rows per segment so the two pipeline-fill rows stay cheap
@@ -279,23 +248,26 @@ cudaError_t launch_step(dugks_ctx* ctx) {
         dim3 grid((ctx->nx + 127) / 128, std::min(ctx->ny, 65535));
         naive_step<T, NC><<<grid, 128, 0, ctx->stream>>>(a, k);
     } else {
-        const size_t smem = fused_smem(int(ctx->elem), ctx->nt, ctx->stages);
         dim3 grid(ctx->nstrips, ctx->nseg);
-        const CUtensorMap& tm = ctx->tmap[ctx->cur];
-        switch (ctx->nt) {
-            case 96: fused_step<T, NC, 96><<<grid, 96, smem, ctx->stream>>>(tm, a, k, ctx->seg_rows, ctx->stages); break;
-            case 128: fused_step<T, NC, 128><<<grid, 128, smem, ctx->stream>>>(tm, a, k, ctx->seg_rows, ctx->stages); break;
-            case 160: fused_step<T, NC, 160><<<grid, 160, smem, ctx->stream>>>(tm, a, k, ctx->seg_rows, ctx->stages); break;
-            default: fused_step<T, NC, 192><<<grid, 192, smem, ctx->stream>>>(tm, a, k, ctx->seg_rows, ctx->stages); break;
-        }
+        fused_step<T, NC><<<grid, 32, fused_smem(ctx), ctx->stream>>>(ctx->tmap[ctx->cur], a, k, ctx->seg_rows,
+                                                                     ctx->stages);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_step_any(dugks_ctx* ctx) {
-    if (ctx->precision == 32)
-        return ctx->nc == NC_SMALL ? launch_step<float, NC_SMALL>(ctx) : launch_step<float, NC_LARGE>(ctx);
-    return ctx->nc == NC_SMALL ? launch_step<double, NC_SMALL>(ctx) : launch_step<double, NC_LARGE>(ctx);
+    if (ctx->precision == 32) {
+        switch (ctx->nc) {
+            case 3: return launch_step<float, 3>(ctx);
+            case 4: return launch_step<float, 4>(ctx);
+            default: return launch_step<float, NC_LARGE>(ctx);
+        }
+    }
+    switch (ctx->nc) {
+        case 3: return launch_step<double, 3>(ctx);
+        case 4: return launch_step<double, 4>(ctx);
+        default: return launch_step<double, NC_LARGE>(ctx);
+    }
 }
 
 template <typename T, typename Tin>
@@ -303,12 +275,9 @@ cudaError_t launch_init(dugks_ctx* ctx, const Tin* phi0) {
     const long long n = (long long)ctx->nx * ctx->ny;
     const int blocks = int(std::min<long long>((n + 255) / 256, 65535));
     T* f = static_cast<T*>(ctx->buf[ctx->cur]);
-    if (ctx->nc == NC_SMALL)
-        init_kernel<T, NC_SMALL, Tin><<<blocks, 256, 0, ctx->stream>>>(phi0, f, ctx->nx, ctx->ny, ctx->pitch, ctx->plane,
-                                                                      make_consts<T, NC_SMALL>(ctx));
-    else
-        init_kernel<T, NC_LARGE, Tin><<<blocks, 256, 0, ctx->stream>>>(phi0, f, ctx->nx, ctx->ny, ctx->pitch, ctx->plane,
-                                                                      make_consts<T, NC_LARGE>(ctx));
+    // the initialisation is not on the hot path: always the generic polynomial degree
+    init_kernel<T, NC_LARGE, Tin><<<blocks, 256, 0, ctx->stream>>>(phi0, f, ctx->nx, ctx->ny, ctx->pitch, ctx->plane,
+                                                                  make_consts<T, NC_LARGE>(ctx));
     return cudaGetLastError();
 }
 
@@ -470,7 +439,7 @@ dugks_status dugks_create(const dugks_mesh* mesh, const dugks_vset* vset, const 
             if (v != 0.0) maxdeg = std::max(maxdeg, m);
         }
     }
-    ctx->nc = maxdeg < NC_SMALL ? NC_SMALL : NC_LARGE;
+    ctx->nc = maxdeg <= 2 ? 3 : (maxdeg == 3 ? 4 : NC_LARGE);
 
     const int lane = 128 / int(ctx->elem);  // rows padded to 128 bytes
     ctx->pitch = ((long long)ctx->nx + lane - 1) / lane * lane;

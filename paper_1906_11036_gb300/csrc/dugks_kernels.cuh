@@ -5,15 +5,15 @@
 //   naive_step  : one thread per cell; recomputes P = fbar^+ of its 3x3
 //                 neighbourhood straight from global memory.  A simple
 //                 cross-check of the fused kernel.
-//   fused_step  : the production kernel.  A CTA owns a strip of NT-2
+//   fused_step  : the production kernel.  One warp owns a strip of 30
 //                 columns (plus one halo column on each side) and a segment
 //                 of rows, and marches up the segment one row at a time.
 //                 Each row of ftilde (all nine planes) arrives in shared
 //                 memory by one 3-D TMA copy, several rows ahead, so ftilde
 //                 is read once and written once per step.  P of the last
-//                 three rows, the y-face flux of the row below and the lower
-//                 half of the next y-face stay in registers; x-neighbours
-//                 exchange their halves of the x-face through shared memory.
+//                 rows, the y-face flux of the row below and the lower half
+//                 of the next y-face stay in registers; x-neighbours exchange
+//                 their halves of the x-face by warp shuffles.
 #pragma once
 #include <cuda.h>
 
@@ -158,77 +158,73 @@ __device__ void naive_cell(const StepArgs<T, NC>& a, const Consts<T, NC>& k, con
 // fused streaming kernel
 // ---------------------------------------------------------------------------
 
-template <typename T, int NT>
-struct FusedLayout {
-    static constexpr int ALIGN = 16 / int(sizeof(T));  // TMA x-coordinate granule (16 bytes)
-    static constexpr int BOXW = NT + ALIGN;            // columns per TMA box row
-    static constexpr int STAGE_BYTES = ((Q * BOXW * int(sizeof(T)) + 127) / 128) * 128;
-    static constexpr int PROW = NT + 2;
-    static constexpr int XROW = NT + 1;
-    static size_t bytes(int stages) {
-        return size_t(stages) * STAGE_BYTES + size_t(stages) * 8 +
-               sizeof(T) * (size_t(Q) * PROW + size_t(Q) * XROW + size_t(6) * XROW) + 128;
-    }
+// One warp owns WI = 30 interior columns of one row segment, plus one halo
+// column on each side (lanes 0 and 31); lane l holds column xw - 1 + l.
+// Warps are independent: each has its own ring of S shared-memory stages
+// filled by 3-D TMA copies (one row of all nine planes per copy) and its own
+// mbarriers, and exchanges neighbour values with warp shuffles only.
+template <typename T>
+struct WarpLayout {
+    static constexpr int WI = 30;                       // interior columns per warp
+    static constexpr int ALIGN = 16 / int(sizeof(T));   // TMA x-coordinate granule (16 bytes)
+    static constexpr int BOXW = 32 + ALIGN;             // columns per TMA box row
+    static constexpr int BOX_BYTES = Q * BOXW * int(sizeof(T));
+    static constexpr int STAGE_BYTES = ((BOX_BYTES + 127) / 128) * 128;
+    static size_t bytes(int stages) { return size_t(stages) * (STAGE_BYTES + 8) + 128; }
 };
 
 enum ColRole { ROLE_IN = 0, ROLE_GHOST_W, ROLE_GHOST_E, ROLE_WRAP_W, ROLE_WRAP_E, ROLE_OUT };
 
-template <typename T, int NC, int NT>
-__global__ void __launch_bounds__(NT) fused_step(const __grid_constant__ CUtensorMap tin, const StepArgs<T, NC> a,
-                                                 const Consts<T, NC> k, const int seg_rows, const int S) {
-    using L = FusedLayout<T, NT>;
-    constexpr int W = NT - 2;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    // TMA destinations must be 128-byte aligned; the layout reserves 128 bytes of slack
-    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    unsigned char* stage_base = smem;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + size_t(S) * L::STAGE_BYTES);
-    T* Prow = reinterpret_cast<T*>(bars + S);  // [Q][PROW]
-    T* RX = Prow + Q * L::PROW;                // [Q][XROW]
-    T* FX = RX + Q * L::XROW;                  // [6][XROW]
+template <typename T>
+__device__ __forceinline__ T shfl_dn(T v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+template <typename T>
+__device__ __forceinline__ T shfl_up(T v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 
-    const int t = threadIdx.x;
+template <typename T, int NC, bool EDGE>
+__device__ __forceinline__ void warp_rows(const CUtensorMap* tin, const StepArgs<T, NC>& a, const Consts<T, NC>& k,
+                                          unsigned char* stages, uint64_t* bars, const int S, const int lane,
+                                          const int xw, const int y0, const int y1) {
+    using L = WarpLayout<T>;
     const int nx = a.nx, ny = a.ny;
-    const int x0 = blockIdx.x * W;
-    const int j = x0 - 1 + t;
-    const int xs = (x0 - 1) & ~(L::ALIGN - 1);
-    const int y0 = blockIdx.y * seg_rows;
-    const int y1 = min(y0 + seg_rows, ny);
-    if (y0 >= ny) return;
+    const int j = xw - 1 + lane;
+    const int xs = (xw - 1) & ~(L::ALIGN - 1);
     const int R = y1 - y0 + 2;  // rows r = y0-1 .. y1 pass through the pipeline
 
-    int role, scol;
-    if (j >= 0 && j < nx) { role = ROLE_IN; scol = j; }
-    else if (j == -1) { role = a.xper ? ROLE_WRAP_W : ROLE_GHOST_W; scol = a.xper ? nx - 1 : 0; }
-    else if (j == nx) { role = a.xper ? ROLE_WRAP_E : ROLE_GHOST_E; scol = a.xper ? 0 : nx - 1; }
-    else { role = ROLE_OUT; scol = 0; }
-    const bool from_smem = role == ROLE_IN || role == ROLE_GHOST_W || role == ROLE_GHOST_E;
-    const bool updates = role == ROLE_IN && t >= 1 && t <= W;
-    const bool ghost_col = role == ROLE_GHOST_W || role == ROLE_GHOST_E;
-    const int jm = min(max(j, -1), nx);  // clamped index for metric loads
+    int role = ROLE_IN, scol = j;
+    if (EDGE) {
+        if (j >= 0 && j < nx) { role = ROLE_IN; scol = j; }
+        else if (j == -1) { role = a.xper ? ROLE_WRAP_W : ROLE_GHOST_W; scol = a.xper ? nx - 1 : 0; }
+        else if (j == nx) { role = a.xper ? ROLE_WRAP_E : ROLE_GHOST_E; scol = a.xper ? 0 : nx - 1; }
+        else { role = ROLE_OUT; scol = 0; }
+    }
+    const bool from_smem = !EDGE || role == ROLE_IN || role == ROLE_GHOST_W || role == ROLE_GHOST_E;
+    const bool ghost_col = EDGE && (role == ROLE_GHOST_W || role == ROLE_GHOST_E);
+    const bool updates = (!EDGE || role == ROLE_IN) && lane >= 1 && lane <= L::WI;
+    const int jm = EDGE ? min(max(j, -1), nx) : j;
     const FaceM<T> fW = a.fx[jm + 1], fE = a.fx[jm + 2];
     const CellM<T> cxj = a.cx[jm + 1];
     const T bvx = role == ROLE_GHOST_W ? k.bcv[0] : k.bcv[1];
+    const int soff = scol - xs;  // this lane's column inside a stage row
 
-    if (t == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
-        fence_mbar_init();
+    // per-lane x-face coefficients: value weights for e_x = -1, 0, +1 and the tangential weights
+    T axL[3], axR[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        axL[e] = (T(1) - fE.w) + T(e - 1) * fE.hcd;  // this cell as the left cell of its east face
+        axR[e] = fW.w - T(e - 1) * fW.hcd;           // this cell as the right cell of its west face
     }
-    __syncthreads();
+    const T gxL = k.hc * fE.tl, gxR = k.hc * fW.tr;
 
     auto src_row = [&](int r) -> int {
-        if (r >= 0 && r < ny) return r;
-        if (a.yper) return ((r % ny) + ny) % ny;
-        return r < 0 ? 0 : ny - 1;
+        if (r < 0) return a.yper ? r + ny : 0;
+        if (r >= ny) return a.yper ? r - ny : ny - 1;
+        return r;
     };
-    auto issue = [&](int idx) {
-        const int s = idx % S;
-        unsigned char* dst = stage_base + size_t(s) * L::STAGE_BYTES;
-        mbar_arrive_expect_tx(&bars[s], uint32_t(Q * L::BOXW * sizeof(T)));
-        tma_load_3d(dst, &tin, &bars[s], xs, src_row(y0 - 1 + idx), 0);
-    };
-    if (t == 0) {
-        for (int idx = 0; idx < min(S, R); ++idx) issue(idx);
+    if (lane == 0) {
+        for (int q = 0; q < min(S, R); ++q) {
+            mbar_arrive_expect_tx(&bars[q], uint32_t(L::BOX_BYTES));
+            tma_load_3d(stages + size_t(q) * L::STAGE_BYTES, tin, &bars[q], xs, src_row(y0 - 1 + q), 0);
+        }
     }
 
     T P0[Q], Pm[6], Fp0[Q], Ly[Q], fS[6];
@@ -237,25 +233,39 @@ __global__ void __launch_bounds__(NT) fused_step(const __grid_constant__ CUtenso
 #pragma unroll
     for (int o = 0; o < 6; ++o) { Pm[o] = T(0); fS[o] = T(0); }
 
+    int s = 0;
+    uint32_t ph = 0;
     int idx = 0;
     bool failed = false;
     for (; idx < R; ++idx) {
         const int r = y0 - 1 + idx;
-        const int s = idx % S;
-        const bool ok = mbar_wait_bounded(&bars[s], uint32_t((idx / S) & 1), 2000000000ull);
-        // ---- P (and Fp) of row r for this thread's column ----
-        const T* st = reinterpret_cast<const T*>(stage_base + size_t(s) * L::STAGE_BYTES);
-        const int sr = src_row(r);
-        T ft[Q], fe[Q], P[Q], Fp[Q];
-        T phi = T(0);
+        const bool ok = mbar_wait_bounded(&bars[s], ph, 2000000000ull);
+        if (__any_sync(0xffffffffu, !ok)) { failed = true; break; }
+        // ---- P (and Fp) of row r for this lane's column ----
+        const T* st = reinterpret_cast<const T*>(stages + size_t(s) * L::STAGE_BYTES);
+        T ft[Q];
+        if (from_smem) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            T v = T(0);
-            if (from_smem) v = st[i * L::BOXW + (scol - xs)];
-            else if (role != ROLE_OUT) v = a.fin[i * a.plane + sr * a.pitch + scol];
-            ft[i] = v;
-            phi += v;
+            for (int i = 0; i < Q; ++i) ft[i] = st[i * L::BOXW + soff];
+        } else if (role != ROLE_OUT) {
+            const int sr = src_row(r);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) ft[i] = a.fin[i * a.plane + (long long)sr * a.pitch + scol];
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) ft[i] = T(0);
         }
+        __syncwarp();
+        if (lane == 0 && idx + S < R) {  // refill the stage just consumed
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bars[s], uint32_t(L::BOX_BYTES));
+            tma_load_3d(stages + size_t(s) * L::STAGE_BYTES, tin, &bars[s], xs, src_row(r + S), 0);
+        }
+        if (++s == S) { s = 0; ph ^= 1u; }
+        T phi = ft[0];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) phi += ft[i];
+        T fe[Q], P[Q], Fp[Q];
         feq_all(k, phi, fe);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -263,76 +273,72 @@ __global__ void __launch_bounds__(NT) fused_step(const __grid_constant__ CUtenso
             Fp[i] = fma(k.a_tp, ft[i], k.b_tp * fe[i]);
         }
         const bool ghost_row = !a.yper && (r < 0 || r >= ny);
-        if (ghost_col || ghost_row) {
+        if (ghost_row || ghost_col) {
             const T bv = ghost_col ? bvx : (r < 0 ? k.bcv[2] : k.bcv[3]);
             T fg[Q];
             feq_all(k, T(2) * bv - phi, fg);
 #pragma unroll
             for (int i = 0; i < Q; ++i) P[i] = fg[i] + (P[i] - fe[i]);
         }
-#pragma unroll
-        for (int i = 0; i < Q; ++i) Prow[i * L::PROW + t + 1] = P[i];
-        const int bad = __syncthreads_or(ok ? 0 : 1);
-        if (bad) { failed = true; break; }
-        if (t == 0 && idx + S < R) {
-            fence_proxy_async_smem();
-            issue(idx + S);
-        }
-        // ---- y-face r-1/2 (lower half carried in Ly) and upper half for r+1/2 ----
+        // ---- tangential x-slope of row r, y-face r-1/2 and the lower half of r+1/2 ----
+        const FaceM<T> fyR = a.fy[r + 1], fyN = a.fy[r + 2];
+        const T igx = ghost_row ? T(0) : cxj.ig;
         T Gx[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) Gx[i] = T(0);
-        if (updates && !ghost_row) {
-#pragma unroll
-            for (int i = 0; i < Q; ++i)
-                if (EX(i) != 0) Gx[i] = (Prow[i * L::PROW + t + 2] - Prow[i * L::PROW + t]) * cxj.ig;
+        for (int i = 0; i < Q; ++i) {
+            Gx[i] = T(0);
+            if (EX(i) != 0) Gx[i] = (shfl_dn(P[i]) - shfl_up(P[i])) * igx;
         }
-        const FaceM<T> fyR = a.fy[r + 1], fyN = a.fy[r + 2];
         T fN[6];
         if (idx >= 1) {
+            const T ayR[3] = {fyR.w + fyR.hcd, fyR.w, fyR.w - fyR.hcd};
+            const T gy = k.hc * fyR.tr;
             T fb[Q];
 #pragma unroll
-            for (int i = 0; i < Q; ++i)
-                fb[i] = Ly[i] + ((fyR.w - T(EY(i)) * fyR.hcd) * P[i] - T(EX(i)) * k.hc * fyR.tr * Gx[i]);
+            for (int i = 0; i < Q; ++i) {
+                T v = ayR[EY(i) + 1] * P[i];
+                if (EX(i) != 0) v = fma(-T(EX(i)) * gy, Gx[i], v);
+                fb[i] = Ly[i] + v;
+            }
             face_original<T, NC, false>(k, fb, fN);
         }
+        {
+            const T ayL[3] = {(T(1) - fyN.w) - fyN.hcd, T(1) - fyN.w, (T(1) - fyN.w) + fyN.hcd};
+            const T gy = k.hc * fyN.tl;
 #pragma unroll
-        for (int i = 0; i < Q; ++i)
-            Ly[i] = ((T(1) - fyN.w) + T(EY(i)) * fyN.hcd) * P[i] - T(EX(i)) * k.hc * fyN.tl * Gx[i];
-        // ---- x-faces and update of row k = r-1 ----
+            for (int i = 0; i < Q; ++i) {
+                T v = ayL[EY(i) + 1] * P[i];
+                if (EX(i) != 0) v = fma(-T(EX(i)) * gy, Gx[i], v);
+                Ly[i] = v;
+            }
+        }
+        // ---- x-faces and update of row kr = r-1 ----
         if (idx >= 2) {
             const int kr = r - 1;
             const CellM<T> cyk = a.cy[kr + 1];
-            T Gy[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) Gy[i] = T(0);
-            if (!ghost_col && role != ROLE_OUT) {
-#pragma unroll
-                for (int i = 0; i < Q; ++i)
-                    if (EY(i) != 0) Gy[i] = (P[i] - Pm[YSLOT(i)]) * cyk.ig;
-            }
-            T Lx[Q];
+            const T igy = ghost_col || (EDGE && role == ROLE_OUT) ? T(0) : cyk.ig;
+            T fb[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                Lx[i] = ((T(1) - fE.w) + T(EX(i)) * fE.hcd) * P0[i] - T(EY(i)) * k.hc * fE.tl * Gy[i];
-                RX[i * L::XROW + t] = (fW.w - T(EX(i)) * fW.hcd) * P0[i] - T(EY(i)) * k.hc * fW.tr * Gy[i];
+                T lx = axL[EX(i) + 1] * P0[i], rx = axR[EX(i) + 1] * P0[i];
+                if (EY(i) != 0) {
+                    const T gyv = (P[i] - Pm[YSLOT(i)]) * igy;
+                    lx = fma(-T(EY(i)) * gxL, gyv, lx);
+                    rx = fma(-T(EY(i)) * gxR, gyv, rx);
+                }
+                fb[i] = lx + shfl_dn(rx);
             }
-            __syncthreads();
-            T fb[Q], fEx[6];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) fb[i] = Lx[i] + RX[i * L::XROW + t + 1];
+            T fEx[6], fWx[6];
             face_original<T, NC, true>(k, fb, fEx);
 #pragma unroll
-            for (int o = 0; o < 6; ++o) FX[o * L::XROW + t] = fEx[o];
-            __syncthreads();
+            for (int o = 0; o < 6; ++o) fWx[o] = shfl_up(fEx[o]);  // west face = east face of lane - 1
             if (updates) {
                 T* out = a.fout + (long long)kr * a.pitch + j;
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
                     T v = Fp0[i];
-                    if (XSLOT(i) >= 0)
-                        v -= T(EX(i)) * cxj.r * (fEx[XSLOT(i)] - FX[XSLOT(i) * L::XROW + t - 1]);
-                    if (YSLOT(i) >= 0) v -= T(EY(i)) * cyk.r * (fN[YSLOT(i)] - fS[YSLOT(i)]);
+                    if (XSLOT(i) >= 0) v = fma(-T(EX(i)) * cxj.r, fEx[XSLOT(i)] - fWx[XSLOT(i)], v);
+                    if (YSLOT(i) >= 0) v = fma(-T(EY(i)) * cyk.r, fN[YSLOT(i)] - fS[YSLOT(i)], v);
                     out[i * a.plane] = v;
                 }
             }
@@ -349,14 +355,38 @@ __global__ void __launch_bounds__(NT) fused_step(const __grid_constant__ CUtenso
             for (int o = 0; o < 6; ++o) fS[o] = fN[o];
         }
     }
-    if (failed) {
-        // record the timeout and wait (bounded) for this CTA's copies still in flight
-        if (t == 0) {
-            atomicOr(a.err, 1);
-            for (int q = idx; q < min(idx + S, R); ++q) mbar_wait_bounded(&bars[q % S], uint32_t((q / S) & 1), 100000000ull);
+    if (failed && lane == 0) {
+        // record the timeout; wait (bounded) for this warp's copies still in flight
+        atomicOr(a.err, 1);
+        for (int q = idx; q < min(idx + S, R); ++q) {
+            mbar_wait_bounded(&bars[s], ph, 100000000ull);
+            if (++s == S) { s = 0; ph ^= 1u; }
         }
-        __syncthreads();
     }
+    __syncwarp();
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(32) fused_step(const __grid_constant__ CUtensorMap tin, const StepArgs<T, NC> a,
+                                                 const Consts<T, NC> k, const int seg_rows, const int S) {
+    using L = WarpLayout<T>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // TMA destinations must be 128-byte aligned; the layout reserves 128 bytes of slack
+    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + size_t(S) * L::STAGE_BYTES);
+    const int lane = threadIdx.x;
+    const int xw = blockIdx.x * L::WI;
+    const int y0 = blockIdx.y * seg_rows;
+    const int y1 = min(y0 + seg_rows, a.ny);
+    if (y0 >= a.ny || xw >= a.nx) return;
+    if (lane == 0) {
+        for (int q = 0; q < S; ++q) mbar_init(&bars[q], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const bool edge = xw - 1 < 0 || xw + L::WI >= a.nx;
+    if (edge) warp_rows<T, NC, true>(&tin, a, k, smem, bars, S, lane, xw, y0, y1);
+    else warp_rows<T, NC, false>(&tin, a, k, smem, bars, S, lane, xw, y0, y1);
 }
 
 // ---------------------------------------------------------------------------
