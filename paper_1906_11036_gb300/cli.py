@@ -1,0 +1,50 @@
+"""Command line: advance one of the preset workloads on the GPU.
+
+    python -m paper_1906_11036_gb300.cli --workload nonuniform --n 2048 --steps 5 [--precision 32]
+
+Builds the library if needed, initialises ftilde = feq(phi0) and runs the
+requested number of DUGKS time steps through the C ABI, then prints the
+mass and the range of phi.  Also the command used for kernel profiles.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(prog="python -m paper_1906_11036_gb300.cli")
+    ap.add_argument("--workload", default="nonuniform", choices=["gaussian_hill", "burgers", "nonuniform"])
+    ap.add_argument("--n", type=int, default=None, help="cells per side (default: the preset's)")
+    ap.add_argument("--steps", type=int, default=None, help="time steps (default: the preset's)")
+    ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "fused", "naive"])
+    a = ap.parse_args(argv)
+
+    import torch
+
+    from . import build, inputs
+    from .dugks import Solver
+
+    build.build()
+    maker = inputs.PRESETS[a.workload]
+    p, phi0 = maker() if a.n is None else maker(a.n)
+    steps = p.steps if a.steps is None else a.steps
+    s = Solver(p, precision=a.precision, kernel=a.kernel)
+    s.init_phi(torch.tensor(phi0, device="cuda"))
+    m0 = s.mass()
+    t0 = time.perf_counter()
+    s.step(steps)
+    phi, m = s.get_phi(mass=True)
+    el = time.perf_counter() - t0
+    info = s.info()
+    s.close()
+    print(json.dumps({"workload": p.name, "steps": steps, "precision": a.precision, "mass0": m0, "mass": m,
+                      "phi_min": float(phi.min()), "phi_max": float(phi.max()), "seconds": el,
+                      "block": info["block_threads"], "grid": info["grid_blocks"]}))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -133,13 +134,37 @@ Consts<T, NC> make_consts(const dugks_ctx* ctx) {
     Consts<T, NC> k;
     for (int i = 0; i < Q; ++i)
         for (int m = 0; m < NC; ++m) k.feq[i][m] = T(ctx->feq_coef[i][m]);
-    k.a_bp = T(ctx->a_bp); k.b_bp = T(ctx->b_bp);
+    // Eq. 2.21 weights also sum to one (2h = dt)
+    k.a_bp = T(ctx->a_bp);
+    k.b_bp = T(1.0 - double(k.a_bp));
     // Eq. 2.13 weights sum to one; keep that exact in the stored precision
     k.a_tp = T(ctx->a_tp);
     k.b_tp = T(1.0 - double(k.a_tp));
     k.a_f = T(ctx->a_f); k.b_f = T(ctx->b_f);
+    for (int i = 0; i < Q; ++i)
+        for (int m = 0; m < NC; ++m) {
+            k.hbp[i][m] = T(double(k.b_bp) * ctx->feq_coef[i][m]);
+            k.hf[i][m] = T(ctx->b_f * ctx->feq_coef[i][m]);
+        }
+    k.third = T(1.0 / 3.0);
     k.hc = T(ctx->hc);
     for (int w = 0; w < 4; ++w) k.bcv[w] = T(ctx->bcv[w]);
+    return k;
+}
+
+template <int NC>
+ConstsP<NC> make_constsp(const dugks_ctx* ctx) {
+    ConstsP<NC> k;
+    k.s = make_consts<float, NC>(ctx);
+    for (int q = 0; q < 4; ++q)
+        for (int m = 0; m < NC; ++m) {
+            k.hbp[q][m] = make_float2(k.s.hbp[PA(q)][m], k.s.hbp[PB(q)][m]);
+            k.hf[q][m] = make_float2(k.s.hf[PA(q)][m], k.s.hf[PB(q)][m]);
+        }
+    k.a_bp = k.s.a_bp; k.b_bp = k.s.b_bp; k.third = k.s.third; k.hc = k.s.hc;
+    k.a_bp2 = make_float2(k.a_bp, k.a_bp);
+    k.a_f2 = make_float2(k.s.a_f, k.s.a_f);
+    k.third2 = make_float2(k.third, k.third);
     return k;
 }
 
@@ -162,9 +187,9 @@ StepArgs<T, NC> make_args(const dugks_ctx* ctx, int from) {
 void* fused_fn(const dugks_ctx* ctx) {
     if (ctx->precision == 32) {
         switch (ctx->nc) {
-            case 3: return reinterpret_cast<void*>(&fused_step<float, 3>);
-            case 4: return reinterpret_cast<void*>(&fused_step<float, 4>);
-            default: return reinterpret_cast<void*>(&fused_step<float, NC_LARGE>);
+            case 3: return reinterpret_cast<void*>(&fused_step_vp<3>);
+            case 4: return reinterpret_cast<void*>(&fused_step_vp<4>);
+            default: return reinterpret_cast<void*>(&fused_step<float, NC_LARGE>);  // high degree: scalar path
         }
     }
     switch (ctx->nc) {
@@ -193,7 +218,9 @@ dugks_status make_tensor_maps(dugks_ctx* ctx) {
     const int align = 16 / int(ctx->elem);
     const cuuint64_t dims[3] = {cuuint64_t(ctx->nx), cuuint64_t(ctx->ny), cuuint64_t(Q)};
     const cuuint64_t strides[2] = {cuuint64_t(ctx->pitch) * ctx->elem, cuuint64_t(ctx->plane) * ctx->elem};
-    const cuuint32_t box[3] = {cuuint32_t(32 + align), 1u, cuuint32_t(Q)};
+    const cuuint32_t box[3] = {cuuint32_t(ctx->precision == 32 ? WarpLayout<float>::BOXW : WarpLayout<double>::BOXW),
+                               1u, cuuint32_t(Q)};
+    (void)align;
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     for (int b = 0; b < 2; ++b) {
         CUresult r = encode(&ctx->tmap[b], ctx->precision == 32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
@@ -217,7 +244,9 @@ dugks_status plan_fused(dugks_ctx* ctx) {
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaDeviceGetAttribute");
     ctx->nt = 32;
-    ctx->stages = ctx->precision == 32 ? 8 : 6;
+    ctx->stages = 4;  // rows in flight per warp; deeper rings measured no faster
+    // tuning overrides (pipeline depth and rows per warp), e.g. for a sweep
+    if (const char* v = getenv("DUGKS_STAGES")) ctx->stages = std::max(2, std::min(16, atoi(v)));
     void* fn = fused_fn(ctx);
     const size_t smem = fused_smem(ctx);
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -230,12 +259,14 @@ dugks_status plan_fused(dugks_ctx* ctx) {
         return DUGKS_ERR_UNSUPPORTED;
     }
     ctx->occupancy = occ;
-    ctx->nstrips = (ctx->nx + WarpLayout<float>::WI - 1) / WarpLayout<float>::WI;
+    const int wi = WarpLayout<float>::WI;
+    ctx->nstrips = (ctx->nx + wi - 1) / wi;
     const long long slots = (long long)sms * occ;
     long long nseg = std::max<long long>(1, slots / ctx->nstrips);
     // at least 16 rows per segment so the two pipeline-fill rows stay cheap
     nseg = std::min<long long>(nseg, std::max(1, ctx->ny / 16));
     ctx->seg_rows = int((ctx->ny + nseg - 1) / nseg);
+    if (const char* v = getenv("DUGKS_SEG_ROWS")) ctx->seg_rows = std::max(1, std::min(ctx->ny, atoi(v)));
     ctx->nseg = (ctx->ny + ctx->seg_rows - 1) / ctx->seg_rows;
     return DUGKS_OK;
 }
@@ -249,8 +280,12 @@ cudaError_t launch_step(dugks_ctx* ctx) {
         naive_step<T, NC><<<grid, 128, 0, ctx->stream>>>(a, k);
     } else {
         dim3 grid(ctx->nstrips, ctx->nseg);
-        fused_step<T, NC><<<grid, 32, fused_smem(ctx), ctx->stream>>>(ctx->tmap[ctx->cur], a, k, ctx->seg_rows,
-                                                                     ctx->stages);
+        if constexpr (sizeof(T) == 4 && NC != NC_LARGE)
+            fused_step_vp<NC><<<grid, 32, fused_smem(ctx), ctx->stream>>>(ctx->tmap[ctx->cur], a, make_constsp<NC>(ctx),
+                                                                         ctx->seg_rows, ctx->stages);
+        else
+            fused_step<T, NC><<<grid, 32, fused_smem(ctx), ctx->stream>>>(ctx->tmap[ctx->cur], a, k, ctx->seg_rows,
+                                                                         ctx->stages);
     }
     return cudaGetLastError();
 }

@@ -49,6 +49,9 @@ struct CellM {
 template <typename T, int NC>
 struct Consts {
     T feq[Q][NC];  // feq_i(phi) = sum_m feq[i][m] phi^m
+    T hbp[Q][NC];  // b_bp * feq[i][m]: P = a_bp ft + hbp_i(phi)
+    T hf[Q][NC];   // b_f * feq[i][m]: f = a_f fbar + hf_i(phi_b)
+    T third;       // 1/3 of Eq. 2.23
     T a_bp, b_bp;  // P  = a_bp ft + b_bp feq   (Eq. 2.21)
     T a_tp, b_tp;  // Fp = a_tp ft + b_tp feq   (Eq. 2.13)
     T a_f, b_f;    // f  = a_f fbar + b_f feq(phi_b) at a face (Eq. 2.22)

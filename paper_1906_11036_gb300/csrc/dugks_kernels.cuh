@@ -180,6 +180,23 @@ __device__ __forceinline__ T shfl_dn(T v) { return __shfl_down_sync(0xffffffffu,
 template <typename T>
 __device__ __forceinline__ T shfl_up(T v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 
+// b_bp feq_i(x) and b_f feq_i(x) by Horner's rule (coefficients read straight from the
+// constant bank; i must be a compile-time constant after unrolling)
+template <typename T, int NC>
+__device__ __forceinline__ T hbp_i(const Consts<T, NC>& k, int i, T x) {
+    T s = k.hbp[i][NC - 1];
+#pragma unroll
+    for (int m = NC - 2; m >= 0; --m) s = fma(s, x, k.hbp[i][m]);
+    return s;
+}
+template <typename T, int NC>
+__device__ __forceinline__ T hf_i(const Consts<T, NC>& k, int i, T x) {
+    T s = k.hf[i][NC - 1];
+#pragma unroll
+    for (int m = NC - 2; m >= 0; --m) s = fma(s, x, k.hf[i][m]);
+    return s;
+}
+
 template <typename T, int NC, bool EDGE>
 __device__ __forceinline__ void warp_rows(const CUtensorMap* tin, const StepArgs<T, NC>& a, const Consts<T, NC>& k,
                                           unsigned char* stages, uint64_t* bars, const int S, const int lane,
@@ -204,16 +221,18 @@ __device__ __forceinline__ void warp_rows(const CUtensorMap* tin, const StepArgs
     const FaceM<T> fW = a.fx[jm + 1], fE = a.fx[jm + 2];
     const CellM<T> cxj = a.cx[jm + 1];
     const T bvx = role == ROLE_GHOST_W ? k.bcv[0] : k.bcv[1];
-    const int soff = scol - xs;  // this lane's column inside a stage row
+    const int soff = scol - xs;
 
-    // per-lane x-face coefficients: value weights for e_x = -1, 0, +1 and the tangential weights
+    // x-face weights of this cell, for e_x = -1, 0, +1: as the left cell of its east face and
+    // as the right cell of its west face; tangential weights h c tl and h c tr
     T axL[3], axR[3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-        axL[e] = (T(1) - fE.w) + T(e - 1) * fE.hcd;  // this cell as the left cell of its east face
-        axR[e] = fW.w - T(e - 1) * fW.hcd;           // this cell as the right cell of its west face
+        axL[e] = (T(1) - fE.w) + T(e - 1) * fE.hcd;
+        axR[e] = fW.w - T(e - 1) * fW.hcd;
     }
     const T gxL = k.hc * fE.tl, gxR = k.hc * fW.tr;
+    const T igx_in = cxj.ig, rx = cxj.r;
 
     auto src_row = [&](int r) -> int {
         if (r < 0) return a.yper ? r + ny : 0;
@@ -226,131 +245,173 @@ __device__ __forceinline__ void warp_rows(const CUtensorMap* tin, const StepArgs
             tma_load_3d(stages + size_t(q) * L::STAGE_BYTES, tin, &bars[q], xs, src_row(y0 - 1 + q), 0);
         }
     }
-
-    T P0[Q], Pm[6], Fp0[Q], Ly[Q], fS[6];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) { P0[i] = T(0); Fp0[i] = T(0); Ly[i] = T(0); }
-#pragma unroll
-    for (int o = 0; o < 6; ++o) { Pm[o] = T(0); fS[o] = T(0); }
-
-    int s = 0;
+    int s = 0, issued = min(S, R), consumed = 0;
     uint32_t ph = 0;
-    int idx = 0;
-    bool failed = false;
-    for (; idx < R; ++idx) {
-        const int r = y0 - 1 + idx;
+
+    // next row of ftilde from the pipeline; refills the stage it frees
+    auto load_row = [&](int r, T (&ft)[Q]) -> bool {
         const bool ok = mbar_wait_bounded(&bars[s], ph, 2000000000ull);
-        if (__any_sync(0xffffffffu, !ok)) { failed = true; break; }
-        // ---- P (and Fp) of row r for this lane's column ----
-        const T* st = reinterpret_cast<const T*>(stages + size_t(s) * L::STAGE_BYTES);
-        T ft[Q];
+        if (__any_sync(0xffffffffu, !ok)) return false;
         if (from_smem) {
+            const T* st = reinterpret_cast<const T*>(stages + size_t(s) * L::STAGE_BYTES) + soff;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) ft[i] = st[i * L::BOXW + soff];
+            for (int i = 0; i < Q; ++i) ft[i] = st[i * L::BOXW];
         } else if (role != ROLE_OUT) {
-            const int sr = src_row(r);
+            const long long base = (long long)src_row(r) * a.pitch + scol;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) ft[i] = a.fin[i * a.plane + (long long)sr * a.pitch + scol];
+            for (int i = 0; i < Q; ++i) ft[i] = a.fin[i * a.plane + base];
         } else {
 #pragma unroll
             for (int i = 0; i < Q; ++i) ft[i] = T(0);
         }
         __syncwarp();
-        if (lane == 0 && idx + S < R) {  // refill the stage just consumed
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&bars[s], uint32_t(L::BOX_BYTES));
-            tma_load_3d(stages + size_t(s) * L::STAGE_BYTES, tin, &bars[s], xs, src_row(r + S), 0);
+        if (issued < R) {
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&bars[s], uint32_t(L::BOX_BYTES));
+                tma_load_3d(stages + size_t(s) * L::STAGE_BYTES, tin, &bars[s], xs, src_row(r + S), 0);
+            }
+            ++issued;
         }
         if (++s == S) { s = 0; ph ^= 1u; }
+        ++consumed;
+        return true;
+    };
+    // P = fbar^+ (Eq. 2.21, with b_bp folded into the equilibrium polynomials) and
+    // Fp = ftilde^+ = P + (P - ft)/3 (Eq. 2.23); ghost cells by the NEE reading
+    auto cell_row = [&](int r, const T (&ft)[Q], T (&P)[Q], T (&Fp)[Q]) {
         T phi = ft[0];
 #pragma unroll
         for (int i = 1; i < Q; ++i) phi += ft[i];
-        T fe[Q], P[Q], Fp[Q];
-        feq_all(k, phi, fe);
+        T hs = T(0);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            P[i] = fma(k.a_bp, ft[i], k.b_bp * fe[i]);
-            Fp[i] = fma(k.a_tp, ft[i], k.b_tp * fe[i]);
+        for (int i = 1; i < Q; ++i) {
+            const T h = hbp_i(k, i, phi);
+            P[i] = fma(k.a_bp, ft[i], h);
+            hs += h;
         }
+        P[0] = fma(k.a_bp, ft[0], fma(k.b_bp, phi, -hs));  // rest velocity via the zeroth moment
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Fp[i] = fma(k.third, P[i] - ft[i], P[i]);
         const bool ghost_row = !a.yper && (r < 0 || r >= ny);
         if (ghost_row || ghost_col) {
             const T bv = ghost_col ? bvx : (r < 0 ? k.bcv[2] : k.bcv[3]);
-            T fg[Q];
+            T fe[Q], fg[Q];
+            feq_all(k, phi, fe);
             feq_all(k, T(2) * bv - phi, fg);
 #pragma unroll
             for (int i = 0; i < Q; ++i) P[i] = fg[i] + (P[i] - fe[i]);
         }
-        // ---- tangential x-slope of row r, y-face r-1/2 and the lower half of r+1/2 ----
-        const FaceM<T> fyR = a.fy[r + 1], fyN = a.fy[r + 2];
-        const T igx = ghost_row ? T(0) : cxj.ig;
-        T Gx[Q];
+    };
+    // tangential x-slope of P (zero on ghost rows: only ever weighted by zero there)
+    auto grad_x = [&](int r, const T (&P)[Q], T (&Gx)[Q]) {
+        const T ig = (!a.yper && (r < 0 || r >= ny)) ? T(0) : igx_in;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             Gx[i] = T(0);
-            if (EX(i) != 0) Gx[i] = (shfl_dn(P[i]) - shfl_up(P[i])) * igx;
+            if (EX(i) != 0) Gx[i] = (shfl_dn(P[i]) - shfl_up(P[i])) * ig;
         }
-        T fN[6];
-        if (idx >= 1) {
-            const T ayR[3] = {fyR.w + fyR.hcd, fyR.w, fyR.w - fyR.hcd};
-            const T gy = k.hc * fyR.tr;
-            T fb[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                T v = ayR[EY(i) + 1] * P[i];
-                if (EX(i) != 0) v = fma(-T(EX(i)) * gy, Gx[i], v);
-                fb[i] = Ly[i] + v;
-            }
-            face_original<T, NC, false>(k, fb, fN);
-        }
-        {
-            const T ayL[3] = {(T(1) - fyN.w) - fyN.hcd, T(1) - fyN.w, (T(1) - fyN.w) + fyN.hcd};
-            const T gy = k.hc * fyN.tl;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                T v = ayL[EY(i) + 1] * P[i];
-                if (EX(i) != 0) v = fma(-T(EX(i)) * gy, Gx[i], v);
-                Ly[i] = v;
-            }
-        }
-        // ---- x-faces and update of row kr = r-1 ----
-        if (idx >= 2) {
-            const int kr = r - 1;
-            const CellM<T> cyk = a.cy[kr + 1];
-            const T igy = ghost_col || (EDGE && role == ROLE_OUT) ? T(0) : cyk.ig;
-            T fb[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                T lx = axL[EX(i) + 1] * P0[i], rx = axR[EX(i) + 1] * P0[i];
-                if (EY(i) != 0) {
-                    const T gyv = (P[i] - Pm[YSLOT(i)]) * igy;
-                    lx = fma(-T(EY(i)) * gxL, gyv, lx);
-                    rx = fma(-T(EY(i)) * gxR, gyv, rx);
-                }
-                fb[i] = lx + shfl_dn(rx);
-            }
-            T fEx[6], fWx[6];
-            face_original<T, NC, true>(k, fb, fEx);
-#pragma unroll
-            for (int o = 0; o < 6; ++o) fWx[o] = shfl_up(fEx[o]);  // west face = east face of lane - 1
-            if (updates) {
-                T* out = a.fout + (long long)kr * a.pitch + j;
-#pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    T v = Fp0[i];
-                    if (XSLOT(i) >= 0) v = fma(-T(EX(i)) * cxj.r, fEx[XSLOT(i)] - fWx[XSLOT(i)], v);
-                    if (YSLOT(i) >= 0) v = fma(-T(EY(i)) * cyk.r, fN[YSLOT(i)] - fS[YSLOT(i)], v);
-                    out[i * a.plane] = v;
-                }
-            }
-        }
-        // ---- rotate the row window ----
+    };
+    // this row's half of the y-face above it (face r+1/2, lower cell)
+    auto lower_half = [&](int r, const T (&P)[Q], const T (&Gx)[Q], T (&Ly)[Q]) {
+        const FaceM<T> f = a.fy[r + 2];
+        const T ay[3] = {(T(1) - f.w) - f.hcd, T(1) - f.w, (T(1) - f.w) + f.hcd};
+        const T g = k.hc * f.tl;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            if (EY(i) != 0) Pm[YSLOT(i)] = P0[i];
-            P0[i] = P[i];
-            Fp0[i] = Fp[i];
+            T v = ay[EY(i) + 1] * P[i];
+            if (EX(i) != 0) v = fma(-T(EX(i)) * g, Gx[i], v);
+            Ly[i] = v;
         }
-        if (idx >= 1) {
+    };
+    // y-face r-1/2 from the lower half Ly and this row (upper cell): original f of the crossing velocities
+    auto y_face = [&](int r, const T (&P)[Q], const T (&Gx)[Q], const T (&Ly)[Q], T (&fy)[6]) {
+        const FaceM<T> f = a.fy[r + 1];
+        const T ay[3] = {f.w + f.hcd, f.w, f.w - f.hcd};
+        const T g = k.hc * f.tr;
+        T fb[Q];
+        T phib = T(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            T v = ay[EY(i) + 1] * P[i];
+            if (EX(i) != 0) v = fma(-T(EX(i)) * g, Gx[i], v);
+            fb[i] = Ly[i] + v;
+            phib += fb[i];
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            if (YSLOT(i) >= 0) fy[YSLOT(i)] = fma(k.a_f, fb[i], hf_i(k, i, phib));
+    };
+    // x-faces of row kr and its cell update (Eq. 2.12)
+    auto x_update = [&](int kr, const T (&P0)[Q], const T (&P)[Q], const T (&Pm)[6], const T (&Fp0)[Q],
+                        const T (&fN)[6], const T (&fS)[6]) {
+        const CellM<T> cyk = a.cy[kr + 1];
+        const T igy = (ghost_col || (EDGE && role == ROLE_OUT)) ? T(0) : cyk.ig;
+        T fb[Q];
+        T phib = T(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            T lx = axL[EX(i) + 1] * P0[i], rxh = axR[EX(i) + 1] * P0[i];
+            if (EY(i) != 0) {
+                const T gyv = (P[i] - Pm[YSLOT(i)]) * igy;
+                lx = fma(-T(EY(i)) * gxL, gyv, lx);
+                rxh = fma(-T(EY(i)) * gxR, gyv, rxh);
+            }
+            fb[i] = lx + shfl_dn(rxh);
+            phib += fb[i];
+        }
+        T fEx[6], dW[6];
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            if (XSLOT(i) >= 0) fEx[XSLOT(i)] = fma(k.a_f, fb[i], hf_i(k, i, phib));
+#pragma unroll
+        for (int o = 0; o < 6; ++o) dW[o] = fEx[o] - shfl_up(fEx[o]);  // east minus west (lane - 1's east)
+        if (updates) {
+            T* out = a.fout + (long long)kr * a.pitch + j;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                T v = Fp0[i];
+                if (XSLOT(i) >= 0) v = fma(-T(EX(i)) * rx, dW[XSLOT(i)], v);
+                if (YSLOT(i) >= 0) v = fma(-T(EY(i)) * cyk.r, fN[YSLOT(i)] - fS[YSLOT(i)], v);
+                out[i * a.plane] = v;
+            }
+        }
+    };
+
+    bool failed = false;
+    T ft[Q], P0[Q], Fp0[Q], Pm[6], Ly[Q], fS[6], Gx[Q];
+    // ---- pipeline fill: rows y0-1 and y0 ----
+    if (!load_row(y0 - 1, ft)) { failed = true; }
+    if (!failed) {
+        cell_row(y0 - 1, ft, P0, Fp0);
+        grad_x(y0 - 1, P0, Gx);
+        lower_half(y0 - 1, P0, Gx, Ly);
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            if (EY(i) != 0) Pm[YSLOT(i)] = P0[i];
+        if (!load_row(y0, ft)) failed = true;
+    }
+    if (!failed) {
+        cell_row(y0, ft, P0, Fp0);
+        grad_x(y0, P0, Gx);
+        y_face(y0, P0, Gx, Ly, fS);
+        lower_half(y0, P0, Gx, Ly);
+        // ---- steady state: row r enters, row r-1 is updated ----
+#pragma unroll 2
+        for (int r = y0 + 1; r <= y1; ++r) {
+            T P[Q], Fp[Q], fN[6];
+            if (!load_row(r, ft)) { failed = true; break; }
+            cell_row(r, ft, P, Fp);
+            grad_x(r, P, Gx);
+            y_face(r, P, Gx, Ly, fN);
+            lower_half(r, P, Gx, Ly);
+            x_update(r - 1, P0, P, Pm, Fp0, fN, fS);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                if (EY(i) != 0) Pm[YSLOT(i)] = P0[i];
+                P0[i] = P[i];
+                Fp0[i] = Fp[i];
+            }
 #pragma unroll
             for (int o = 0; o < 6; ++o) fS[o] = fN[o];
         }
@@ -358,7 +419,7 @@ __device__ __forceinline__ void warp_rows(const CUtensorMap* tin, const StepArgs
     if (failed && lane == 0) {
         // record the timeout; wait (bounded) for this warp's copies still in flight
         atomicOr(a.err, 1);
-        for (int q = idx; q < min(idx + S, R); ++q) {
+        for (int q = consumed; q < issued; ++q) {
             mbar_wait_bounded(&bars[s], ph, 100000000ull);
             if (++s == S) { s = 0; ph ^= 1u; }
         }
@@ -387,6 +448,342 @@ __global__ void __launch_bounds__(32) fused_step(const __grid_constant__ CUtenso
     const bool edge = xw - 1 < 0 || xw + L::WI >= a.nx;
     if (edge) warp_rows<T, NC, true>(&tin, a, k, smem, bars, S, lane, xw, y0, y1);
     else warp_rows<T, NC, false>(&tin, a, k, smem, bars, S, lane, xw, y0, y1);
+}
+
+// ---------------------------------------------------------------------------
+// fused streaming kernel, single precision, velocity pairs
+// ---------------------------------------------------------------------------
+//
+// Same dataflow and lane layout as fused_step (one cell per lane, 30 interior
+// columns per warp).  The nine velocities are grouped into the opposite
+// pairs q = (1,3), (2,4), (5,7), (6,8) plus the rest velocity 0; a pair is one
+// float2 and runs on the packed FP32 instructions of sm_100+ (__fadd2_rn,
+// __fmul2_rn, __ffma2_rn), halving the issue slots of the per-velocity
+// arithmetic.  The pair's second velocity is the opposite of the first, so
+// every per-pair weight has the form (a + s b, a - s b).
+
+struct F2 {
+    float2 v;
+};
+__device__ __forceinline__ F2 f2(float a, float b) { return F2{make_float2(a, b)}; }
+__device__ __forceinline__ F2 f2(float a) { return F2{make_float2(a, a)}; }
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2{__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2{__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) { return F2{__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2{__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)}; }
+__device__ __forceinline__ F2 shfl_dn2(F2 x) {
+    return f2(__shfl_down_sync(0xffffffffu, x.v.x, 1), __shfl_down_sync(0xffffffffu, x.v.y, 1));
+}
+__device__ __forceinline__ F2 shfl_up2(F2 x) {
+    return f2(__shfl_up_sync(0xffffffffu, x.v.x, 1), __shfl_up_sync(0xffffffffu, x.v.y, 1));
+}
+// (a + s b, a - s b) for the direction sign s of a pair's first velocity
+__device__ __forceinline__ F2 sgn2(float a, float b, int s) {
+    return s > 0 ? f2(a + b, a - b) : (s < 0 ? f2(a - b, a + b) : f2(a));
+}
+
+// pair q holds velocities (PA(q), PB(q)); QX, QY = direction of PA(q)
+__host__ __device__ constexpr int PA(int q) { return q == 0 ? 1 : q == 1 ? 2 : q == 2 ? 5 : 6; }
+__host__ __device__ constexpr int PB(int q) { return q == 0 ? 3 : q == 1 ? 4 : q == 2 ? 7 : 8; }
+__host__ __device__ constexpr int QX(int q) { return EX(PA(q)); }
+__host__ __device__ constexpr int QY(int q) { return EY(PA(q)); }
+
+// resident warps per SM the packed kernel is compiled for (sets its register budget)
+#ifndef DUGKS_VP_MIN_WARPS
+#define DUGKS_VP_MIN_WARPS 16
+#endif
+
+struct V9 {
+    F2 p[4];
+    float z;  // rest velocity
+};
+
+template <int NC>
+struct ConstsP {
+    float2 hbp[4][NC];  // per pair: b_bp * (feq_PA, feq_PB) coefficients in powers of phi
+    float2 hf[4][NC];   // per pair: b_f * (feq_PA, feq_PB)
+    float2 a_bp2, a_f2, third2;
+    float a_bp, b_bp, third, hc;
+    Consts<float, NC> s;  // scalar constants (ghost cells)
+};
+
+template <int NC>
+__device__ __forceinline__ F2 hbp2(const ConstsP<NC>& k, int q, F2 x) {
+    F2 s{k.hbp[q][NC - 1]};
+#pragma unroll
+    for (int m = NC - 2; m >= 0; --m) s = fma2(s, x, F2{k.hbp[q][m]});
+    return s;
+}
+template <int NC>
+__device__ __forceinline__ F2 hf2(const ConstsP<NC>& k, int q, F2 x) {
+    F2 s{k.hf[q][NC - 1]};
+#pragma unroll
+    for (int m = NC - 2; m >= 0; --m) s = fma2(s, x, F2{k.hf[q][m]});
+    return s;
+}
+__device__ __forceinline__ float vsum(const V9& a) {
+    const F2 s = (a.p[0] + a.p[1]) + (a.p[2] + a.p[3]);
+    return a.z + (s.v.x + s.v.y);
+}
+
+template <int NC, bool EDGE>
+__device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<float, NC>& a, const ConstsP<NC>& k,
+                                        unsigned char* stages, uint64_t* bars, const int S, const int lane,
+                                        const int xw, const int y0, const int y1) {
+    using L = WarpLayout<float>;
+    const int nx = a.nx, ny = a.ny;
+    const int j = xw - 1 + lane;
+    const int xs = (xw - 1) & ~(L::ALIGN - 1);
+    const int R = y1 - y0 + 2;
+
+    int role = ROLE_IN, scol = j;
+    if (EDGE) {
+        if (j >= 0 && j < nx) { role = ROLE_IN; scol = j; }
+        else if (j == -1) { role = a.xper ? ROLE_WRAP_W : ROLE_GHOST_W; scol = a.xper ? nx - 1 : 0; }
+        else if (j == nx) { role = a.xper ? ROLE_WRAP_E : ROLE_GHOST_E; scol = a.xper ? 0 : nx - 1; }
+        else { role = ROLE_OUT; scol = 0; }
+    }
+    const bool from_smem = !EDGE || role == ROLE_IN || role == ROLE_GHOST_W || role == ROLE_GHOST_E;
+    const bool ghost_col = EDGE && (role == ROLE_GHOST_W || role == ROLE_GHOST_E);
+    const bool updates = (!EDGE || role == ROLE_IN) && lane >= 1 && lane <= L::WI;
+    const int jm = EDGE ? min(max(j, -1), nx) : j;
+    const FaceM<float> fW = a.fx[jm + 1], fE = a.fx[jm + 2];
+    const CellM<float> cxj = a.cx[jm + 1];
+    const float bvx = role == ROLE_GHOST_W ? k.s.bcv[0] : k.s.bcv[1];
+    const int soff = scol - xs;
+
+    // per-lane x-face weights for pairs with e_x sign +1 (q = 0, 2), -1 (q = 3), 0 (q = 1)
+    const F2 axLp = sgn2(1.f - fE.w, fE.hcd, 1), axLn = sgn2(1.f - fE.w, fE.hcd, -1), axL0 = f2(1.f - fE.w);
+    const F2 axRp = sgn2(fW.w, -fW.hcd, 1), axRn = sgn2(fW.w, -fW.hcd, -1), axR0 = f2(fW.w);
+    const F2 gxL = sgn2(0.f, -k.hc * fE.tl, 1), gxR = sgn2(0.f, -k.hc * fW.tr, 1);  // all y-crossing pairs have e_y sign +1
+    const F2 rxp = sgn2(0.f, -cxj.r, 1), rxn = sgn2(0.f, -cxj.r, -1);
+    auto axL = [&](int q) { return QX(q) > 0 ? axLp : (QX(q) < 0 ? axLn : axL0); };
+    auto axR = [&](int q) { return QX(q) > 0 ? axRp : (QX(q) < 0 ? axRn : axR0); };
+    const float igx_in = cxj.ig;
+
+    auto src_row = [&](int r) -> int {
+        if (r < 0) return a.yper ? r + ny : 0;
+        if (r >= ny) return a.yper ? r - ny : ny - 1;
+        return r;
+    };
+    if (lane == 0) {
+        for (int q = 0; q < min(S, R); ++q) {
+            mbar_arrive_expect_tx(&bars[q], uint32_t(L::BOX_BYTES));
+            tma_load_3d(stages + size_t(q) * L::STAGE_BYTES, tin, &bars[q], xs, src_row(y0 - 1 + q), 0);
+        }
+    }
+    int s = 0, issued = min(S, R), consumed = 0;
+    uint32_t ph = 0;
+
+    auto load_row = [&](int r, V9& F) -> bool {
+        const bool ok = mbar_wait_bounded(&bars[s], ph, 2000000000ull);
+        if (__any_sync(0xffffffffu, !ok)) return false;
+        float ft[Q];
+        if (from_smem) {
+            const float* st = reinterpret_cast<const float*>(stages + size_t(s) * L::STAGE_BYTES) + soff;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) ft[i] = st[i * L::BOXW];
+        } else if (role != ROLE_OUT) {
+            const long long base = (long long)src_row(r) * a.pitch + scol;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) ft[i] = a.fin[i * a.plane + base];
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) ft[i] = 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) F.p[q] = f2(ft[PA(q)], ft[PB(q)]);
+        F.z = ft[0];
+        __syncwarp();
+        if (issued < R) {
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&bars[s], uint32_t(L::BOX_BYTES));
+                tma_load_3d(stages + size_t(s) * L::STAGE_BYTES, tin, &bars[s], xs, src_row(r + S), 0);
+            }
+            ++issued;
+        }
+        if (++s == S) { s = 0; ph ^= 1u; }
+        ++consumed;
+        return true;
+    };
+    // P (Eq. 2.21, b_bp folded into the polynomials) and Fp = P + (P - ft)/3 (Eq. 2.23)
+    auto cell_row = [&](int r, const V9& F, V9& P, V9& Fp) {
+        const float phi = vsum(F);
+        const F2 phi2 = f2(phi);
+        F2 hs = f2(0.f);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const F2 h = hbp2(k, q, phi2);
+            P.p[q] = fma2(F2{k.a_bp2}, F.p[q], h);
+            hs = hs + h;
+        }
+        P.z = fmaf(k.a_bp, F.z, fmaf(k.b_bp, phi, -(hs.v.x + hs.v.y)));  // rest velocity via the zeroth moment
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Fp.p[q] = fma2(F2{k.third2}, P.p[q] - F.p[q], P.p[q]);
+        Fp.z = fmaf(k.third, P.z - F.z, P.z);
+        const bool ghost_row = !a.yper && (r < 0 || r >= ny);
+        if (ghost_row || ghost_col) {
+            const float bv = ghost_col ? bvx : (r < 0 ? k.s.bcv[2] : k.s.bcv[3]);
+            float fe[Q], fg[Q];
+            feq_all(k.s, phi, fe);
+            feq_all(k.s, 2.f * bv - phi, fg);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                P.p[q] = P.p[q] + f2(fg[PA(q)] - fe[PA(q)], fg[PB(q)] - fe[PB(q)]);
+            P.z += fg[0] - fe[0];
+        }
+    };
+    auto grad_x = [&](int r, const V9& P, F2 (&Gx)[4]) {
+        const F2 ig = f2((!a.yper && (r < 0 || r >= ny)) ? 0.f : igx_in);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (QX(q) != 0) Gx[q] = (shfl_dn2(P.p[q]) - shfl_up2(P.p[q])) * ig;
+    };
+    auto lower_half = [&](const FaceM<float>& f, const V9& P, const F2 (&Gx)[4], V9& Ly) {
+        const F2 ayp = sgn2(1.f - f.w, f.hcd, 1), ay0 = f2(1.f - f.w);
+        const F2 gp = sgn2(0.f, -k.hc * f.tl, 1), gn = sgn2(0.f, -k.hc * f.tl, -1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            F2 v = (QY(q) != 0 ? ayp : ay0) * P.p[q];
+            if (QX(q) != 0) v = fma2(QX(q) > 0 ? gp : gn, Gx[q], v);
+            Ly.p[q] = v;
+        }
+        Ly.z = (1.f - f.w) * P.z;
+    };
+    auto y_face = [&](const FaceM<float>& f, const V9& P, const F2 (&Gx)[4], const V9& Ly, F2 (&fy)[4]) {
+        const F2 ayp = sgn2(f.w, -f.hcd, 1), ay0 = f2(f.w);
+        const F2 gp = sgn2(0.f, -k.hc * f.tr, 1), gn = sgn2(0.f, -k.hc * f.tr, -1);
+        V9 fb;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            F2 v = (QY(q) != 0 ? ayp : ay0) * P.p[q];
+            if (QX(q) != 0) v = fma2(QX(q) > 0 ? gp : gn, Gx[q], v);
+            fb.p[q] = Ly.p[q] + v;
+        }
+        fb.z = fmaf(f.w, P.z, Ly.z);
+        const F2 phib = f2(vsum(fb));
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (QY(q) != 0) fy[q] = fma2(F2{k.a_f2}, fb.p[q], hf2(k, q, phib));
+    };
+    auto x_update = [&](int kr, const V9& P0, const V9& P, const F2 (&Pm)[4], const V9& Fp0, const F2 (&fN)[4],
+                        const F2 (&fS)[4]) {
+        const CellM<float> cyk = a.cy[kr + 1];
+        const F2 igy = f2((ghost_col || (EDGE && role == ROLE_OUT)) ? 0.f : cyk.ig);
+        V9 fb;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            F2 lx = axL(q) * P0.p[q], rxh = axR(q) * P0.p[q];
+            if (QY(q) != 0) {
+                const F2 gyv = (P.p[q] - Pm[q]) * igy;
+                lx = fma2(gxL, gyv, lx);
+                rxh = fma2(gxR, gyv, rxh);
+            }
+            fb.p[q] = lx + shfl_dn2(rxh);
+        }
+        fb.z = (1.f - fE.w) * P0.z + __shfl_down_sync(0xffffffffu, fW.w * P0.z, 1);
+        const F2 phib = f2(vsum(fb));
+        F2 dW[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (QX(q) != 0) {
+                const F2 fe = fma2(F2{k.a_f2}, fb.p[q], hf2(k, q, phib));
+                dW[q] = fe - shfl_up2(fe);  // east minus west (lane - 1's east face)
+            }
+        const F2 ryp = sgn2(0.f, -cyk.r, 1);
+        V9 v = Fp0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (QX(q) != 0) v.p[q] = fma2(QX(q) > 0 ? rxp : rxn, dW[q], v.p[q]);
+            if (QY(q) != 0) v.p[q] = fma2(ryp, fN[q] - fS[q], v.p[q]);
+        }
+        if (updates) {
+            float* out = a.fout + (long long)kr * a.pitch + j;
+            out[0] = v.z;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                out[PA(q) * a.plane] = v.p[q].v.x;
+                out[PB(q) * a.plane] = v.p[q].v.y;
+            }
+        }
+    };
+
+    bool failed = false;
+    V9 F, P0, Fp0, Ly;
+    F2 Pm[4], fS[4], Gx[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { Pm[q] = fS[q] = Gx[q] = f2(0.f); }
+    if (!load_row(y0 - 1, F)) failed = true;
+    // face metrics: fyB = face below the current row, fyA = face above it (index f+1 for face f)
+    FaceM<float> fyB = a.fy[y0], fyA = a.fy[y0 + 1];
+    if (!failed) {
+        cell_row(y0 - 1, F, P0, Fp0);
+        grad_x(y0 - 1, P0, Gx);
+        lower_half(fyA, P0, Gx, Ly);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Pm[q] = P0.p[q];
+        if (!load_row(y0, F)) failed = true;
+    }
+    if (!failed) {
+        fyB = fyA;
+        fyA = a.fy[y0 + 2];
+        cell_row(y0, F, P0, Fp0);
+        grad_x(y0, P0, Gx);
+        y_face(fyB, P0, Gx, Ly, fS);
+        lower_half(fyA, P0, Gx, Ly);
+#pragma unroll 2
+        for (int r = y0 + 1; r <= y1; ++r) {
+            V9 P, Fp;
+            F2 fN[4];
+            if (!load_row(r, F)) { failed = true; break; }
+            fyB = fyA;
+            fyA = a.fy[r + 2];
+            cell_row(r, F, P, Fp);
+            grad_x(r, P, Gx);
+            y_face(fyB, P, Gx, Ly, fN);
+            lower_half(fyA, P, Gx, Ly);
+            x_update(r - 1, P0, P, Pm, Fp0, fN, fS);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                Pm[q] = P0.p[q];
+                fS[q] = fN[q];
+            }
+            P0 = P;
+            Fp0 = Fp;
+        }
+    }
+    if (failed && lane == 0) {
+        atomicOr(a.err, 1);
+        for (int q = consumed; q < issued; ++q) {
+            mbar_wait_bounded(&bars[s], ph, 100000000ull);
+            if (++s == S) { s = 0; ph ^= 1u; }
+        }
+    }
+    __syncwarp();
+}
+
+template <int NC>
+__global__ void __launch_bounds__(32, DUGKS_VP_MIN_WARPS) fused_step_vp(const __grid_constant__ CUtensorMap tin,
+                                                        const StepArgs<float, NC> a, const ConstsP<NC> k,
+                                                        const int seg_rows, const int S) {
+    using L = WarpLayout<float>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + size_t(S) * L::STAGE_BYTES);
+    const int lane = threadIdx.x;
+    const int xw = blockIdx.x * L::WI;
+    const int y0 = blockIdx.y * seg_rows;
+    const int y1 = min(y0 + seg_rows, a.ny);
+    if (y0 >= a.ny || xw >= a.nx) return;
+    if (lane == 0) {
+        for (int q = 0; q < S; ++q) mbar_init(&bars[q], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const bool edge = xw - 1 < 0 || xw + L::WI >= a.nx;
+    if (edge) vp_rows<NC, true>(&tin, a, k, smem, bars, S, lane, xw, y0, y1);
+    else vp_rows<NC, false>(&tin, a, k, smem, bars, S, lane, xw, y0, y1);
 }
 
 // ---------------------------------------------------------------------------
