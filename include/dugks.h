@@ -174,6 +174,38 @@ dugks_status dugks_sync(dugks_ctx *ctx);
 /* Sizes and launch shape of a context. */
 dugks_status dugks_info(const dugks_ctx *ctx, dugks_info_t *out);
 
+/* ---- allocation-free variant -------------------------------------------
+ * No counterpart in the paper: a convenience for callers that cannot
+ * allocate device memory, for example a host application whose memory pool
+ * already owns the GPU's free memory, or code that must not trigger the
+ * device-wide synchronisation that cudaMalloc/cudaFree may imply.
+ *
+ * Computes the same phi = sum_i ftilde_i and mass M = sum |V_jk| phi_jk as
+ * dugks_get_phi, without a context and without allocating anything: the
+ * per-block partial sums live in a fixed array in the library's device
+ * memory (DUGKS_NOALLOC_MAX_BLOCKS doubles = 512 KiB, present on every GPU
+ * that loads the library until the process exits).
+ *
+ *   f_dev        device, [9][ny][nx] contiguous, float (precision 32) or double (64)
+ *   dx_dev       device, nx doubles: cell widths in x; dy_dev: ny doubles in y
+ *   phi_dev_out  device, [ny][nx] of the precision's type, or NULL
+ *   mass_dev_out device, one double (written; not read)
+ *   stream       cudaStream_t or NULL for the legacy default stream
+ *
+ * Asynchronous on `stream`.  Returns DUGKS_ERR_ARG for null pointers, a bad
+ * precision or nx, ny < 1, and DUGKS_ERR_UNSUPPORTED when nx*ny exceeds
+ * DUGKS_NOALLOC_MAX_CELLS (one partial sum per 256 cells).  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All
+ * calls share the one array: calls that overlap on the GPU (concurrent
+ * streams, or several host threads) race and must be serialised by the
+ * caller.  Every partial sum is overwritten before it is read, so nothing
+ * from an earlier call leaks into a later one. */
+#define DUGKS_NOALLOC_MAX_BLOCKS 65536
+#define DUGKS_NOALLOC_MAX_CELLS (256LL * DUGKS_NOALLOC_MAX_BLOCKS)
+dugks_status dugks_phi_mass_noalloc(const void *f_dev, int precision, int nx, int ny, const double *dx_dev,
+                                    const double *dy_dev, void *phi_dev_out, double *mass_dev_out, void *stream);
+
 /* Static text for a status code; never NULL. */
 const char *dugks_status_string(dugks_status s);
 

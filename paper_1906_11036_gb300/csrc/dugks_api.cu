@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -678,3 +679,55 @@ dugks_status dugks_info(const dugks_ctx* ctx, dugks_info_t* out) {
 }
 
 }  // extern "C"
+
+// ---- allocation-free phi / mass --------------------------------------------
+// Partial sums of the reduction live in this fixed device array instead of
+// a context's buffer.  Host code cannot use the symbol's address directly
+// (in host code it names a host-side shadow), so its device address is
+// looked up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) double g_noalloc_partial[DUGKS_NOALLOC_MAX_BLOCKS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+cudaError_t noalloc_scratch(int dev, double** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partial);  // the current device is `dev`
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
+extern "C" dugks_status dugks_phi_mass_noalloc(const void* f_dev, int precision, int nx, int ny,
+                                               const double* dx_dev, const double* dy_dev, void* phi_dev_out,
+                                               double* mass_dev_out, void* stream) {
+    if (!f_dev || !dx_dev || !dy_dev || !mass_dev_out) return DUGKS_ERR_ARG;
+    if (precision != DUGKS_FP32 && precision != DUGKS_FP64) return DUGKS_ERR_ARG;
+    if (nx < 1 || ny < 1) return DUGKS_ERR_ARG;
+    const long long n = (long long)nx * ny;
+    if (n > DUGKS_NOALLOC_MAX_CELLS) return DUGKS_ERR_UNSUPPORTED;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DUGKS_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return DUGKS_ERR_UNSUPPORTED;
+    double* partial = nullptr;
+    if (noalloc_scratch(dev, &partial) != cudaSuccess) return DUGKS_ERR_CUDA;
+    const int blocks = int((n + 255) / 256);  // one partial per 256 cells, each written exactly once
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == DUGKS_FP32)
+        phi_mass_kernel<float, float><<<blocks, 256, 0, s>>>(static_cast<const float*>(f_dev),
+                                                             static_cast<float*>(phi_dev_out), nx, ny, nx, n, dx_dev,
+                                                             dy_dev, partial);
+    else
+        phi_mass_kernel<double, double><<<blocks, 256, 0, s>>>(static_cast<const double*>(f_dev),
+                                                               static_cast<double*>(phi_dev_out), nx, ny, nx, n,
+                                                               dx_dev, dy_dev, partial);
+    sum_partials_kernel<<<1, 256, 0, s>>>(partial, blocks, mass_dev_out);
+    return cudaGetLastError() == cudaSuccess ? DUGKS_OK : DUGKS_ERR_CUDA;
+}
