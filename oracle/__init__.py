@@ -70,6 +70,8 @@ def lib():
         L.oracle_step.argtypes = [P, dp, dp, ctypes.c_int]
         L.oracle_run.argtypes = [P, dp, ctypes.c_long, ctypes.c_int]
         L.oracle_max_threads.restype = ctypes.c_int
+        L.oracle_equilibrium_deriv.argtypes = [P, ctypes.c_double, dp]
+        L.oracle_adjoint_step.argtypes = [P, dp, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -116,6 +118,11 @@ class Oracle:
         self.L.oracle_equilibrium(ctypes.byref(self.s), float(phi), _ptr(out))
         return out
 
+    def equilibrium_deriv(self, phi: float) -> np.ndarray:
+        out = np.zeros(Q)
+        self.L.oracle_equilibrium_deriv(ctypes.byref(self.s), float(phi), _ptr(out))
+        return out
+
     def cell_transforms(self, ft, feq):
         ft = np.ascontiguousarray(ft, dtype=np.float64)
         feq = np.ascontiguousarray(feq, dtype=np.float64)
@@ -151,6 +158,39 @@ class Oracle:
         if rc != 0:
             raise RuntimeError(f"oracle_run failed ({rc})")
         return f
+
+    def adjoint_step(self, f: np.ndarray, mu: np.ndarray):
+        """(lam, dJ/dalpha) for one step at state f given mu = dJ/d f^{n+1}."""
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+        lam = np.empty_like(f)
+        da = ctypes.c_double(0.0)
+        rc = self.L.oracle_adjoint_step(ctypes.byref(self.s), _ptr(f), _ptr(mu), _ptr(lam),
+                                        ctypes.cast(ctypes.pointer(da), ctypes.POINTER(ctypes.c_double)))
+        if rc != 0:
+            raise RuntimeError(f"oracle_adjoint_step failed ({rc})")
+        return lam, da.value
+
+    def gradient(self, phi0: np.ndarray, nsteps: int, dj_dphiN, threads: int = 0):
+        """Reverse-mode gradient of J(phi^N) with respect to phi0 and alpha, storing
+        every state: dj_dphiN(phi^N) returns dJ/dphi^N; returns (J-independent)
+        (grad_phi0, dJ/dalpha, phi^N)."""
+        states = [self.init(phi0)]
+        for _ in range(nsteps):
+            states.append(self.step(states[-1], threads))
+        phiN = self.phi(states[-1])
+        g = np.asarray(dj_dphiN(phiN), dtype=np.float64)
+        lam = np.broadcast_to(g, (Q,) + g.shape).copy()   # phi = sum_i f_i
+        dalpha = 0.0
+        for n in range(nsteps - 1, -1, -1):
+            lam, da = self.adjoint_step(states[n], lam)
+            dalpha += da
+        # f^0 = feq(phi0): dJ/dphi0 = sum_i feq_i'(phi0) lam_i
+        gphi = np.zeros_like(phi0, dtype=np.float64)
+        for k in range(self.ny):
+            for j in range(self.nx):
+                gphi[k, j] = float(self.equilibrium_deriv(phi0[k, j]) @ lam[:, k, j])
+        return gphi, dalpha, phiN
 
     def phi(self, f: np.ndarray) -> np.ndarray:
         f = np.ascontiguousarray(f, dtype=np.float64)

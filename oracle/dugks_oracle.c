@@ -131,6 +131,33 @@ void oracle_equilibrium(const oracle_problem *p, double phi, double *feq) {
     }
 }
 
+/* d feq_i / d phi, term by term from Eq. 2.3: B' = u b', D' = d' I, C' = u u b'^2. */
+void oracle_equilibrium_deriv(const oracle_problem *p, double phi, double *dfeq) {
+    const double cs2 = p->c * p->c / 3.0;
+    double db = 0.0, dd = 0.0, pw = 1.0;
+    for (int k = 1; k < p->nb; k++) { db += k * p->b[k] * pw; pw *= phi; }
+    pw = 1.0;
+    for (int k = 1; k < p->nd; k++) { dd += k * p->d[k] * pw; pw *= phi; }
+    const double dc = p->c_zero ? 0.0 : db * db;
+    double dB[2], dT[2][2];
+    for (int a = 0; a < 2; a++) dB[a] = p->u[a] * db;
+    for (int a = 0; a < 2; a++)
+        for (int e = 0; e < 2; e++) {
+            double delta = (a == e) ? 1.0 : 0.0;
+            dT[a][e] = cs2 * dd * delta + p->u[a] * p->u[e] * dc - cs2 * delta;
+        }
+    for (int i = 0; i < Q; i++) {
+        double ci[2] = {CX[i] * p->c, CY[i] * p->c};
+        double contr = 0.0;
+        for (int a = 0; a < 2; a++)
+            for (int e = 0; e < 2; e++) {
+                double delta = (a == e) ? 1.0 : 0.0;
+                contr += dT[a][e] * (ci[a] * ci[e] - cs2 * delta);
+            }
+        dfeq[i] = WT[i] * (1.0 + (ci[0] * dB[0] + ci[1] * dB[1]) / cs2 + contr / (2.0 * cs2 * cs2));
+    }
+}
+
 static double relax_time(const oracle_problem *p) { return p->alpha / (p->c * p->c / 3.0); }
 
 /* Eqs. 2.21 and 2.13 for one cell: fbar^+ and ftilde^+ from ftilde and feq. */
@@ -450,4 +477,224 @@ int oracle_max_threads(void) {
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------ */
+/* Adjoint of one time step (reverse mode of oracle_step)              */
+/* ------------------------------------------------------------------ */
+/*
+ * Given f = ftilde^n and mu = dJ/d ftilde^{n+1}, returns lam = dJ/d ftilde^n
+ * = (d step / d f)^T mu, and adds to *dj_dalpha the explicit dependence of
+ * the step on alpha (through lambda = alpha / c_s^2 in the weights of Eqs.
+ * 2.13, 2.21 and 2.22) contracted with mu.  The forward quantities are
+ * recomputed exactly as in oracle_step; every stage is then transposed in
+ * reverse order: cell update, face flux and Eq. 2.22, reconstruction
+ * (Eqs. 2.19, 2.20, 2.26), ghost cells, Eqs. 2.21 / 2.13, phi = sum f.
+ */
+int oracle_adjoint_step(const oracle_problem *p, const double *f_in, const double *mu, double *lam,
+                        double *dj_dalpha) {
+    if (!valid(p)) return -2;
+    workspace ws, *w = &ws;
+    if (ws_alloc(w, p) != 0) { ws_free(w); return -1; }
+    const int nx = p->nx, ny = p->ny, ex = nx + 2, ey = ny + 2;
+    const size_t n = (size_t)nx * ny, ne = (size_t)ex * ey;
+    const double h = 0.5 * p->dt, dt = p->dt, lam_t = relax_time(p);
+    const double den1 = 2.0 * lam_t + dt, den2 = 2.0 * lam_t + h;
+    const double a_bp = (2.0 * lam_t - h) / den1, b_bp = 3.0 * h / den1;
+    const double a_tp = (2.0 * lam_t - dt) / den1, b_tp = 2.0 * dt / den1;
+    const double a_f = 2.0 * lam_t / den2, b_f = h / den2;
+    /* derivatives of the weights with respect to lambda */
+    const double da_bp = 2.0 * (dt + h) / (den1 * den1), db_bp = -6.0 * h / (den1 * den1);
+    const double da_tp = 4.0 * dt / (den1 * den1), db_tp = -4.0 * dt / (den1 * den1);
+    const double da_f = 2.0 * h / (den2 * den2), db_f = -2.0 * h / (den2 * den2);
+    const int xper = p->bc[WALL_W] == BC_PERIODIC, yper = p->bc[WALL_S] == BC_PERIODIC;
+    double djdl = 0.0;
+
+    /* forward recomputation: phi, feq, fbar^+ with halo */
+    for (int k = 0; k < ny; k++)
+        for (int j = 0; j < nx; j++) {
+            size_t c = (size_t)k * nx + j;
+            double ft[Q], feq[Q], fbp[Q], ftp[Q], phi = 0.0;
+            for (int i = 0; i < Q; i++) { ft[i] = f_in[i * n + c]; phi += ft[i]; }
+            oracle_equilibrium(p, phi, feq);
+            oracle_cell_transforms(p, ft, feq, fbp, ftp);
+            w->phi[c] = phi;
+            for (int i = 0; i < Q; i++) {
+                w->feq[i * n + c] = feq[i];
+                EXT(w, i, k + 1, j + 1) = fbp[i];
+            }
+        }
+    fill_halo(p, w);
+
+    double *Pb = calloc(Q * ne, sizeof(double));   /* adjoint of fbar^+ on the extended grid */
+    if (!Pb) { ws_free(w); return -1; }
+#define PB(i, k, j) Pb[((size_t)(i) * ey + (size_t)(k)) * ex + (size_t)(j)]
+
+    /* x-faces: recompute fbar, phi_b; then the adjoint of the face */
+    for (int k = 0; k < ny; k++)
+        for (int jf = 0; jf <= nx; jf++) {
+            const int jl = jf, jr = jf + 1, ke = k + 1;
+            const double xb = p->xf[jf], dxc = w->xc[jr] - w->xc[jl];
+            const double wgt = (xb - w->xc[jl]) / dxc;
+            const int wallW = !xper && jf == 0, wallE = !xper && jf == nx;
+            double fbar[Q], gtl[Q], gtr[Q];
+            for (int i = 0; i < Q; i++) {
+                double gn = (EXT(w, i, ke, jr) - EXT(w, i, ke, jl)) / dxc;
+                double val = EXT(w, i, ke, jl) + (xb - w->xc[jl]) * gn;
+                double gt;
+                if (wallW) gt = grad_y(w, i, ke, jr);
+                else if (wallE) gt = grad_y(w, i, ke, jl);
+                else gt = (1.0 - wgt) * grad_y(w, i, ke, jl) + wgt * grad_y(w, i, ke, jr);
+                fbar[i] = val - h * (CX[i] * p->c * gn + CY[i] * p->c * gt);
+                gtl[i] = wallW ? 0.0 : (wallE ? 1.0 : 1.0 - wgt); /* weight of the left G */
+                gtr[i] = wallE ? 0.0 : (wallW ? 1.0 : wgt);       /* weight of the right G */
+            }
+            double phib = 0.0, feqb[Q], dfeqb[Q];
+            for (int i = 0; i < Q; i++) phib += fbar[i];
+            oracle_equilibrium(p, phib, feqb);
+            oracle_equilibrium_deriv(p, phib, dfeqb);
+            /* adjoint of the face values f_i: the update is ftp - dt/|V| (c_ix f_E dy - c_ix f_W dy + ...) */
+            double fbarf[Q], s = 0.0;
+            for (int i = 0; i < Q; i++) {
+                double g = 0.0;
+                if (jf >= 1) g -= dt / (p->xf[jf] - p->xf[jf - 1]) * CX[i] * p->c * mu[i * n + (size_t)k * nx + (jf - 1)];
+                if (jf <= nx - 1) g += dt / (p->xf[jf + 1] - p->xf[jf]) * CX[i] * p->c * mu[i * n + (size_t)k * nx + jf];
+                fbarf[i] = g;  /* dJ/d f_i at this face */
+                djdl += g * (da_f * fbar[i] + db_f * feqb[i]);
+                s += g * b_f * dfeqb[i];
+            }
+            for (int i = 0; i < Q; i++) {
+                const double fbb = a_f * fbarf[i] + s;  /* dJ/d fbar_i (Eq. 2.22 and phi_b = sum fbar) */
+                const double cl = 1.0 - (xb - w->xc[jl]) / dxc + h * CX[i] * p->c / dxc;
+                const double cr = (xb - w->xc[jl]) / dxc - h * CX[i] * p->c / dxc;
+                PB(i, ke, jl) += cl * fbb;
+                PB(i, ke, jr) += cr * fbb;
+                const double gb = -h * CY[i] * p->c * fbb;  /* dJ/d gt */
+                if (gtl[i] != 0.0) {
+                    const double q = gb * gtl[i] / (w->yc[ke + 1] - w->yc[ke - 1]);
+                    PB(i, ke + 1, jl) += q;
+                    PB(i, ke - 1, jl) -= q;
+                }
+                if (gtr[i] != 0.0) {
+                    const double q = gb * gtr[i] / (w->yc[ke + 1] - w->yc[ke - 1]);
+                    PB(i, ke + 1, jr) += q;
+                    PB(i, ke - 1, jr) -= q;
+                }
+            }
+        }
+    /* y-faces */
+    for (int kf = 0; kf <= ny; kf++)
+        for (int j = 0; j < nx; j++) {
+            const int kl = kf, kr = kf + 1, je = j + 1;
+            const double yb = p->yf[kf], dyc = w->yc[kr] - w->yc[kl];
+            const double wgt = (yb - w->yc[kl]) / dyc;
+            const int wallS = !yper && kf == 0, wallN = !yper && kf == ny;
+            double fbar[Q], gtl[Q], gtr[Q];
+            for (int i = 0; i < Q; i++) {
+                double gn = (EXT(w, i, kr, je) - EXT(w, i, kl, je)) / dyc;
+                double val = EXT(w, i, kl, je) + (yb - w->yc[kl]) * gn;
+                double gt;
+                if (wallS) gt = grad_x(w, i, kr, je);
+                else if (wallN) gt = grad_x(w, i, kl, je);
+                else gt = (1.0 - wgt) * grad_x(w, i, kl, je) + wgt * grad_x(w, i, kr, je);
+                fbar[i] = val - h * (CX[i] * p->c * gt + CY[i] * p->c * gn);
+                gtl[i] = wallS ? 0.0 : (wallN ? 1.0 : 1.0 - wgt);
+                gtr[i] = wallN ? 0.0 : (wallS ? 1.0 : wgt);
+            }
+            double phib = 0.0, feqb[Q], dfeqb[Q];
+            for (int i = 0; i < Q; i++) phib += fbar[i];
+            oracle_equilibrium(p, phib, feqb);
+            oracle_equilibrium_deriv(p, phib, dfeqb);
+            double fbarf[Q], s = 0.0;
+            for (int i = 0; i < Q; i++) {
+                double g = 0.0;
+                if (kf >= 1) g -= dt / (p->yf[kf] - p->yf[kf - 1]) * CY[i] * p->c * mu[i * n + (size_t)(kf - 1) * nx + j];
+                if (kf <= ny - 1) g += dt / (p->yf[kf + 1] - p->yf[kf]) * CY[i] * p->c * mu[i * n + (size_t)kf * nx + j];
+                fbarf[i] = g;
+                djdl += g * (da_f * fbar[i] + db_f * feqb[i]);
+                s += g * b_f * dfeqb[i];
+            }
+            for (int i = 0; i < Q; i++) {
+                const double fbb = a_f * fbarf[i] + s;
+                const double cl = 1.0 - (yb - w->yc[kl]) / dyc + h * CY[i] * p->c / dyc;
+                const double cr = (yb - w->yc[kl]) / dyc - h * CY[i] * p->c / dyc;
+                PB(i, kl, je) += cl * fbb;
+                PB(i, kr, je) += cr * fbb;
+                const double gb = -h * CX[i] * p->c * fbb;
+                if (gtl[i] != 0.0) {
+                    const double q = gb * gtl[i] / (w->xc[je + 1] - w->xc[je - 1]);
+                    PB(i, kl, je + 1) += q;
+                    PB(i, kl, je - 1) -= q;
+                }
+                if (gtr[i] != 0.0) {
+                    const double q = gb * gtr[i] / (w->xc[je + 1] - w->xc[je - 1]);
+                    PB(i, kr, je + 1) += q;
+                    PB(i, kr, je - 1) -= q;
+                }
+            }
+        }
+    /* ghosts, in the reverse order of fill_halo */
+    double *phib_extra = calloc(n, sizeof(double));  /* dJ/d phi of interior cells through NEE ghosts */
+    if (!phib_extra) { free(Pb); ws_free(w); return -1; }
+    if (yper)
+        for (int i = 0; i < Q; i++)
+            for (int j = 0; j <= nx + 1; j++) {
+                PB(i, ny, j) += PB(i, 0, j);
+                PB(i, 1, j) += PB(i, ny + 1, j);
+                PB(i, 0, j) = PB(i, ny + 1, j) = 0.0;
+            }
+    if (xper)
+        for (int i = 0; i < Q; i++)
+            for (int k = 0; k <= ny + 1; k++) {
+                PB(i, k, nx) += PB(i, k, 0);
+                PB(i, k, 1) += PB(i, k, nx + 1);
+                PB(i, k, 0) = PB(i, k, nx + 1) = 0.0;
+            }
+    /* NEE ghost (jg,kg) from interior (ji,ki): P_g = feq(2 bv - phi_1) + P_1 - feq(phi_1) */
+#define FOLD(jg, kg, ji, ki, bv)                                                                 \
+    do {                                                                                         \
+        const size_t c1 = (size_t)((ki) - 1) * nx + (size_t)((ji) - 1);                          \
+        const double phi1 = w->phi[c1], phig = 2.0 * (bv) - phi1;                                \
+        double d1[Q], dg[Q], acc = 0.0;                                                          \
+        oracle_equilibrium_deriv(p, phi1, d1);                                                   \
+        oracle_equilibrium_deriv(p, phig, dg);                                                   \
+        for (int i = 0; i < Q; i++) {                                                            \
+            const double g = PB(i, (kg), (jg));                                                  \
+            PB(i, (ki), (ji)) += g;                                                              \
+            acc -= g * (dg[i] + d1[i]);                                                          \
+            PB(i, (kg), (jg)) = 0.0;                                                             \
+        }                                                                                        \
+        phib_extra[c1] += acc;                                                                   \
+    } while (0)
+    if (!xper)
+        for (int k = 1; k <= ny; k++) {
+            FOLD(0, k, 1, k, p->bc_value[WALL_W]);
+            FOLD(nx + 1, k, nx, k, p->bc_value[WALL_E]);
+        }
+    if (!yper)
+        for (int j = 1; j <= nx; j++) {
+            FOLD(j, 0, j, 1, p->bc_value[WALL_S]);
+            FOLD(j, ny + 1, j, ny, p->bc_value[WALL_N]);
+        }
+#undef FOLD
+    /* cells: P = a_bp f + b_bp feq(phi) (Eq. 2.21), T = a_tp f + b_tp feq(phi) (Eq. 2.13), phi = sum f */
+    for (int k = 0; k < ny; k++)
+        for (int j = 0; j < nx; j++) {
+            const size_t c = (size_t)k * nx + j;
+            double dfe[Q], acc = phib_extra[c];
+            oracle_equilibrium_deriv(p, w->phi[c], dfe);
+            for (int i = 0; i < Q; i++) {
+                const double pb = PB(i, k + 1, j + 1), tb = mu[i * n + c];
+                acc += (b_bp * pb + b_tp * tb) * dfe[i];
+                djdl += pb * (da_bp * f_in[i * n + c] + db_bp * w->feq[i * n + c]) +
+                        tb * (da_tp * f_in[i * n + c] + db_tp * w->feq[i * n + c]);
+            }
+            for (int i = 0; i < Q; i++) lam[i * n + c] = a_bp * PB(i, k + 1, j + 1) + a_tp * mu[i * n + c] + acc;
+        }
+#undef PB
+    if (dj_dalpha) *dj_dalpha += djdl / (p->c * p->c / 3.0);
+    free(phib_extra);
+    free(Pb);
+    ws_free(w);
+    return 0;
 }
