@@ -575,13 +575,14 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
     int s = 0, issued = min(S, R), consumed = 0;
     uint32_t ph = 0;
 
-    // ftilde of row r for this lane, from stage `st` of the ring (or global memory for wrap columns)
-    auto read_row = [&](int r, int st, V9& F) {
+    auto load_row = [&](int r, V9& F) -> bool {
+        const bool ok = mbar_wait_bounded(&bars[s], ph, 2000000000ull);
+        if (__any_sync(0xffffffffu, !ok)) return false;
         float ft[Q];
         if (from_smem) {
-            const float* sp = reinterpret_cast<const float*>(stages + size_t(st) * L::STAGE_BYTES) + soff;
+            const float* st = reinterpret_cast<const float*>(stages + size_t(s) * L::STAGE_BYTES) + soff;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) ft[i] = sp[i * L::BOXW];
+            for (int i = 0; i < Q; ++i) ft[i] = st[i * L::BOXW];
         } else if (role != ROLE_OUT) {
             const long long base = (long long)src_row(r) * a.pitch + scol;
 #pragma unroll
@@ -593,31 +594,21 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
 #pragma unroll
         for (int q = 0; q < 4; ++q) F.p[q] = f2(ft[PA(q)], ft[PB(q)]);
         F.z = ft[0];
-    };
-    // wait for the next row; the stage of the row two back (last read by the previous
-    // iteration's cell update) is refilled with the row S ahead of it
-    int s_prev = 0;
-    auto load_row = [&](int r, V9& F) -> bool {
-        const bool ok = mbar_wait_bounded(&bars[s], ph, 2000000000ull);
-        if (__any_sync(0xffffffffu, !ok)) return false;
-        read_row(r, s, F);
-        if (consumed >= 2 && issued < R) {
-            const int so = s >= 2 ? s - 2 : s + S - 2;
-            __syncwarp();
+        __syncwarp();
+        if (issued < R) {
             if (lane == 0) {
                 fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&bars[so], uint32_t(L::BOX_BYTES));
-                tma_load_3d(stages + size_t(so) * L::STAGE_BYTES, tin, &bars[so], xs, src_row(y0 - 1 + issued), 0);
+                mbar_arrive_expect_tx(&bars[s], uint32_t(L::BOX_BYTES));
+                tma_load_3d(stages + size_t(s) * L::STAGE_BYTES, tin, &bars[s], xs, src_row(r + S), 0);
             }
             ++issued;
         }
-        s_prev = s;
         if (++s == S) { s = 0; ph ^= 1u; }
         ++consumed;
         return true;
     };
-    // P = fbar^+ (Eq. 2.21, b_bp folded into the polynomials)
-    auto cell_row = [&](int r, const V9& F, V9& P) {
+    // P (Eq. 2.21, b_bp folded into the polynomials) and Fp = P + (P - ft)/3 (Eq. 2.23)
+    auto cell_row = [&](int r, const V9& F, V9& P, V9& Fp) {
         const float phi = vsum(F);
         const F2 phi2 = f2(phi);
         F2 hs = f2(0.f);
@@ -628,6 +619,9 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
             hs = hs + h;
         }
         P.z = fmaf(k.a_bp, F.z, fmaf(k.b_bp, phi, -(hs.v.x + hs.v.y)));  // rest velocity via the zeroth moment
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Fp.p[q] = fma2(F2{k.third2}, P.p[q] - F.p[q], P.p[q]);
+        Fp.z = fmaf(k.third, P.z - F.z, P.z);
         const bool ghost_row = !a.yper && (r < 0 || r >= ny);
         if (ghost_row || ghost_col) {
             const float bv = ghost_col ? bvx : (r < 0 ? k.s.bcv[2] : k.s.bcv[3]);
@@ -673,8 +667,9 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
         for (int q = 0; q < 4; ++q)
             if (QY(q) != 0) fy[q] = fma2(F2{k.a_f2}, fb.p[q], hf2(k, q, phib));
     };
-    auto x_update = [&](int kr, int st_kr, const CellM<float>& cyk, const V9& P0, const V9& P, const F2 (&Pm)[4],
-                        const F2 (&fN)[4], const F2 (&fS)[4]) {
+    auto x_update = [&](int kr, const V9& P0, const V9& P, const F2 (&Pm)[4], const V9& Fp0, const F2 (&fN)[4],
+                        const F2 (&fS)[4]) {
+        const CellM<float> cyk = a.cy[kr + 1];
         const F2 igy = f2((ghost_col || (EDGE && role == ROLE_OUT)) ? 0.f : cyk.ig);
         V9 fb;
 #pragma unroll
@@ -697,12 +692,7 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
                 dW[q] = fe - shfl_up2(fe);  // east minus west (lane - 1's east face)
             }
         const F2 ryp = sgn2(0.f, -cyk.r, 1);
-        // Fp = ftilde^+ = P + (P - ftilde)/3 (Eq. 2.23), ftilde re-read from this row's stage
-        V9 v, F0;
-        read_row(kr, st_kr, F0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) v.p[q] = fma2(F2{k.third2}, P0.p[q] - F0.p[q], P0.p[q]);
-        v.z = fmaf(k.third, P0.z - F0.z, P0.z);
+        V9 v = Fp0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             if (QX(q) != 0) v.p[q] = fma2(QX(q) > 0 ? rxp : rxn, dW[q], v.p[q]);
@@ -720,7 +710,7 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
     };
 
     bool failed = false;
-    V9 F, P0, Ly;
+    V9 F, P0, Fp0, Ly;
     F2 Pm[4], fS[4], Gx[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) { Pm[q] = fS[q] = Gx[q] = f2(0.f); }
@@ -728,7 +718,7 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
     // face metrics: fyB = face below the current row, fyA = face above it (index f+1 for face f)
     FaceM<float> fyB = a.fy[y0], fyA = a.fy[y0 + 1];
     if (!failed) {
-        cell_row(y0 - 1, F, P0);
+        cell_row(y0 - 1, F, P0, Fp0);
         grad_x(y0 - 1, P0, Gx);
         lower_half(fyA, P0, Gx, Ly);
 #pragma unroll
@@ -738,35 +728,29 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
     if (!failed) {
         fyB = fyA;
         fyA = a.fy[y0 + 2];
-        cell_row(y0, F, P0);
+        cell_row(y0, F, P0, Fp0);
         grad_x(y0, P0, Gx);
         y_face(fyB, P0, Gx, Ly, fS);
         lower_half(fyA, P0, Gx, Ly);
-        // per-row metrics are loaded one row ahead, off the critical path
-        FaceM<float> fyNext = a.fy[y0 + 3];
-        CellM<float> cyNext = a.cy[y0 + 1];
-#pragma unroll 1
+#pragma unroll 2
         for (int r = y0 + 1; r <= y1; ++r) {
-            V9 P;
+            V9 P, Fp;
             F2 fN[4];
-            const int st_kr = s_prev;  // stage holding row r - 1
             if (!load_row(r, F)) { failed = true; break; }
             fyB = fyA;
-            fyA = fyNext;
-            const CellM<float> cyk = cyNext;
-            fyNext = a.fy[min(r + 3, ny + 2)];
-            cyNext = a.cy[min(r + 1, ny + 1)];
-            cell_row(r, F, P);
+            fyA = a.fy[r + 2];
+            cell_row(r, F, P, Fp);
             grad_x(r, P, Gx);
             y_face(fyB, P, Gx, Ly, fN);
             lower_half(fyA, P, Gx, Ly);
-            x_update(r - 1, st_kr, cyk, P0, P, Pm, fN, fS);
+            x_update(r - 1, P0, P, Pm, Fp0, fN, fS);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 Pm[q] = P0.p[q];
                 fS[q] = fN[q];
             }
             P0 = P;
+            Fp0 = Fp;
         }
     }
     if (failed && lane == 0) {
