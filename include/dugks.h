@@ -174,6 +174,31 @@ dugks_status dugks_sync(dugks_ctx *ctx);
 /* Sizes and launch shape of a context. */
 dugks_status dugks_info(const dugks_ctx *ctx, dugks_info_t *out);
 
+/* ---- adjoint (gradients) -------------------------------------------------
+ * Discrete adjoint of the step of Section 2 (reverse mode of Eqs. 2.9,
+ * 2.12, 2.13, 2.19-2.22, 2.26 and of the mirrored NEE ghosts), for
+ * gradients of a misfit J(phi^N) with respect to phi^0 and alpha (alpha
+ * enters through lambda = alpha / c_s^2, Section 3).
+ *
+ * dugks_adjoint_step: lam = (d ftilde^{n+1} / d ftilde^n)^T mu at the forward
+ * state f = ftilde^n, and *dj_dalpha_dev += mu . d ftilde^{n+1} / d alpha.
+ * f_dev, mu_dev, lam_dev: device, [9][ny][nx] contiguous, precision's type
+ * (lam_dev must not alias f_dev or mu_dev); dj_dalpha_dev: device double,
+ * accumulated in a fixed order (deterministic).  Asynchronous. */
+dugks_status dugks_adjoint_step(dugks_ctx *ctx, const void *f_dev, const void *mu_dev, void *lam_dev,
+                                double *dj_dalpha_dev);
+
+/* Gradient of J through nsteps steps from phi0: given grad_phiN = dJ/dphi^N
+ * (device, [ny][nx]), writes dJ/dphi^0 into grad_phi0_dev (device [ny][nx])
+ * and dJ/dalpha into *grad_alpha_out (host; may be NULL).  Runs the forward
+ * sweep keeping one state every checkpoint_every steps, then for each segment
+ * from the last recomputes its states and steps the adjoint back through it
+ * (memory: ceil(nsteps/K) + K + 2 states of 9 nx ny elements, allocated for
+ * the call and freed).  Synchronises the stream.  The context's own state is
+ * left at an intermediate step: initialise it again before stepping. */
+dugks_status dugks_adjoint(dugks_ctx *ctx, const void *phi0_dev, long long nsteps, int checkpoint_every,
+                           const void *grad_phiN_dev, void *grad_phi0_dev, double *grad_alpha_out);
+
 /* ---- allocation-free variant -------------------------------------------
  * No counterpart in the paper: a convenience for callers that cannot
  * allocate device memory, for example a host application whose memory pool

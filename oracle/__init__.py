@@ -171,22 +171,32 @@ class Oracle:
             raise RuntimeError(f"oracle_adjoint_step failed ({rc})")
         return lam, da.value
 
-    def gradient(self, phi0: np.ndarray, nsteps: int, dj_dphiN, threads: int = 0):
-        """Reverse-mode gradient of J(phi^N) with respect to phi0 and alpha, storing
-        every state: dj_dphiN(phi^N) returns dJ/dphi^N; returns (J-independent)
-        (grad_phi0, dJ/dalpha, phi^N)."""
-        states = [self.init(phi0)]
-        for _ in range(nsteps):
-            states.append(self.step(states[-1], threads))
-        phiN = self.phi(states[-1])
+    def gradient(self, phi0: np.ndarray, nsteps: int, dj_dphiN, threads: int = 0, checkpoint_every: int = 0):
+        """Reverse-mode gradient of J(phi^N) with respect to phi0 and alpha.
+        dj_dphiN(phi^N) returns dJ/dphi^N.  With checkpoint_every = K > 0 only
+        every K-th state is kept and each segment is recomputed.  Returns
+        (dJ/dphi0, dJ/dalpha, phi^N)."""
+        K = nsteps if checkpoint_every <= 0 else checkpoint_every
+        K = max(1, min(K, max(nsteps, 1)))
+        ckpt = [self.init(phi0)]
+        for s in range(0, nsteps, K):
+            f = ckpt[-1]
+            f = self.run(f, min(K, nsteps - s), threads)
+            ckpt.append(f)
+        phiN = self.phi(ckpt[-1])
         g = np.asarray(dj_dphiN(phiN), dtype=np.float64)
         lam = np.broadcast_to(g, (Q,) + g.shape).copy()   # phi = sum_i f_i
         dalpha = 0.0
-        for n in range(nsteps - 1, -1, -1):
-            lam, da = self.adjoint_step(states[n], lam)
-            dalpha += da
+        for si in range(len(ckpt) - 2, -1, -1):
+            ns = min(K, nsteps - si * K)
+            states = [ckpt[si]]
+            for _ in range(ns - 1):
+                states.append(self.step(states[-1], threads))
+            for n in range(ns - 1, -1, -1):
+                lam, da = self.adjoint_step(states[n], lam)
+                dalpha += da
         # f^0 = feq(phi0): dJ/dphi0 = sum_i feq_i'(phi0) lam_i
-        gphi = np.zeros_like(phi0, dtype=np.float64)
+        gphi = np.zeros(phi0.shape, dtype=np.float64)
         for k in range(self.ny):
             for j in range(self.nx):
                 gphi[k, j] = float(self.equilibrium_deriv(phi0[k, j]) @ lam[:, k, j])

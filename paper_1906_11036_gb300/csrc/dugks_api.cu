@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/dugks.h"
+#include "dugks_adjoint.cuh"
 #include "dugks_kernels.cuh"
 
 using namespace dugks;
@@ -62,6 +63,11 @@ struct dugks_ctx {
     CUtensorMap tmap[2];
     int nt = 32, stages = 8, seg_rows = 0, nstrips = 0, nseg = 0, occupancy = 0;
     long long steps_done = 0;
+    // adjoint work buffers (allocated on first use)
+    void* adj_ax = nullptr;
+    void* adj_ay = nullptr;
+    double* adj_partial = nullptr;
+    double* adj_dalpha = nullptr;
     std::string last_error;
 };
 
@@ -331,7 +337,9 @@ void free_ctx(dugks_ctx* ctx) {
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(ctx->device);
-    for (void* p : {ctx->buf[0], ctx->buf[1], ctx->fxm, ctx->fym, ctx->cxm, ctx->cym}) if (p) cudaFree(p);
+    for (void* p : {ctx->buf[0], ctx->buf[1], ctx->fxm, ctx->fym, ctx->cxm, ctx->cym, ctx->adj_ax, ctx->adj_ay,
+                    static_cast<void*>(ctx->adj_partial), static_cast<void*>(ctx->adj_dalpha)})
+        if (p) cudaFree(p);
     for (void* p : {static_cast<void*>(ctx->dxv), static_cast<void*>(ctx->dyv), static_cast<void*>(ctx->staging),
                     static_cast<void*>(ctx->partial), static_cast<void*>(ctx->mass_dev),
                     static_cast<void*>(ctx->err_dev)})
@@ -351,6 +359,88 @@ struct DeviceGuard {
         if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
     }
 };
+
+template <typename T, int NC>
+AdjConsts<T, NC> make_adj_consts(const dugks_ctx* ctx) {
+    AdjConsts<T, NC> ka;
+    for (int i = 0; i < Q; ++i)
+        for (int m = 0; m < NC; ++m) ka.dfeq[i][m] = T(m + 1 < NC_LARGE ? double(m + 1) * ctx->feq_coef[i][m + 1] : 0.0);
+    const double lam = ctx->lambda, dt = ctx->dt, h = 0.5 * dt;
+    const double d1 = 2.0 * lam + dt, d2 = 2.0 * lam + h;
+    ka.a_bp = T(ctx->a_bp); ka.b_bp = T(ctx->b_bp);
+    ka.a_tp = T(ctx->a_tp); ka.b_tp = T(ctx->b_tp);
+    ka.a_f = T(ctx->a_f); ka.b_f = T(ctx->b_f);
+    ka.da_bp = T(2.0 * (dt + h) / (d1 * d1)); ka.db_bp = T(-6.0 * h / (d1 * d1));  // d/dlambda of Eq. 2.21 weights
+    ka.da_tp = T(4.0 * dt / (d1 * d1)); ka.db_tp = T(-4.0 * dt / (d1 * d1));        // Eq. 2.13
+    ka.da_f = T(2.0 * h / (d2 * d2)); ka.db_f = T(-2.0 * h / (d2 * d2));            // Eq. 2.22
+    return ka;
+}
+
+int adj_face_blocks(const dugks_ctx* ctx) {
+    const long long nf = (long long)(ctx->nx + 1) * ctx->ny + (long long)ctx->nx * (ctx->ny + 1);
+    return int((nf + 127) / 128);
+}
+int adj_cell_blocks(const dugks_ctx* ctx) { return int(((long long)ctx->nx * ctx->ny + 127) / 128); }
+
+dugks_status adj_alloc(dugks_ctx* ctx) {
+    if (ctx->adj_ax) return DUGKS_OK;
+    cudaError_t e;
+    const size_t nxf = size_t(ctx->nx + 1) * ctx->ny, nyf = size_t(ctx->nx) * (ctx->ny + 1);
+    if ((e = cudaMalloc(&ctx->adj_ax, Q * nxf * ctx->elem)) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->adj_ay, Q * nyf * ctx->elem)) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->adj_partial, sizeof(double) * size_t(adj_face_blocks(ctx) + adj_cell_blocks(ctx)))) !=
+            cudaSuccess ||
+        (e = cudaMalloc(&ctx->adj_dalpha, sizeof(double))) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaMalloc(adjoint buffers)");
+    return DUGKS_OK;
+}
+
+template <typename T, int NC>
+cudaError_t launch_adjoint_step(dugks_ctx* ctx, const void* f, const void* mu, void* lam, double* dj_dalpha) {
+    StepArgs<T, NC> a = make_args<T, NC>(ctx, 0);
+    a.fin = static_cast<const T*>(f);  // the adjoint reads contiguous [Q][ny][nx] states
+    a.pitch = ctx->nx;
+    a.plane = (long long)ctx->nx * ctx->ny;
+    const Consts<T, NC> k = make_consts<T, NC>(ctx);
+    const AdjConsts<T, NC> ka = make_adj_consts<T, NC>(ctx);
+    AdjArgs<T> g;
+    g.f = static_cast<const T*>(f);
+    g.mu = static_cast<const T*>(mu);
+    g.lam = static_cast<T*>(lam);
+    g.Ax = static_cast<T*>(ctx->adj_ax);
+    g.Ay = static_cast<T*>(ctx->adj_ay);
+    g.partial = ctx->adj_partial;
+    const int fb = adj_face_blocks(ctx), cb = adj_cell_blocks(ctx);
+    adj_face_kernel<T, NC><<<fb, 128, 0, ctx->stream>>>(a, k, ka, g);
+    adj_cell_kernel<T, NC><<<cb, 128, 0, ctx->stream>>>(a, k, ka, g, fb);
+    adj_sum_kernel<<<1, 256, 0, ctx->stream>>>(ctx->adj_partial, fb + cb, 3.0 / (ctx->c * ctx->c), dj_dalpha);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_step_any(dugks_ctx* ctx, const void* f, const void* mu, void* lam, double* dj_dalpha) {
+    if (ctx->precision == 32) {
+        switch (ctx->nc) {
+            case 3: return launch_adjoint_step<float, 3>(ctx, f, mu, lam, dj_dalpha);
+            case 4: return launch_adjoint_step<float, 4>(ctx, f, mu, lam, dj_dalpha);
+            default: return launch_adjoint_step<float, NC_LARGE>(ctx, f, mu, lam, dj_dalpha);
+        }
+    }
+    switch (ctx->nc) {
+        case 3: return launch_adjoint_step<double, 3>(ctx, f, mu, lam, dj_dalpha);
+        case 4: return launch_adjoint_step<double, 4>(ctx, f, mu, lam, dj_dalpha);
+        default: return launch_adjoint_step<double, NC_LARGE>(ctx, f, mu, lam, dj_dalpha);
+    }
+}
+
+template <typename T>
+cudaError_t launch_init_adjoint(dugks_ctx* ctx, const void* phi0, const void* lam, void* gphi0) {
+    const long long n = (long long)ctx->nx * ctx->ny;
+    const int blocks = int(std::min<long long>((n + 255) / 256, 65535));
+    init_adjoint_kernel<T, NC_LARGE><<<blocks, 256, 0, ctx->stream>>>(
+        static_cast<const T*>(phi0), static_cast<const T*>(lam), static_cast<T*>(gphi0), n,
+        make_adj_consts<T, NC_LARGE>(ctx));
+    return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -675,6 +765,94 @@ dugks_status dugks_info(const dugks_ctx* ctx, dugks_info_t* out) {
     out->grid_blocks = ctx->kernel == DUGKS_KERNEL_NAIVE ? ((ctx->nx + 127) / 128) * std::min(ctx->ny, 65535)
                                                          : ctx->nstrips * ctx->nseg;
     out->state_bytes = (long long)Q * ctx->plane * (long long)ctx->elem;
+    return DUGKS_OK;
+}
+
+dugks_status dugks_adjoint_step(dugks_ctx* ctx, const void* f_dev, const void* mu_dev, void* lam_dev,
+                                double* dj_dalpha_dev) {
+    if (!ctx || !f_dev || !mu_dev || !lam_dev || !dj_dalpha_dev) return DUGKS_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    dugks_status st = adj_alloc(ctx);
+    if (st != DUGKS_OK) return st;
+    CK(launch_adjoint_step_any(ctx, f_dev, mu_dev, lam_dev, dj_dalpha_dev));
+    return DUGKS_OK;
+}
+
+dugks_status dugks_adjoint(dugks_ctx* ctx, const void* phi0_dev, long long nsteps, int checkpoint_every,
+                           const void* grad_phiN_dev, void* grad_phi0_dev, double* grad_alpha_out) {
+    if (!ctx || !phi0_dev || !grad_phiN_dev || !grad_phi0_dev || nsteps < 0 || checkpoint_every < 1)
+        return DUGKS_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    dugks_status st = adj_alloc(ctx);
+    if (st != DUGKS_OK) return st;
+    const long long K = std::min<long long>(checkpoint_every, std::max<long long>(nsteps, 1));
+    const long long nseg = nsteps == 0 ? 0 : (nsteps + K - 1) / K;
+    const size_t sbytes = size_t(Q) * ctx->nx * ctx->ny * ctx->elem;
+    std::vector<void*> bufs;
+    auto release = [&]() {
+        for (void* p : bufs) cudaFree(p);
+        bufs.clear();
+    };
+    auto take = [&](void** p) -> bool {
+        if (cudaMalloc(p, sbytes) != cudaSuccess) return false;
+        bufs.push_back(*p);
+        return true;
+    };
+    std::vector<void*> ckpt(size_t(nseg), nullptr), seg(size_t(K), nullptr);
+    void* lam[2] = {nullptr, nullptr};
+    for (auto& p : ckpt)
+        if (!take(&p)) { release(); ctx->last_error = "checkpoint allocation failed"; return DUGKS_ERR_NOMEM; }
+    for (auto& p : seg)
+        if (!take(&p)) { release(); ctx->last_error = "segment allocation failed"; return DUGKS_ERR_NOMEM; }
+    if (!take(&lam[0]) || !take(&lam[1])) { release(); ctx->last_error = "adjoint allocation failed"; return DUGKS_ERR_NOMEM; }
+    auto fail = [&](cudaError_t e, const char* what) {
+        dugks_status s = cuda_fail(ctx, e, what);
+        cudaStreamSynchronize(ctx->stream);
+        release();
+        return s;
+    };
+    cudaError_t e;
+    // forward sweep, keeping one state per segment
+    if ((st = dugks_init_phi(ctx, phi0_dev)) != DUGKS_OK) { release(); return st; }
+    for (long long s = 0; s < nseg; ++s) {
+        if ((st = dugks_save_state(ctx, ckpt[s])) != DUGKS_OK) { release(); return st; }
+        if ((st = dugks_step(ctx, std::min(K, nsteps - s * K))) != DUGKS_OK) { release(); return st; }
+    }
+    if ((e = cudaMemsetAsync(ctx->adj_dalpha, 0, sizeof(double), ctx->stream)) != cudaSuccess)
+        return fail(e, "cudaMemsetAsync");
+    const long long n = (long long)ctx->nx * ctx->ny;
+    const int blocks = int(std::min<long long>((n + 255) / 256, 65535));
+    if (ctx->precision == 32)
+        broadcast_phi_adjoint<float><<<blocks, 256, 0, ctx->stream>>>(static_cast<const float*>(grad_phiN_dev),
+                                                                     static_cast<float*>(lam[0]), n);
+    else
+        broadcast_phi_adjoint<double><<<blocks, 256, 0, ctx->stream>>>(static_cast<const double*>(grad_phiN_dev),
+                                                                       static_cast<double*>(lam[0]), n);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "broadcast_phi_adjoint");
+    int cur = 0;
+    // reverse sweep: recompute each segment from its checkpoint, then step the adjoint back through it
+    for (long long s = nseg - 1; s >= 0; --s) {
+        const long long ns = std::min(K, nsteps - s * K);
+        if ((st = dugks_load_state(ctx, ckpt[s])) != DUGKS_OK) { release(); return st; }
+        for (long long q = 0; q < ns; ++q) {
+            if ((st = dugks_save_state(ctx, seg[q])) != DUGKS_OK) { release(); return st; }
+            if (q + 1 < ns && (st = dugks_step(ctx, 1)) != DUGKS_OK) { release(); return st; }
+        }
+        for (long long q = ns - 1; q >= 0; --q) {
+            if ((e = launch_adjoint_step_any(ctx, seg[q], lam[cur], lam[1 - cur], ctx->adj_dalpha)) != cudaSuccess)
+                return fail(e, "adjoint step");
+            cur ^= 1;
+        }
+    }
+    e = ctx->precision == 32 ? launch_init_adjoint<float>(ctx, phi0_dev, lam[cur], grad_phi0_dev)
+                             : launch_init_adjoint<double>(ctx, phi0_dev, lam[cur], grad_phi0_dev);
+    if (e != cudaSuccess) return fail(e, "init adjoint");
+    double da = 0.0;
+    if ((e = cudaMemcpyAsync(&da, ctx->adj_dalpha, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+        return fail(e, "cudaMemcpyAsync");
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return fail(e, "cudaStreamSynchronize");
+    release();
+    if (grad_alpha_out) *grad_alpha_out = da;
     return DUGKS_OK;
 }
 

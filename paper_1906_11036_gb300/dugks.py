@@ -79,13 +79,17 @@ def library():
         L.dugks_set_stream.argtypes = [vp, vp]
         L.dugks_sync.argtypes = [vp]
         L.dugks_info.argtypes = [vp, P(Info)]
+        L.dugks_adjoint_step.argtypes = [vp, vp, vp, vp, vp]
+        L.dugks_adjoint.argtypes = [vp, vp, ctypes.c_longlong, ctypes.c_int, vp, vp, P(ctypes.c_double)]
+        L.dugks_phi_mass_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp]
         L.dugks_status_string.argtypes = [ctypes.c_int]
         L.dugks_status_string.restype = ctypes.c_char_p
         L.dugks_last_error.argtypes = [vp]
         L.dugks_last_error.restype = ctypes.c_char_p
         for name in ("dugks_check_config", "dugks_create", "dugks_destroy", "dugks_init_phi", "dugks_init_phi_host",
                      "dugks_step", "dugks_get_phi", "dugks_get_phi_host", "dugks_save_state", "dugks_load_state",
-                     "dugks_set_stream", "dugks_sync", "dugks_info"):
+                     "dugks_set_stream", "dugks_sync", "dugks_info", "dugks_adjoint_step", "dugks_adjoint",
+                     "dugks_phi_mass_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -238,7 +242,69 @@ class Solver:
     def sync(self):
         self._check(self.L.dugks_sync(self.h), "dugks_sync")
 
+    def adjoint_step(self, f, mu, dj_dalpha=None):
+        """lam = (d f^{n+1}/d f^n)^T mu at state f (CUDA tensors [9, ny, nx]); the
+        explicit alpha-derivative is accumulated into dj_dalpha (a CUDA float64
+        tensor of one element, created if None).  Returns (lam, dj_dalpha)."""
+        t = self.torch
+        f = f.to(device=self.device, dtype=self.dtype).contiguous()
+        mu = mu.to(device=self.device, dtype=self.dtype).contiguous()
+        lam = t.empty_like(f)
+        if dj_dalpha is None:
+            dj_dalpha = t.zeros(1, dtype=t.float64, device=self.device)
+        self._check(self.L.dugks_adjoint_step(self.h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(mu.data_ptr()),
+                                              ctypes.c_void_p(lam.data_ptr()), ctypes.c_void_p(dj_dalpha.data_ptr())),
+                    "dugks_adjoint_step")
+        return lam, dj_dalpha
+
+    def gradient(self, phi0, nsteps: int, grad_phiN, checkpoint_every: int = 20):
+        """(dJ/dphi0, dJ/dalpha) through nsteps steps, given dJ/dphi^N (checkpointed
+        reverse sweep in the library).  Leaves the solver's state at an
+        intermediate step."""
+        t = self.torch
+        phi0 = phi0.to(device=self.device, dtype=self.dtype).contiguous()
+        g = grad_phiN.to(device=self.device, dtype=self.dtype).contiguous()
+        out = t.empty_like(phi0)
+        da = ctypes.c_double(0.0)
+        self._check(self.L.dugks_adjoint(self.h, ctypes.c_void_p(phi0.data_ptr()), int(nsteps), int(checkpoint_every),
+                                         ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                         ctypes.byref(da)), "dugks_adjoint")
+        return out, da.value
+
     def info(self) -> dict:
         i = Info()
         self._check(self.L.dugks_info(self.h, ctypes.byref(i)), "dugks_info")
         return {f: getattr(i, f) for f, _ in Info._fields_}
+
+
+def run_fn():
+    """A torch.autograd.Function over the whole run: phiN = run(phi0, alpha).
+
+    forward(phi0, alpha, solver, nsteps, checkpoint_every) advances the solver
+    (created with that alpha) from phi0; backward runs the library's
+    checkpointed adjoint and returns dJ/dphi0 and dJ/dalpha.  alpha is a
+    one-element tensor that must equal the solver's diffusion coefficient;
+    it is an input only so that its gradient can be returned.
+    """
+    import torch
+
+    class DugksRun(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, phi0, alpha, solver, nsteps, checkpoint_every):
+            if abs(float(alpha) - float(solver.problem.alpha)) > 1e-12 * abs(float(solver.problem.alpha)):
+                raise ValueError("alpha does not match the solver's diffusion coefficient")
+            solver.init_phi(phi0.detach())
+            solver.step(nsteps)
+            ctx.solver, ctx.nsteps, ctx.k = solver, int(nsteps), int(checkpoint_every)
+            ctx.save_for_backward(phi0.detach())
+            return solver.get_phi().to(phi0.dtype)
+
+        @staticmethod
+        def backward(ctx, grad_phiN):
+            (phi0,) = ctx.saved_tensors
+            gphi0, galpha = ctx.solver.gradient(phi0, ctx.nsteps, grad_phiN, ctx.k)
+            return (gphi0.to(phi0.dtype), torch.tensor([galpha], dtype=torch.float64, device=phi0.device),
+                    None, None, None)
+
+    return DugksRun
+

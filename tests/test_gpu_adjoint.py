@@ -1,0 +1,159 @@
+"""GPU adjoint (dugks_adjoint_step / dugks_adjoint, through the C ABI) against
+the FP64 oracle's adjoint, which test_oracle_adjoint.py pins to central
+finite differences.
+
+Tolerances: FP64 GPU 1e-11 relative (rounding order only); FP32 GPU 1e-4
+relative on the gradient (the FP64 accumulation of dJ/dalpha keeps alpha's
+error at FP32 rounding of the summands).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import Oracle  # noqa: E402
+from paper_1906_11036_gb300 import inputs as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def _solver(p, prec):
+    from paper_1906_11036_gb300.dugks import Solver
+
+    return Solver(p, precision=prec)
+
+
+def _mixed(xwall, ywall, nx, ny):
+    xf = I.tanh_faces(nx, 1.5) if xwall else I.uniform_faces(nx)
+    yf = I.tanh_faces(ny, 1.5) if ywall else I.uniform_faces(ny)
+    bc = ((I.DIRICHLET,) * 2 if xwall else (I.PERIODIC,) * 2) + ((I.DIRICHLET,) * 2 if ywall else (I.PERIODIC,) * 2)
+    return I.Problem(xf=xf, yf=yf, bc=bc, bc_value=(1.2, 0.6, 0.9, 0.7), c=2.0, u=(0.3, -0.2),
+                     b=(0.0, 0.0, 0.5), alpha=0.02, d=(0.0, 1.0, 0.5), dt=I.cfl_dt(xf, yf, 2.0, 0.4))
+
+
+CASES = {
+    "burgers_37x23": lambda: I.burgers(37, 23)[0],
+    "nonuniform_33x29": lambda: I.nonuniform(33, 29)[0],
+    "xwall_21x17": lambda: _mixed(True, False, 21, 17),
+    "ywall_19x22": lambda: _mixed(False, True, 19, 22),
+    "czero_16x16": lambda: I.burgers(16, 16)[0].with_(c_zero=True),
+    "poly_20x13": lambda: I.burgers(20, 13)[0].with_(b=(0.05, 0.3, 0.2, 0.1), d=(0.1, 0.6, 0.2, 0.05)),
+    "tiny_3x2": lambda: I.burgers(3, 2)[0],
+    "tiny_walls_2x3": lambda: I.nonuniform(2, 3)[0],
+}
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("name", list(CASES))
+def test_adjoint_step_matches_oracle(name, prec):
+    p = CASES[name]()
+    rng = np.random.default_rng(len(name))
+    o = Oracle(p)
+    f = o.init(1.0 + 0.2 * rng.standard_normal((p.ny, p.nx))) + 0.01 * rng.standard_normal((9, p.ny, p.nx))
+    mu = rng.standard_normal(f.shape)
+    lam_ref, da_ref = o.adjoint_step(f, mu)
+    s = _solver(p, prec)
+    dt = s.dtype
+    lam, da = s.adjoint_step(torch.tensor(f, dtype=dt, device="cuda"), torch.tensor(mu, dtype=dt, device="cuda"))
+    lam = lam.double().cpu().numpy()
+    da = float(da.item())
+    s.close()
+    tol = 1e-11 if prec == 64 else 2e-5
+    assert _rel(lam, lam_ref) <= tol, _rel(lam, lam_ref)
+    assert abs(da - da_ref) <= tol * 10 * max(abs(da_ref), 1e-12)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_checkpointed_gradient_matches_oracle(prec):
+    p, phi0 = I.burgers(48, 40, steps=60)
+    xc, yc = p.centres()
+    area = np.outer(np.diff(p.yf), np.diff(p.xf))
+    target = I.burgers_phi0(xc, yc, seed=5)
+    gref, daref, phiN_ref = Oracle(p).gradient(phi0, p.steps, lambda phiN: area * (phiN - target), threads=8,
+                                               checkpoint_every=20)
+    s = _solver(p, prec)
+    dt = s.dtype
+    s.init_phi(torch.tensor(phi0, dtype=dt, device="cuda"))
+    s.step(p.steps)
+    phiN = s.get_phi().double().cpu().numpy()
+    gN = torch.tensor(area * (phiN - target), dtype=dt, device="cuda")
+    g0, da = s.gradient(torch.tensor(phi0, dtype=dt, device="cuda"), p.steps, gN, checkpoint_every=20)
+    s.close()
+    tol = 1e-10 if prec == 64 else 1e-4
+    assert _rel(g0.double().cpu().numpy(), gref) <= tol
+    assert abs(da - daref) <= tol * abs(daref)
+
+
+def test_autograd_function_and_checkpoint_length_invariance():
+    """torch.autograd through the run; the gradient does not depend on the
+    checkpoint spacing (recomputation is exact)."""
+    from paper_1906_11036_gb300.dugks import Solver, run_fn
+
+    p, phi0 = I.nonuniform(40, 36, steps=25)
+    xc, yc = p.centres()
+    target = torch.tensor(I.smooth_phi0(xc, yc, seed=9), dtype=torch.float64, device="cuda")
+    area = torch.tensor(np.outer(np.diff(p.yf), np.diff(p.xf)), device="cuda")
+    s = Solver(p, precision=64)
+    Run = run_fn()
+    grads = []
+    for k in (1, 7, 25):
+        x = torch.tensor(phi0, dtype=torch.float64, device="cuda", requires_grad=True)
+        al = torch.tensor([p.alpha], dtype=torch.float64, device="cuda", requires_grad=True)
+        phiN = Run.apply(x, al, s, p.steps, k)
+        J = 0.5 * (area * (phiN - target) ** 2).sum()
+        J.backward()
+        grads.append((x.grad.cpu().numpy(), float(al.grad.item())))
+    s.close()
+    gref, daref, _ = Oracle(p).gradient(phi0, p.steps,
+                                        lambda phiN: area.cpu().numpy() * (phiN - target.cpu().numpy()))
+    for g, da in grads:
+        assert _rel(g, gref) <= 1e-10 and abs(da - daref) <= 1e-10 * abs(daref)
+
+
+def test_adjoint_workload_512_fp32_against_oracle_and_fd():
+    """The adjoint workload at full size: 512^2 periodic Burgers-type NCDE, 400
+    FP32 steps checkpointed every 20; gradient of the L2 misfit to a seeded
+    target w.r.t. phi0 and alpha, against the FP64 oracle's adjoint and, on two
+    random directions, against FP64 central differences (eps = 1e-4)."""
+    p, phi0 = I.burgers(512, steps=400)
+    xc, yc = p.centres()
+    area = np.outer(np.diff(p.yf), np.diff(p.xf))
+    target = I.burgers_phi0(xc, yc, seed=5)
+    s = _solver(p, 32)
+    s.init_phi(torch.tensor(phi0, dtype=torch.float32, device="cuda"))
+    s.step(p.steps)
+    phiN = s.get_phi().double().cpu().numpy()
+    gN = torch.tensor(area * (phiN - target), dtype=torch.float32, device="cuda")
+    g0, da = s.gradient(torch.tensor(phi0, dtype=torch.float32, device="cuda"), p.steps, gN, checkpoint_every=20)
+    s.close()
+    g0 = g0.double().cpu().numpy()
+    o = Oracle(p)
+    gref, daref, _ = o.gradient(phi0, p.steps, lambda ph: area * (ph - target), threads=16, checkpoint_every=20)
+    print(f"adjoint 512^2 x 400 FP32: rel-L2(grad phi0) {_rel(g0, gref):.2e}, rel(dJ/dalpha) {abs(da - daref) / abs(daref):.2e}")
+    assert _rel(g0, gref) <= 1e-4
+    assert abs(da - daref) <= 1e-4 * abs(daref)
+
+    def J(phi0_):
+        ph = o.phi(o.run(o.init(phi0_), p.steps, 16))
+        return 0.5 * float((area * (ph - target) ** 2).sum())
+
+    rng = np.random.default_rng(5)
+    for _ in range(2):
+        d = rng.standard_normal(phi0.shape)
+        d /= np.linalg.norm(d)
+        fd = (J(phi0 + 1e-4 * d) - J(phi0 - 1e-4 * d)) / 2e-4
+        assert abs(fd - float((g0 * d).sum())) <= 1e-3 * abs(fd)
