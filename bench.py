@@ -205,6 +205,55 @@ def run_reference(args):
     return 0
 
 
+def adjoint_ratio(args):
+    """Adjoint/step ratio on the adjoint workload (512^2 periodic Burgers-type
+    NCDE, FP32, 400 steps checkpointed every 20): time of one adjoint step
+    against one forward step, and of the whole checkpointed gradient against
+    the forward run."""
+    import torch
+
+    from paper_1906_11036_gb300 import inputs as I
+    from paper_1906_11036_gb300.dugks import Solver
+
+    p, phi0 = I.burgers(512, steps=400)
+    s = Solver(p, precision=32)
+    phi0_t = torch.tensor(phi0, dtype=torch.float32, device="cuda")
+    s.init_phi(phi0_t)
+    s.step(20)
+    f = s.save_state().clone()
+    mu = torch.randn_like(f)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record(s.stream)
+    s.step(200)
+    ev[1].record(s.stream)
+    lam, da = s.adjoint_step(f, mu)
+    for _ in range(3):
+        lam, da = s.adjoint_step(f, mu, da)
+    torch.cuda.synchronize()
+    ev[2].record(s.stream)
+    for _ in range(50):
+        lam, da = s.adjoint_step(f, mu, da)
+    ev[3].record(s.stream)
+    ev[3].synchronize()
+    t_fwd = ev[0].elapsed_time(ev[1]) / 200
+    t_adj = ev[2].elapsed_time(ev[3]) / 50
+    s.init_phi(phi0_t)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.step(p.steps)
+    phiN = s.get_phi()
+    torch.cuda.synchronize()
+    t_run = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    s.gradient(phi0_t, p.steps, phiN, checkpoint_every=20)
+    t_grad = time.perf_counter() - t0
+    s.close()
+    return {"workload": "burgers_512x512, 400 FP32 steps, checkpoint every 20",
+            "forward_ms_per_step": t_fwd, "adjoint_ms_per_step": t_adj, "adjoint_step_ratio": t_adj / t_fwd,
+            "forward_run_s": t_run, "gradient_s": t_grad, "gradient_to_forward_ratio": t_grad / t_run}
+
+
 def config_dict(args, p):
     return {"workload": f"{args.workload}_{p.nx}x{p.ny}", "nx": p.nx, "ny": p.ny, "velocity_set": "D2Q9",
             "mesh": "tanh-stretched k=2, Dirichlet walls" if args.workload == "nonuniform" else "uniform periodic",
@@ -222,6 +271,7 @@ def main():
     ap.add_argument("--substeps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -296,6 +346,7 @@ def main():
     barrier()
     t_e2e = time.perf_counter() - t0
     solver.close()
+    adjoint = adjoint_ratio(args) if (world == 1 and not args.no_adjoint) else None
 
     times = torch.tensor([t_dev, t_e2e], device="cuda", dtype=torch.float64)
     if world > 1:
@@ -325,6 +376,8 @@ def main():
         "clocks": clk.summary(),
         "launch": {"block": info["block_threads"], "grid": info["grid_blocks"]},
     }
+    if adjoint is not None:
+        line["adjoint"] = adjoint
     if world == 1 and not args.no_cpu_baseline:
         import oracle
 
