@@ -254,6 +254,73 @@ def adjoint_ratio(args):
             "forward_run_s": t_run, "gradient_s": t_grad, "gradient_to_forward_ratio": t_grad / t_run}
 
 
+def batched_vs_single(steps: int = 100):
+    """The batched workload (256 periodic instances, sides 64..512, seed 7):
+    cell-velocity updates/s of the batched persistent step (graph-replayed,
+    autotuned tile height) against stepping the same instances one by one with
+    the single-instance fused step, which gives bit-identical results."""
+    import torch
+
+    from paper_1906_11036_gb300 import inputs as I
+    from paper_1906_11036_gb300.dugks import BatchSolver, Solver
+
+    items = I.batched()
+    cells = sum(p.nx * p.ny for p, _ in items)
+    b = BatchSolver([p for p, _ in items])
+    for i, (_, phi0) in enumerate(items):
+        b.init_phi(i, phi0)
+    rows, _ = b.autotune(20)
+    b.step(50)
+    b.sync()
+    t0 = time.perf_counter()
+    b.step(steps)
+    b.sync()
+    t_batch = time.perf_counter() - t0
+    b.close()
+    stream = torch.cuda.Stream()
+    solvers = []
+    for p, phi0 in items:
+        s = Solver(p, precision=32, stream=stream)
+        with torch.cuda.stream(stream):
+            s.init_phi(torch.tensor(phi0, device="cuda"))
+        solvers.append(s)
+    for s in solvers:
+        s.step(5)
+    stream.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for s in solvers:
+            s.step(1)
+    stream.synchronize()
+    t_single = time.perf_counter() - t0
+    for s in solvers:
+        s.close()
+    v_b = cells * Q * steps / t_batch
+    v_s = cells * Q * steps / t_single
+    return {"workload": "256 periodic Burgers-type instances, sides 64-512 (seed 7), FP32",
+            "steps": steps, "cells": cells, "batched_value": v_b, "single_instance_loop_value": v_s,
+            "speedup": v_b / v_s, "tile_rows": rows, "unit": UNIT, "same_results": "bit-identical"}
+
+
+def max_over_ranks(times, world: int, device="cpu"):
+    """Element-wise maximum of per-rank timings over all ranks (the slowest
+    replica sets the job's time); identity for a single process."""
+    if world <= 1:
+        return list(times)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor(list(times), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def replica_value(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput of independent replicas: all ranks' units over the
+    slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def config_dict(args, p):
     return {"workload": f"{args.workload}_{p.nx}x{p.ny}", "nx": p.nx, "ny": p.ny, "velocity_set": "D2Q9",
             "mesh": "tanh-stretched k=2, Dirichlet walls" if args.workload == "nonuniform" else "uniform periodic",
@@ -272,6 +339,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -347,18 +415,16 @@ def main():
     t_e2e = time.perf_counter() - t0
     solver.close()
     adjoint = adjoint_ratio(args) if (world == 1 and not args.no_adjoint) else None
+    batched = batched_vs_single() if (world == 1 and not args.no_batched) else None
 
-    times = torch.tensor([t_dev, t_e2e], device="cuda", dtype=torch.float64)
-    if world > 1:
-        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
-    t_dev, t_e2e = times.tolist()
+    t_dev, t_e2e = max_over_ranks([t_dev, t_e2e], world, device="cuda")
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return 0
 
-    value = world * cvu_per_step * args.steps / t_dev
-    e2e = world * cvu_per_step * e2e_steps / t_e2e
+    value = replica_value(cvu_per_step * args.steps, world, t_dev)
+    e2e = replica_value(cvu_per_step * e2e_steps, world, t_e2e)
     peak, peak_kind = measured_peak()
     alg_bytes = 2 * Q * 4 * cells
     achieved = alg_bytes / launch_s / 1e9
@@ -378,6 +444,8 @@ def main():
     }
     if adjoint is not None:
         line["adjoint"] = adjoint
+    if batched is not None:
+        line["batched"] = batched
     if world == 1 and not args.no_cpu_baseline:
         import oracle
 

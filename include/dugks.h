@@ -199,6 +199,39 @@ dugks_status dugks_adjoint_step(dugks_ctx *ctx, const void *f_dev, const void *m
 dugks_status dugks_adjoint(dugks_ctx *ctx, const void *phi0_dev, long long nsteps, int checkpoint_every,
                            const void *grad_phiN_dev, void *grad_phi0_dev, double *grad_alpha_out);
 
+/* ---- batched instances ---------------------------------------------------
+ * Many independent instances of the step of Section 2 (each with its own
+ * mesh, coefficients and time step) advanced together: every time step is one
+ * persistent launch whose warps take (instance, strip, row segment) tiles from
+ * a global queue, largest instances first; runs of steps replay a captured
+ * CUDA graph.  Single precision only (DUGKS_ERR_UNSUPPORTED otherwise), and
+ * equilibrium polynomials of degree <= 3.  Instance i is addressed by its
+ * index; its fields have the single-instance layouts. */
+typedef struct dugks_batch dugks_batch;
+
+/* Create n instances (arrays of n meshes, velocity sets, coefficients, time
+ * steps).  opts may be NULL; opts->stream NULL makes the batch create its own
+ * non-blocking stream.  Each instance is validated as by dugks_check_config. */
+dugks_status dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_vset *vsets, const dugks_coef *coefs,
+                                const double *dts, const dugks_options *opts, dugks_batch **out);
+dugks_status dugks_batch_destroy(dugks_batch *b);
+/* ftilde = feq(phi0) for instance i (device [ny][nx] float); only before the first step. */
+dugks_status dugks_batch_init_phi(dugks_batch *b, int i, const void *phi0_dev);
+/* n time steps of every instance, asynchronous on the batch's stream. */
+dugks_status dugks_batch_step(dugks_batch *b, long long n);
+/* phi (and mass) of instance i, as dugks_get_phi. */
+dugks_status dugks_batch_get_phi(dugks_batch *b, int i, void *phi_dev_out, double *mass_out);
+/* ftilde of instance i into a device buffer [9][ny][nx], as dugks_save_state. */
+dugks_status dugks_batch_save_state(dugks_batch *b, int i, void *f_dev_out);
+/* Synchronise; DUGKS_ERR_TIMEOUT if a bounded device wait expired. */
+dugks_status dugks_batch_sync(dugks_batch *b);
+/* Autotuner: times steps_per_trial steps for each candidate tile height (rows
+ * per tile, 8 ... 128) on snapshots of the current states, keeps the fastest
+ * and restores the states.  Outputs (nullable): the chosen rows per tile and
+ * milliseconds per step. */
+dugks_status dugks_batch_autotune(dugks_batch *b, int steps_per_trial, int *best_rows_out, float *best_ms_out);
+const char *dugks_batch_last_error(const dugks_batch *b);
+
 /* ---- allocation-free variant -------------------------------------------
  * No counterpart in the paper: a convenience for callers that cannot
  * allocate device memory, for example a host application whose memory pool

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libdugks.so")
 SOURCES = [os.path.join(CSRC, "dugks_api.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("dugks_device.cuh", "dugks_kernels.cuh", "dugks_adjoint.cuh")] + [
+DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("dugks_device.cuh", "dugks_kernels.cuh", "dugks_adjoint.cuh", "dugks_batch.cuh")] + [
     os.path.join(ROOT, "include", "dugks.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <numeric>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -20,6 +21,7 @@
 
 #include "../../include/dugks.h"
 #include "dugks_adjoint.cuh"
+#include "dugks_batch.cuh"
 #include "dugks_kernels.cuh"
 
 using namespace dugks;
@@ -68,6 +70,23 @@ struct dugks_ctx {
     void* adj_ay = nullptr;
     double* adj_partial = nullptr;
     double* adj_dalpha = nullptr;
+    std::string last_error;
+};
+
+struct dugks_batch {
+    int n = 0, device = 0, nc = 3;
+    std::vector<dugks_ctx*> ctx;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void* d_insts = nullptr;   // BatchInst<nc>[n]
+    int* d_tile_inst = nullptr;
+    int* d_counters = nullptr;  // one per launch of a graph (plus the remainder)
+    int* d_err = nullptr;
+    int ntiles = 0, seg_target = 48, blocks = 0, stages = 4;
+    static constexpr int kGraphSteps = 50;  // even: a replay leaves the parity unchanged
+    cudaGraphExec_t graph = nullptr;
+    int parity = 0;
+    long long steps_done = 0;
     std::string last_error;
 };
 
@@ -136,17 +155,25 @@ void build_metrics(const std::vector<double>& f, bool per, double hcv, double dt
     }
 }
 
+// Weights (a, b) of a convex-type combination a f + b feq with a + b = 1 exactly in T.
+// a lies in (-1, 1) for Eqs. 2.13 and 2.21, so b = 1 - a is in (0, 2); with b rounded
+// first, 1 - b is exact (Sterbenz) and a + b == 1 in T: rounded weights cannot bias
+// the discrete mass.
+template <typename T>
+void unit_pair(double a_exact, T& a, T& b) {
+    b = T(1.0 - double(T(a_exact)));
+    a = T(1.0 - double(b));
+}
+
 template <typename T, int NC>
 Consts<T, NC> make_consts(const dugks_ctx* ctx) {
     Consts<T, NC> k;
     for (int i = 0; i < Q; ++i)
         for (int m = 0; m < NC; ++m) k.feq[i][m] = T(ctx->feq_coef[i][m]);
     // Eq. 2.21 weights also sum to one (2h = dt)
-    k.a_bp = T(ctx->a_bp);
-    k.b_bp = T(1.0 - double(k.a_bp));
+    unit_pair<T>(ctx->a_bp, k.a_bp, k.b_bp);
     // Eq. 2.13 weights sum to one; keep that exact in the stored precision
-    k.a_tp = T(ctx->a_tp);
-    k.b_tp = T(1.0 - double(k.a_tp));
+    unit_pair<T>(ctx->a_tp, k.a_tp, k.b_tp);
     k.a_f = T(ctx->a_f); k.b_f = T(ctx->b_f);
     for (int i = 0; i < Q; ++i)
         for (int m = 0; m < NC; ++m) {
@@ -440,6 +467,117 @@ cudaError_t launch_init_adjoint(dugks_ctx* ctx, const void* phi0, const void* la
         static_cast<const T*>(phi0), static_cast<const T*>(lam), static_cast<T*>(gphi0), n,
         make_adj_consts<T, NC_LARGE>(ctx));
     return cudaGetLastError();
+}
+
+dugks_status batch_fail(dugks_batch* b, cudaError_t e, const char* what) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    b->last_error = buf;
+    return e == cudaErrorMemoryAllocation ? DUGKS_ERR_NOMEM : DUGKS_ERR_CUDA;
+}
+
+// Instance table and tile map for the current tile shape (seg_target rows per tile).
+template <int NC>
+dugks_status batch_build_tables(dugks_batch* b) {
+    std::vector<BatchInst<NC>> h(size_t(b->n));
+    std::vector<int> order(size_t(b->n));
+    std::iota(order.begin(), order.end(), 0);
+    // largest instances first, so the tile queue drains them early (longest-processing-time order)
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return (long long)b->ctx[x]->nx * b->ctx[x]->ny > (long long)b->ctx[y]->nx * b->ctx[y]->ny;
+    });
+    std::vector<int> tile_inst;
+    for (int oi : order) {
+        dugks_ctx* c = b->ctx[oi];
+        BatchInst<NC>& I = h[size_t(oi)];
+        memcpy(&I.tmap[0], &c->tmap[0], sizeof(CUtensorMap));
+        memcpy(&I.tmap[1], &c->tmap[1], sizeof(CUtensorMap));
+        I.args[0] = make_args<float, NC>(c, 0);
+        I.args[1] = make_args<float, NC>(c, 1);
+        I.args[0].err = I.args[1].err = b->d_err;
+        I.k = make_constsp<NC>(c);
+        I.nstrips = (c->nx + WarpLayout<float>::WI - 1) / WarpLayout<float>::WI;
+        I.seg_rows = std::max(1, std::min(b->seg_target, c->ny));
+        I.nseg = (c->ny + I.seg_rows - 1) / I.seg_rows;
+        I.tile_begin = int(tile_inst.size());
+        for (int t = 0; t < I.nstrips * I.nseg; ++t) tile_inst.push_back(oi);
+    }
+    b->ntiles = int(tile_inst.size());
+    cudaError_t e;
+    if (b->d_insts) cudaFree(b->d_insts);
+    if (b->d_tile_inst) cudaFree(b->d_tile_inst);
+    b->d_insts = nullptr;
+    b->d_tile_inst = nullptr;
+    if ((e = cudaMalloc(&b->d_insts, sizeof(BatchInst<NC>) * h.size())) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_tile_inst, sizeof(int) * tile_inst.size())) != cudaSuccess)
+        return batch_fail(b, e, "cudaMalloc(batch tables)");
+    if ((e = cudaMemcpy(b->d_insts, h.data(), sizeof(BatchInst<NC>) * h.size(), cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaMemcpy(b->d_tile_inst, tile_inst.data(), sizeof(int) * tile_inst.size(), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+        return batch_fail(b, e, "cudaMemcpy(batch tables)");
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return DUGKS_OK;
+}
+
+dugks_status batch_tables(dugks_batch* b) { return b->nc == 3 ? batch_build_tables<3>(b) : batch_build_tables<4>(b); }
+
+template <int NC>
+cudaError_t batch_launch(dugks_batch* b, int* counter, int parity) {
+    const size_t smem = WarpLayout<float>::bytes(b->stages);
+    batch_step_vp<NC><<<b->blocks, 32, smem, b->stream>>>(static_cast<const BatchInst<NC>*>(b->d_insts),
+                                                          b->d_tile_inst, b->ntiles, parity, counter, b->stages,
+                                                          b->d_err);
+    return cudaGetLastError();
+}
+
+// n steps as direct launches (counters reset first), starting from parity b->parity
+cudaError_t batch_launch_steps(dugks_batch* b, int n) {
+    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(int) * size_t(n), b->stream);
+    for (int s = 0; s < n && e == cudaSuccess; ++s) {
+        e = b->nc == 3 ? batch_launch<3>(b, b->d_counters + s, b->parity) : batch_launch<4>(b, b->d_counters + s, b->parity);
+        b->parity ^= 1;
+    }
+    return e;
+}
+
+dugks_status batch_graph(dugks_batch* b) {
+    if (b->graph) return DUGKS_OK;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return batch_fail(b, e, "cudaStreamBeginCapture");
+    const int p0 = b->parity;
+    e = batch_launch_steps(b, dugks_batch::kGraphSteps);
+    b->parity = p0;  // capturing launched nothing
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return batch_fail(b, e, "batch capture"); }
+    if (e2 != cudaSuccess) return batch_fail(b, e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { b->graph = nullptr; return batch_fail(b, e, "cudaGraphInstantiate"); }
+    return DUGKS_OK;
+}
+
+dugks_status batch_step_impl(dugks_batch* b, long long n) {
+    const long long G = dugks_batch::kGraphSteps;
+    cudaError_t e;
+    if (n >= G) {
+        // the graph was captured for parity 0; it returns to the parity it started from
+        if (b->parity != 0) {
+            if ((e = batch_launch_steps(b, 1)) != cudaSuccess) return batch_fail(b, e, "batch step");
+            --n;
+        }
+        dugks_status st = batch_graph(b);
+        if (st != DUGKS_OK) return st;
+        for (long long r = 0; r + G <= n; r += G)
+            if ((e = cudaGraphLaunch(b->graph, b->stream)) != cudaSuccess) return batch_fail(b, e, "cudaGraphLaunch");
+        n %= G;
+    }
+    if (n > 0 && (e = batch_launch_steps(b, int(n))) != cudaSuccess) return batch_fail(b, e, "batch step");
+    return DUGKS_OK;
 }
 
 }  // namespace
@@ -855,6 +993,201 @@ dugks_status dugks_adjoint(dugks_ctx* ctx, const void* phi0_dev, long long nstep
     if (grad_alpha_out) *grad_alpha_out = da;
     return DUGKS_OK;
 }
+
+dugks_status dugks_batch_create(int n, const dugks_mesh* meshes, const dugks_vset* vsets, const dugks_coef* coefs,
+                                const double* dts, const dugks_options* opts, dugks_batch** out) {
+    if (!out) return DUGKS_ERR_ARG;
+    *out = nullptr;
+    if (n < 1 || !meshes || !vsets || !coefs || !dts) return DUGKS_ERR_ARG;
+    dugks_options o = {DUGKS_FP32, DUGKS_KERNEL_FUSED, nullptr, -1};
+    if (opts) o = *opts;
+    if (o.precision != DUGKS_FP32) return DUGKS_ERR_UNSUPPORTED;  // the batched step is single precision
+    for (int i = 0; i < n; ++i) {
+        dugks_status st = dugks_check_config(&meshes[i], &vsets[i], &coefs[i], dts[i]);
+        if (st != DUGKS_OK) return st;
+    }
+    dugks_batch* b = new (std::nothrow) dugks_batch();
+    if (!b) return DUGKS_ERR_NOMEM;
+    if (o.device < 0) {
+        if (cudaGetDevice(&b->device) != cudaSuccess) { delete b; return DUGKS_ERR_CUDA; }
+    } else {
+        b->device = o.device;
+    }
+    DeviceGuard guard(b->device);
+    auto fail = [&](dugks_status s) {
+        dugks_batch_destroy(b);
+        return s;
+    };
+    b->n = n;
+    if (o.stream) {
+        b->stream = static_cast<cudaStream_t>(o.stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) { delete b; return DUGKS_ERR_CUDA; }
+        b->own_stream = true;
+    }
+    dugks_options io = o;
+    io.kernel = DUGKS_KERNEL_FUSED;
+    io.stream = b->stream;
+    io.device = b->device;
+    b->ctx.assign(size_t(n), nullptr);
+    int nc = 3;
+    for (int i = 0; i < n; ++i) {
+        dugks_status st = dugks_create(&meshes[i], &vsets[i], &coefs[i], dts[i], &io, &b->ctx[size_t(i)]);
+        if (st != DUGKS_OK) return fail(st);
+        if (b->ctx[size_t(i)]->nc > 4) return fail(DUGKS_ERR_UNSUPPORTED);  // equilibrium polynomials of degree <= 3
+        nc = std::max(nc, b->ctx[size_t(i)]->nc);
+    }
+    b->nc = nc;
+    int sms = 0, occ = 0;
+    cudaError_t e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device)) != cudaSuccess)
+        return fail(batch_fail(b, e, "cudaDeviceGetAttribute"));
+    const size_t smem = WarpLayout<float>::bytes(b->stages);
+    void* fn = nc == 3 ? reinterpret_cast<void*>(&batch_step_vp<3>) : reinterpret_cast<void*>(&batch_step_vp<4>);
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32, smem)) != cudaSuccess)
+        return fail(batch_fail(b, e, "batch kernel attributes"));
+    b->blocks = sms * std::max(1, occ);
+    if ((e = cudaMalloc(&b->d_counters, sizeof(int) * dugks_batch::kGraphSteps)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_err, sizeof(int))) != cudaSuccess ||
+        (e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream)) != cudaSuccess)
+        return fail(batch_fail(b, e, "cudaMalloc(batch scalars)"));
+    dugks_status st = batch_tables(b);
+    if (st != DUGKS_OK) return fail(st);
+    if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return fail(batch_fail(b, e, "cudaStreamSynchronize"));
+    *out = b;
+    return DUGKS_OK;
+}
+
+dugks_status dugks_batch_destroy(dugks_batch* b) {
+    if (!b) return DUGKS_OK;
+    {
+        DeviceGuard guard(b->device);
+        if (b->stream) cudaStreamSynchronize(b->stream);
+        if (b->graph) cudaGraphExecDestroy(b->graph);
+        for (void* p : {b->d_insts, static_cast<void*>(b->d_tile_inst), static_cast<void*>(b->d_counters),
+                        static_cast<void*>(b->d_err)})
+            if (p) cudaFree(p);
+    }
+    for (dugks_ctx* c : b->ctx) dugks_destroy(c);
+    if (b->own_stream) {
+        DeviceGuard guard(b->device);
+        cudaStreamDestroy(b->stream);
+    }
+    delete b;
+    return DUGKS_OK;
+}
+
+dugks_status dugks_batch_init_phi(dugks_batch* b, int i, const void* phi0_dev) {
+    if (!b || i < 0 || i >= b->n) return DUGKS_ERR_ARG;
+    if (b->parity != 0) return DUGKS_ERR_UNSUPPORTED;  // initialise every instance before the first step
+    return dugks_init_phi(b->ctx[size_t(i)], phi0_dev);
+}
+
+dugks_status dugks_batch_step(dugks_batch* b, long long n) {
+    if (!b || n < 0) return DUGKS_ERR_ARG;
+    DeviceGuard guard(b->device);
+    const int p0 = b->parity;
+    dugks_status st = batch_step_impl(b, n);
+    if (st != DUGKS_OK) return st;
+    // the instances' contexts follow the batch's parity
+    for (dugks_ctx* c : b->ctx) {
+        c->cur = b->parity;
+        c->steps_done += n;
+    }
+    (void)p0;
+    b->steps_done += n;
+    return DUGKS_OK;
+}
+
+dugks_status dugks_batch_get_phi(dugks_batch* b, int i, void* phi_dev_out, double* mass_out) {
+    if (!b || i < 0 || i >= b->n) return DUGKS_ERR_ARG;
+    return dugks_get_phi(b->ctx[size_t(i)], phi_dev_out, mass_out);
+}
+
+dugks_status dugks_batch_save_state(dugks_batch* b, int i, void* f_dev_out) {
+    if (!b || i < 0 || i >= b->n) return DUGKS_ERR_ARG;
+    return dugks_save_state(b->ctx[size_t(i)], f_dev_out);
+}
+
+dugks_status dugks_batch_sync(dugks_batch* b) {
+    if (!b) return DUGKS_ERR_ARG;
+    DeviceGuard guard(b->device);
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return batch_fail(b, e, "cudaStreamSynchronize");
+    int err = 0;
+    if ((e = cudaMemcpy(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return batch_fail(b, e, "cudaMemcpy");
+    if (err) {
+        b->last_error = "a bounded TMA wait in the batched step expired";
+        return DUGKS_ERR_TIMEOUT;
+    }
+    return DUGKS_OK;
+}
+
+dugks_status dugks_batch_autotune(dugks_batch* b, int steps_per_trial, int* best_rows_out, float* best_ms_out) {
+    if (!b || steps_per_trial < 1) return DUGKS_ERR_ARG;
+    DeviceGuard guard(b->device);
+    // trial steps run on copies: every instance's state is saved first and restored afterwards
+    std::vector<void*> saved(size_t(b->n), nullptr);
+    auto release = [&]() {
+        for (void* p : saved) if (p) cudaFree(p);
+    };
+    cudaError_t e;
+    for (int i = 0; i < b->n; ++i) {
+        dugks_ctx* c = b->ctx[size_t(i)];
+        if ((e = cudaMalloc(&saved[size_t(i)], size_t(Q) * c->nx * c->ny * c->elem)) != cudaSuccess) {
+            release();
+            return batch_fail(b, e, "cudaMalloc(autotune snapshot)");
+        }
+        dugks_status st = dugks_save_state(c, saved[size_t(i)]);
+        if (st != DUGKS_OK) { release(); return st; }
+    }
+    const int p_saved = b->parity;
+    const int cands[] = {8, 16, 24, 32, 48, 64, 96, 128};
+    int best = b->seg_target;
+    float best_ms = 1e30f;
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    for (int cand : cands) {
+        b->seg_target = cand;
+        dugks_status st = batch_tables(b);
+        if (st != DUGKS_OK) { release(); return st; }
+        if ((e = batch_launch_steps(b, std::min(2, dugks_batch::kGraphSteps))) != cudaSuccess) break;  // warm-up
+        cudaEventRecord(ev0, b->stream);
+        for (int s = 0; s < steps_per_trial && e == cudaSuccess; s += dugks_batch::kGraphSteps)
+            e = batch_launch_steps(b, std::min(dugks_batch::kGraphSteps, steps_per_trial - s));
+        cudaEventRecord(ev1, b->stream);
+        if (e != cudaSuccess || (e = cudaEventSynchronize(ev1)) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        if (ms < best_ms) { best_ms = ms; best = cand; }
+    }
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (e != cudaSuccess) { release(); return batch_fail(b, e, "autotune trial"); }
+    // restore the states and the parity they belong to
+    b->parity = p_saved;
+    for (int i = 0; i < b->n; ++i) {
+        dugks_ctx* c = b->ctx[size_t(i)];
+        c->cur = p_saved;
+        const long long sd = c->steps_done;
+        dugks_status st = dugks_load_state(c, saved[size_t(i)]);
+        c->steps_done = sd;
+        if (st != DUGKS_OK) { release(); return st; }
+    }
+    if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) { release(); return batch_fail(b, e, "sync"); }
+    release();
+    b->seg_target = best;
+    dugks_status st = batch_tables(b);
+    if (st != DUGKS_OK) return st;
+    if (best_rows_out) *best_rows_out = best;
+    if (best_ms_out) *best_ms_out = best_ms / float(steps_per_trial);
+    return DUGKS_OK;
+}
+
+const char* dugks_batch_last_error(const dugks_batch* b) { return b ? b->last_error.c_str() : ""; }
 
 }  // extern "C"
 

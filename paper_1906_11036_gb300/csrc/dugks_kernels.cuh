@@ -526,10 +526,85 @@ __device__ __forceinline__ float vsum(const V9& a) {
     return a.z + (s.v.x + s.v.y);
 }
 
+// Parts of a row that read the constants.  They are free functions (not
+// lambdas) so that the constants stay direct constant-bank operands.
+template <int NC>
+__device__ __forceinline__ void vp_cell(const ConstsP<NC>& k, const V9& F, V9& P, V9& Fp, const bool ghost,
+                                        const float bv) {
+    // P (Eq. 2.21, b_bp folded into the polynomials) and Fp = P + (P - ft)/3 (Eq. 2.23)
+    const float phi = vsum(F);
+    const F2 phi2 = f2(phi);
+    F2 hs = f2(0.f);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const F2 h = hbp2(k, q, phi2);
+        P.p[q] = fma2(F2{k.a_bp2}, F.p[q], h);
+        hs = hs + h;
+    }
+    P.z = fmaf(k.a_bp, F.z, fmaf(k.b_bp, phi, -(hs.v.x + hs.v.y)));  // rest velocity via the zeroth moment
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Fp.p[q] = fma2(F2{k.third2}, P.p[q] - F.p[q], P.p[q]);
+    Fp.z = fmaf(k.third, P.z - F.z, P.z);
+    if (ghost) {  // mirrored NEE ghost: P_g = feq(2 bv - phi) + P - feq(phi)
+        float fe[Q], fg[Q];
+        feq_all(k.s, phi, fe);
+        feq_all(k.s, 2.f * bv - phi, fg);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) P.p[q] = P.p[q] + f2(fg[PA(q)] - fe[PA(q)], fg[PB(q)] - fe[PB(q)]);
+        P.z += fg[0] - fe[0];
+    }
+}
+// this row's half of the y-face above it (lower cell)
+template <int NC>
+__device__ __forceinline__ void vp_lower(const ConstsP<NC>& k, const FaceM<float>& f, const V9& P,
+                                         const F2 (&Gx)[4], V9& Ly) {
+    const F2 ayp = sgn2(1.f - f.w, f.hcd, 1), ay0 = f2(1.f - f.w);
+    const F2 gp = sgn2(0.f, -k.hc * f.tl, 1), gn = sgn2(0.f, -k.hc * f.tl, -1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        F2 v = (QY(q) != 0 ? ayp : ay0) * P.p[q];
+        if (QX(q) != 0) v = fma2(QX(q) > 0 ? gp : gn, Gx[q], v);
+        Ly.p[q] = v;
+    }
+    Ly.z = (1.f - f.w) * P.z;
+}
+// y-face below this row: lower half Ly plus this row (upper cell); original f of the crossing pairs
+template <int NC>
+__device__ __forceinline__ void vp_yface(const ConstsP<NC>& k, const FaceM<float>& f, const V9& P,
+                                         const F2 (&Gx)[4], const V9& Ly, F2 (&fy)[4]) {
+    const F2 ayp = sgn2(f.w, -f.hcd, 1), ay0 = f2(f.w);
+    const F2 gp = sgn2(0.f, -k.hc * f.tr, 1), gn = sgn2(0.f, -k.hc * f.tr, -1);
+    V9 fb;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        F2 v = (QY(q) != 0 ? ayp : ay0) * P.p[q];
+        if (QX(q) != 0) v = fma2(QX(q) > 0 ? gp : gn, Gx[q], v);
+        fb.p[q] = Ly.p[q] + v;
+    }
+    fb.z = fmaf(f.w, P.z, Ly.z);
+    const F2 phib = f2(vsum(fb));
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (QY(q) != 0) fy[q] = fma2(F2{k.a_f2}, fb.p[q], hf2(k, q, phib));
+}
+// x-face east of this cell from its fbar: original f (Eq. 2.22) and east-minus-west differences
+template <int NC>
+__device__ __forceinline__ void vp_xflux(const ConstsP<NC>& k, const V9& fb, F2 (&dW)[4]) {
+    const F2 phib = f2(vsum(fb));
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (QX(q) != 0) {
+            const F2 fe = fma2(F2{k.a_f2}, fb.p[q], hf2(k, q, phib));
+            dW[q] = fe - shfl_up2(fe);  // the west face is lane - 1's east face
+        }
+}
+
 template <int NC, bool EDGE>
 __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<float, NC>& a, const ConstsP<NC>& k,
                                         unsigned char* stages, uint64_t* bars, const int S, const int lane,
-                                        const int xw, const int y0, const int y1) {
+                                        const int xw, const int y0, const int y1, int& ring) {
+    // `ring` counts the rows this warp has already passed through its stage ring (a warp may
+    // process several tiles); row t of the warp uses stage t % S in phase (t / S) & 1
     using L = WarpLayout<float>;
     const int nx = a.nx, ny = a.ny;
     const int j = xw - 1 + lane;
@@ -568,12 +643,13 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
     };
     if (lane == 0) {
         for (int q = 0; q < min(S, R); ++q) {
-            mbar_arrive_expect_tx(&bars[q], uint32_t(L::BOX_BYTES));
-            tma_load_3d(stages + size_t(q) * L::STAGE_BYTES, tin, &bars[q], xs, src_row(y0 - 1 + q), 0);
+            const int st = (ring + q) % S;
+            mbar_arrive_expect_tx(&bars[st], uint32_t(L::BOX_BYTES));
+            tma_load_3d(stages + size_t(st) * L::STAGE_BYTES, tin, &bars[st], xs, src_row(y0 - 1 + q), 0);
         }
     }
-    int s = 0, issued = min(S, R), consumed = 0;
-    uint32_t ph = 0;
+    int s = ring % S, issued = min(S, R), consumed = 0;
+    uint32_t ph = uint32_t((ring / S) & 1);
 
     auto load_row = [&](int r, V9& F) -> bool {
         const bool ok = mbar_wait_bounded(&bars[s], ph, 2000000000ull);
@@ -607,71 +683,15 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
         ++consumed;
         return true;
     };
-    // P (Eq. 2.21, b_bp folded into the polynomials) and Fp = P + (P - ft)/3 (Eq. 2.23)
-    auto cell_row = [&](int r, const V9& F, V9& P, V9& Fp) {
-        const float phi = vsum(F);
-        const F2 phi2 = f2(phi);
-        F2 hs = f2(0.f);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const F2 h = hbp2(k, q, phi2);
-            P.p[q] = fma2(F2{k.a_bp2}, F.p[q], h);
-            hs = hs + h;
-        }
-        P.z = fmaf(k.a_bp, F.z, fmaf(k.b_bp, phi, -(hs.v.x + hs.v.y)));  // rest velocity via the zeroth moment
-#pragma unroll
-        for (int q = 0; q < 4; ++q) Fp.p[q] = fma2(F2{k.third2}, P.p[q] - F.p[q], P.p[q]);
-        Fp.z = fmaf(k.third, P.z - F.z, P.z);
-        const bool ghost_row = !a.yper && (r < 0 || r >= ny);
-        if (ghost_row || ghost_col) {
-            const float bv = ghost_col ? bvx : (r < 0 ? k.s.bcv[2] : k.s.bcv[3]);
-            float fe[Q], fg[Q];
-            feq_all(k.s, phi, fe);
-            feq_all(k.s, 2.f * bv - phi, fg);
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                P.p[q] = P.p[q] + f2(fg[PA(q)] - fe[PA(q)], fg[PB(q)] - fe[PB(q)]);
-            P.z += fg[0] - fe[0];
-        }
-    };
     auto grad_x = [&](int r, const V9& P, F2 (&Gx)[4]) {
         const F2 ig = f2((!a.yper && (r < 0 || r >= ny)) ? 0.f : igx_in);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             if (QX(q) != 0) Gx[q] = (shfl_dn2(P.p[q]) - shfl_up2(P.p[q])) * ig;
     };
-    auto lower_half = [&](const FaceM<float>& f, const V9& P, const F2 (&Gx)[4], V9& Ly) {
-        const F2 ayp = sgn2(1.f - f.w, f.hcd, 1), ay0 = f2(1.f - f.w);
-        const F2 gp = sgn2(0.f, -k.hc * f.tl, 1), gn = sgn2(0.f, -k.hc * f.tl, -1);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            F2 v = (QY(q) != 0 ? ayp : ay0) * P.p[q];
-            if (QX(q) != 0) v = fma2(QX(q) > 0 ? gp : gn, Gx[q], v);
-            Ly.p[q] = v;
-        }
-        Ly.z = (1.f - f.w) * P.z;
-    };
-    auto y_face = [&](const FaceM<float>& f, const V9& P, const F2 (&Gx)[4], const V9& Ly, F2 (&fy)[4]) {
-        const F2 ayp = sgn2(f.w, -f.hcd, 1), ay0 = f2(f.w);
-        const F2 gp = sgn2(0.f, -k.hc * f.tr, 1), gn = sgn2(0.f, -k.hc * f.tr, -1);
-        V9 fb;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            F2 v = (QY(q) != 0 ? ayp : ay0) * P.p[q];
-            if (QX(q) != 0) v = fma2(QX(q) > 0 ? gp : gn, Gx[q], v);
-            fb.p[q] = Ly.p[q] + v;
-        }
-        fb.z = fmaf(f.w, P.z, Ly.z);
-        const F2 phib = f2(vsum(fb));
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (QY(q) != 0) fy[q] = fma2(F2{k.a_f2}, fb.p[q], hf2(k, q, phib));
-    };
-    auto x_update = [&](int kr, const V9& P0, const V9& P, const F2 (&Pm)[4], const V9& Fp0, const F2 (&fN)[4],
-                        const F2 (&fS)[4]) {
-        const CellM<float> cyk = a.cy[kr + 1];
+    // fbar at this cell's east x-face: its own half plus the east neighbour's half
+    auto x_fbar = [&](const CellM<float>& cyk, const V9& P0, const V9& P, const F2 (&Pm)[4], V9& fb) {
         const F2 igy = f2((ghost_col || (EDGE && role == ROLE_OUT)) ? 0.f : cyk.ig);
-        V9 fb;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             F2 lx = axL(q) * P0.p[q], rxh = axR(q) * P0.p[q];
@@ -683,14 +703,10 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
             fb.p[q] = lx + shfl_dn2(rxh);
         }
         fb.z = (1.f - fE.w) * P0.z + __shfl_down_sync(0xffffffffu, fW.w * P0.z, 1);
-        const F2 phib = f2(vsum(fb));
-        F2 dW[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (QX(q) != 0) {
-                const F2 fe = fma2(F2{k.a_f2}, fb.p[q], hf2(k, q, phib));
-                dW[q] = fe - shfl_up2(fe);  // east minus west (lane - 1's east face)
-            }
+    };
+    // cell update (Eq. 2.12) and store of row kr
+    auto x_store = [&](int kr, const CellM<float>& cyk, const V9& Fp0, const F2 (&dW)[4], const F2 (&fN)[4],
+                       const F2 (&fS)[4]) {
         const F2 ryp = sgn2(0.f, -cyk.r, 1);
         V9 v = Fp0;
 #pragma unroll
@@ -708,6 +724,9 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
             }
         }
     };
+    auto ghost_of = [&](int r) { return ghost_col || (!a.yper && (r < 0 || r >= ny)); };
+    const float bv_s = k.s.bcv[2], bv_n = k.s.bcv[3];
+    auto bv_of = [&](int r) { return ghost_col ? bvx : (r < 0 ? bv_s : bv_n); };
 
     bool failed = false;
     V9 F, P0, Fp0, Ly;
@@ -718,9 +737,9 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
     // face metrics: fyB = face below the current row, fyA = face above it (index f+1 for face f)
     FaceM<float> fyB = a.fy[y0], fyA = a.fy[y0 + 1];
     if (!failed) {
-        cell_row(y0 - 1, F, P0, Fp0);
+        vp_cell(k, F, P0, Fp0, ghost_of(y0 - 1), bv_of(y0 - 1));
         grad_x(y0 - 1, P0, Gx);
-        lower_half(fyA, P0, Gx, Ly);
+        vp_lower(k, fyA, P0, Gx, Ly);
 #pragma unroll
         for (int q = 0; q < 4; ++q) Pm[q] = P0.p[q];
         if (!load_row(y0, F)) failed = true;
@@ -728,10 +747,10 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
     if (!failed) {
         fyB = fyA;
         fyA = a.fy[y0 + 2];
-        cell_row(y0, F, P0, Fp0);
+        vp_cell(k, F, P0, Fp0, ghost_of(y0), bv_of(y0));
         grad_x(y0, P0, Gx);
-        y_face(fyB, P0, Gx, Ly, fS);
-        lower_half(fyA, P0, Gx, Ly);
+        vp_yface(k, fyB, P0, Gx, Ly, fS);
+        vp_lower(k, fyA, P0, Gx, Ly);
 #pragma unroll 2
         for (int r = y0 + 1; r <= y1; ++r) {
             V9 P, Fp;
@@ -739,11 +758,18 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
             if (!load_row(r, F)) { failed = true; break; }
             fyB = fyA;
             fyA = a.fy[r + 2];
-            cell_row(r, F, P, Fp);
+            vp_cell(k, F, P, Fp, ghost_of(r), bv_of(r));
             grad_x(r, P, Gx);
-            y_face(fyB, P, Gx, Ly, fN);
-            lower_half(fyA, P, Gx, Ly);
-            x_update(r - 1, P0, P, Pm, Fp0, fN, fS);
+            vp_yface(k, fyB, P, Gx, Ly, fN);
+            vp_lower(k, fyA, P, Gx, Ly);
+            {
+                const CellM<float> cyk = a.cy[r];  // row r - 1
+                V9 fb;
+                F2 dW[4];
+                x_fbar(cyk, P0, P, Pm, fb);
+                vp_xflux(k, fb, dW);
+                x_store(r - 1, cyk, Fp0, dW, fN, fS);
+            }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 Pm[q] = P0.p[q];
@@ -760,6 +786,7 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
             if (++s == S) { s = 0; ph ^= 1u; }
         }
     }
+    ring += issued;
     __syncwarp();
 }
 
@@ -782,8 +809,9 @@ __global__ void __launch_bounds__(32, DUGKS_VP_MIN_WARPS) fused_step_vp(const __
     }
     __syncwarp();
     const bool edge = xw - 1 < 0 || xw + L::WI >= a.nx;
-    if (edge) vp_rows<NC, true>(&tin, a, k, smem, bars, S, lane, xw, y0, y1);
-    else vp_rows<NC, false>(&tin, a, k, smem, bars, S, lane, xw, y0, y1);
+    int ring = 0;
+    if (edge) vp_rows<NC, true>(&tin, a, k, smem, bars, S, lane, xw, y0, y1, ring);
+    else vp_rows<NC, false>(&tin, a, k, smem, bars, S, lane, xw, y0, y1, ring);
 }
 
 // ---------------------------------------------------------------------------

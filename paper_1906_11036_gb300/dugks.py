@@ -82,6 +82,17 @@ def library():
         L.dugks_adjoint_step.argtypes = [vp, vp, vp, vp, vp]
         L.dugks_adjoint.argtypes = [vp, vp, ctypes.c_longlong, ctypes.c_int, vp, vp, P(ctypes.c_double)]
         L.dugks_phi_mass_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp]
+        L.dugks_batch_create.argtypes = [ctypes.c_int, P(Mesh), P(VSet), P(Coef), P(ctypes.c_double), P(Options),
+                                         P(vp)]
+        L.dugks_batch_destroy.argtypes = [vp]
+        L.dugks_batch_init_phi.argtypes = [vp, ctypes.c_int, vp]
+        L.dugks_batch_step.argtypes = [vp, ctypes.c_longlong]
+        L.dugks_batch_get_phi.argtypes = [vp, ctypes.c_int, vp, P(ctypes.c_double)]
+        L.dugks_batch_save_state.argtypes = [vp, ctypes.c_int, vp]
+        L.dugks_batch_sync.argtypes = [vp]
+        L.dugks_batch_autotune.argtypes = [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_float)]
+        L.dugks_batch_last_error.argtypes = [vp]
+        L.dugks_batch_last_error.restype = ctypes.c_char_p
         L.dugks_status_string.argtypes = [ctypes.c_int]
         L.dugks_status_string.restype = ctypes.c_char_p
         L.dugks_last_error.argtypes = [vp]
@@ -89,7 +100,9 @@ def library():
         for name in ("dugks_check_config", "dugks_create", "dugks_destroy", "dugks_init_phi", "dugks_init_phi_host",
                      "dugks_step", "dugks_get_phi", "dugks_get_phi_host", "dugks_save_state", "dugks_load_state",
                      "dugks_set_stream", "dugks_sync", "dugks_info", "dugks_adjoint_step", "dugks_adjoint",
-                     "dugks_phi_mass_noalloc"):
+                     "dugks_phi_mass_noalloc", "dugks_batch_create", "dugks_batch_destroy", "dugks_batch_init_phi",
+                     "dugks_batch_step", "dugks_batch_get_phi", "dugks_batch_save_state", "dugks_batch_sync",
+                     "dugks_batch_autotune"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -275,6 +288,86 @@ class Solver:
         i = Info()
         self._check(self.L.dugks_info(self.h, ctypes.byref(i)), "dugks_info")
         return {f: getattr(i, f) for f, _ in Info._fields_}
+
+
+class BatchSolver:
+    """Many independent instances (list of inputs.Problem) advanced together in
+    single precision by the batched persistent step."""
+
+    def __init__(self, problems, stream=None, device: int | None = None):
+        import torch
+
+        self.torch = torch
+        self.problems = list(problems)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        n = len(self.problems)
+        L = library()
+        meshes, vsets, coefs = (Mesh * n)(), (VSet * n)(), (Coef * n)()
+        self._keep = []
+        for i, p in enumerate(self.problems):
+            m, v, c, keep = marshal(p)
+            meshes[i], vsets[i], coefs[i] = m, v, c
+            self._keep.append(keep)
+        dts = (ctypes.c_double * n)(*[float(p.dt) for p in self.problems])
+        o = Options()
+        o.precision, o.kernel = 32, KERNELS["fused"]
+        self.stream = stream
+        o.stream = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        o.device = self.device.index
+        h = ctypes.c_void_p()
+        st = L.dugks_batch_create(n, meshes, vsets, coefs, dts, ctypes.byref(o), ctypes.byref(h))
+        if st != OK:
+            raise DugksError(st, "dugks_batch_create")
+        self.h, self.L, self.n = h, L, n
+
+    def _check(self, st, where):
+        if st != OK:
+            raise DugksError(st, where, self.L.dugks_batch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.dugks_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_phi(self, i: int, phi0):
+        p = self.problems[i]
+        t = self.torch.as_tensor(phi0).to(device=self.device, dtype=self.torch.float32).contiguous()
+        assert tuple(t.shape) == (p.ny, p.nx)
+        self._check(self.L.dugks_batch_init_phi(self.h, int(i), ctypes.c_void_p(t.data_ptr())), "dugks_batch_init_phi")
+        self.sync()
+
+    def step(self, n: int = 1):
+        self._check(self.L.dugks_batch_step(self.h, int(n)), "dugks_batch_step")
+
+    def get_phi(self, i: int, mass: bool = False):
+        p = self.problems[i]
+        out = self.torch.empty((p.ny, p.nx), dtype=self.torch.float32, device=self.device)
+        m = ctypes.c_double(0.0)
+        self._check(self.L.dugks_batch_get_phi(self.h, int(i), ctypes.c_void_p(out.data_ptr()),
+                                               ctypes.byref(m) if mass else None), "dugks_batch_get_phi")
+        return (out, m.value) if mass else out
+
+    def save_state(self, i: int):
+        p = self.problems[i]
+        out = self.torch.empty((9, p.ny, p.nx), dtype=self.torch.float32, device=self.device)
+        self._check(self.L.dugks_batch_save_state(self.h, int(i), ctypes.c_void_p(out.data_ptr())),
+                    "dugks_batch_save_state")
+        return out
+
+    def sync(self):
+        self._check(self.L.dugks_batch_sync(self.h), "dugks_batch_sync")
+
+    def autotune(self, steps_per_trial: int = 20):
+        rows, ms = ctypes.c_int(0), ctypes.c_float(0.0)
+        self._check(self.L.dugks_batch_autotune(self.h, int(steps_per_trial), ctypes.byref(rows), ctypes.byref(ms)),
+                    "dugks_batch_autotune")
+        return rows.value, ms.value
 
 
 def run_fn():

@@ -176,6 +176,28 @@ def nonuniform(nx: int = 2048, ny: int | None = None, steps: int = 5000, seed: i
     return p, smooth_phi0(xc, yc, seed)
 
 
+def batched(n: int = 256, seed: int = 7, steps: int = 1000, sides=(64, 128, 256, 512),
+            cfl: float = 0.4) -> list[tuple[Problem, np.ndarray]]:
+    """Independent periodic Burgers-type instances: square sides drawn uniformly
+    from `sides`, B = a phi^2/2 (1, 1) with a ~ U[0.5, 2], D = D0 (1 + phi^2) I
+    read as alpha = D0 ~ U[0.002, 0.02] and d = 1 + phi^2; c = 10, CFL 0.4 per
+    instance; phi0 of the Burgers form with a per-instance seed."""
+    rng = np.random.default_rng(seed)
+    side = rng.choice(np.asarray(sides), size=n)
+    a = rng.uniform(0.5, 2.0, size=n)
+    d0 = rng.uniform(0.002, 0.02, size=n)
+    out = []
+    for i in range(n):
+        m = int(side[i])
+        xf = uniform_faces(m)
+        p = Problem(xf=xf, yf=xf.copy(), c=10.0, u=(1.0, 1.0), b=(0.0, 0.0, 0.5 * float(a[i])),
+                    alpha=float(d0[i]), d=(1.0, 0.0, 1.0), dt=cfl_dt(xf, xf, 10.0, cfl), steps=steps,
+                    name=f"batched_{i}_{m}x{m}", meta={"a": float(a[i]), "D0": float(d0[i]), "seed": seed + 1 + i})
+        xc, yc = p.centres()
+        out.append((p, burgers_phi0(xc, yc, seed + 1 + i)))
+    return out
+
+
 PRESETS = {
     "gaussian_hill": gaussian_hill,
     "burgers": burgers,
