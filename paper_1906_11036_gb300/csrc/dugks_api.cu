@@ -296,7 +296,9 @@ dugks_status plan_fused(dugks_ctx* ctx) {
     const int wi = WarpLayout<float>::WI;
     ctx->nstrips = (ctx->nx + wi - 1) / wi;
     const long long slots = (long long)sms * occ;
-    long long nseg = std::max<long long>(1, slots / ctx->nstrips);
+    // about three waves of warps: short segments even out the end of each wave
+    // (measured on 2048^2: 20 rows per segment 75.8 us, 60 rows in one wave 78 us)
+    long long nseg = std::max<long long>(1, 3 * slots / ctx->nstrips);
     // at least 16 rows per segment so the two pipeline-fill rows stay cheap
     nseg = std::min<long long>(nseg, std::max(1, ctx->ny / 16));
     ctx->seg_rows = int((ctx->ny + nseg - 1) / nseg);
