@@ -37,8 +37,58 @@ struct AdjArgs {
     T* lam;            // out: dJ/d ftilde^n
     T* Ax;             // x-face adjoints [Q][ny][nx+1]
     T* Ay;             // y-face adjoints [Q][ny+1][nx]
+    T* P;              // forward fbar^+ of every cell [Q][ny][nx] (adj_p_kernel)
+    T* phi;            // forward phi of every cell [ny][nx]
     double* partial;   // per-block partial sums of dJ/dlambda (faces, then cells)
 };
+
+// Forward P = fbar^+ (Eq. 2.21) and phi of every cell, once per adjoint step.
+template <typename T, int NC>
+__global__ void __launch_bounds__(256) adj_p_kernel(const StepArgs<T, NC> a, const Consts<T, NC> k, const AdjArgs<T> g) {
+    const long long n = (long long)a.nx * a.ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        T ft[Q], fe[Q];
+        T phi = T(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            ft[i] = g.f[i * n + c];
+            phi += ft[i];
+        }
+        feq_all(k, phi, fe);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g.P[i * n + c] = fma(k.a_bp, ft[i], k.b_bp * fe[i]);
+        g.phi[c] = phi;
+    }
+}
+
+// P at extended cell (jj, kk) from the P buffer: interior, periodic image, or the
+// mirrored NEE ghost P_g = feq(2 bv - phi) + P - feq(phi) of the adjacent interior cell.
+template <typename T, int NC>
+__device__ void buf_P(const StepArgs<T, NC>& a, const Consts<T, NC>& k, const AdjArgs<T>& g, int jj, int kk,
+                      T (&P)[Q]) {
+    if (a.xper) jj = (jj + a.nx) % a.nx;
+    if (a.yper) kk = (kk + a.ny) % a.ny;
+    const bool gx = jj < 0 || jj >= a.nx, gy = kk < 0 || kk >= a.ny;
+    if (gx && gy) {  // corner ghost: only ever multiplied by a zero weight
+#pragma unroll
+        for (int i = 0; i < Q; ++i) P[i] = T(0);
+        return;
+    }
+    const int js = gx ? (jj < 0 ? 0 : a.nx - 1) : jj;
+    const int ks = gy ? (kk < 0 ? 0 : a.ny - 1) : kk;
+    const long long n = (long long)a.nx * a.ny, c = (long long)ks * a.nx + js;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) P[i] = g.P[i * n + c];
+    if (gx || gy) {
+        const T phi = g.phi[c];
+        const T bv = gx ? (jj < 0 ? k.bcv[0] : k.bcv[1]) : (kk < 0 ? k.bcv[2] : k.bcv[3]);
+        T fe[Q], fg[Q];
+        feq_all(k, phi, fe);
+        feq_all(k, T(2) * bv - phi, fg);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) P[i] = fg[i] + (P[i] - fe[i]);
+    }
+}
 
 template <typename T, int NC>
 __device__ __forceinline__ void dfeq_all(const AdjConsts<T, NC>& ka, T phi, T (&out)[Q]) {
@@ -89,22 +139,22 @@ __global__ void __launch_bounds__(128) adj_face_kernel(const StepArgs<T, NC> a, 
         // forward: P of the two cells and their tangential slopes
         T PL[Q], PR[Q], GL[Q], GR[Q], tmpA[Q], tmpB[Q];
         if (xface) {
-            naive_P(a, k, jf - 1, kc, PL);
-            naive_P(a, k, jf, kc, PR);
+            buf_P(a, k, g, jf - 1, kc, PL);
+            buf_P(a, k, g, jf, kc, PR);
         } else {
-            naive_P(a, k, jc, kf - 1, PL);
-            naive_P(a, k, jc, kf, PR);
+            buf_P(a, k, g, jc, kf - 1, PL);
+            buf_P(a, k, g, jc, kf, PR);
         }
         const bool lghost = !per && fidx == 0, rghost = !per && fidx == n;
 #pragma unroll
         for (int i = 0; i < Q; ++i) { GL[i] = T(0); GR[i] = T(0); }
         if (!lghost) {
             if (xface) {
-                naive_P(a, k, jf - 1, kc + 1, tmpA);
-                naive_P(a, k, jf - 1, kc - 1, tmpB);
+                buf_P(a, k, g, jf - 1, kc + 1, tmpA);
+                buf_P(a, k, g, jf - 1, kc - 1, tmpB);
             } else {
-                naive_P(a, k, jc + 1, kf - 1, tmpA);
-                naive_P(a, k, jc - 1, kf - 1, tmpB);
+                buf_P(a, k, g, jc + 1, kf - 1, tmpA);
+                buf_P(a, k, g, jc - 1, kf - 1, tmpB);
             }
             const T ig = xface ? a.cy[kc + 1].ig : a.cx[jc + 1].ig;
 #pragma unroll
@@ -112,11 +162,11 @@ __global__ void __launch_bounds__(128) adj_face_kernel(const StepArgs<T, NC> a, 
         }
         if (!rghost) {
             if (xface) {
-                naive_P(a, k, jf, kc + 1, tmpA);
-                naive_P(a, k, jf, kc - 1, tmpB);
+                buf_P(a, k, g, jf, kc + 1, tmpA);
+                buf_P(a, k, g, jf, kc - 1, tmpB);
             } else {
-                naive_P(a, k, jc + 1, kf, tmpA);
-                naive_P(a, k, jc - 1, kf, tmpB);
+                buf_P(a, k, g, jc + 1, kf, tmpA);
+                buf_P(a, k, g, jc - 1, kf, tmpB);
             }
             const T ig = xface ? a.cy[kc + 1].ig : a.cx[jc + 1].ig;
 #pragma unroll

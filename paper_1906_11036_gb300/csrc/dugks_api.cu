@@ -68,6 +68,8 @@ struct dugks_ctx {
     // adjoint work buffers (allocated on first use)
     void* adj_ax = nullptr;
     void* adj_ay = nullptr;
+    void* adj_p = nullptr;    // forward fbar^+ [Q][ny][nx]
+    void* adj_phi = nullptr;  // forward phi [ny][nx]
     double* adj_partial = nullptr;
     double* adj_dalpha = nullptr;
     std::string last_error;
@@ -367,6 +369,7 @@ void free_ctx(dugks_ctx* ctx) {
     cudaGetDevice(&prev);
     cudaSetDevice(ctx->device);
     for (void* p : {ctx->buf[0], ctx->buf[1], ctx->fxm, ctx->fym, ctx->cxm, ctx->cym, ctx->adj_ax, ctx->adj_ay,
+                    ctx->adj_p, ctx->adj_phi,
                     static_cast<void*>(ctx->adj_partial), static_cast<void*>(ctx->adj_dalpha)})
         if (p) cudaFree(p);
     for (void* p : {static_cast<void*>(ctx->dxv), static_cast<void*>(ctx->dyv), static_cast<void*>(ctx->staging),
@@ -417,6 +420,8 @@ dugks_status adj_alloc(dugks_ctx* ctx) {
     const size_t nxf = size_t(ctx->nx + 1) * ctx->ny, nyf = size_t(ctx->nx) * (ctx->ny + 1);
     if ((e = cudaMalloc(&ctx->adj_ax, Q * nxf * ctx->elem)) != cudaSuccess ||
         (e = cudaMalloc(&ctx->adj_ay, Q * nyf * ctx->elem)) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->adj_p, Q * size_t(ctx->nx) * ctx->ny * ctx->elem)) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->adj_phi, size_t(ctx->nx) * ctx->ny * ctx->elem)) != cudaSuccess ||
         (e = cudaMalloc(&ctx->adj_partial, sizeof(double) * size_t(adj_face_blocks(ctx) + adj_cell_blocks(ctx)))) !=
             cudaSuccess ||
         (e = cudaMalloc(&ctx->adj_dalpha, sizeof(double))) != cudaSuccess)
@@ -438,8 +443,12 @@ cudaError_t launch_adjoint_step(dugks_ctx* ctx, const void* f, const void* mu, v
     g.lam = static_cast<T*>(lam);
     g.Ax = static_cast<T*>(ctx->adj_ax);
     g.Ay = static_cast<T*>(ctx->adj_ay);
+    g.P = static_cast<T*>(ctx->adj_p);
+    g.phi = static_cast<T*>(ctx->adj_phi);
     g.partial = ctx->adj_partial;
     const int fb = adj_face_blocks(ctx), cb = adj_cell_blocks(ctx);
+    const long long ncell = (long long)ctx->nx * ctx->ny;
+    adj_p_kernel<T, NC><<<int(std::min<long long>((ncell + 255) / 256, 65535)), 256, 0, ctx->stream>>>(a, k, g);
     adj_face_kernel<T, NC><<<fb, 128, 0, ctx->stream>>>(a, k, ka, g);
     adj_cell_kernel<T, NC><<<cb, 128, 0, ctx->stream>>>(a, k, ka, g, fb);
     adj_sum_kernel<<<1, 256, 0, ctx->stream>>>(ctx->adj_partial, fb + cb, 3.0 / (ctx->c * ctx->c), dj_dalpha);
