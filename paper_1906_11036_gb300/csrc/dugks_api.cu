@@ -408,11 +408,33 @@ AdjConsts<T, NC> make_adj_consts(const dugks_ctx* ctx) {
     return ka;
 }
 
-int adj_face_blocks(const dugks_ctx* ctx) {
-    const long long nf = (long long)(ctx->nx + 1) * ctx->ny + (long long)ctx->nx * (ctx->ny + 1);
-    return int((nf + 127) / 128);
+// adjoint grids: 128 threads along a row, one block row per grid row (rows
+// beyond 65535 are looped over); faces in two z-slices (x-faces, y-faces)
+constexpr int kAdjThreads = 128;
+dim3 adj_face_grid(const dugks_ctx* ctx) {
+    return dim3(unsigned((ctx->nx + 1 + kAdjThreads - 1) / kAdjThreads), unsigned(std::min(ctx->ny + 1, 65535)), 2u);
 }
-int adj_cell_blocks(const dugks_ctx* ctx) { return int(((long long)ctx->nx * ctx->ny + 127) / 128); }
+dim3 adj_cell_grid(const dugks_ctx* ctx) {
+    return dim3(unsigned((ctx->nx + kAdjThreads - 1) / kAdjThreads), unsigned(std::min(ctx->ny, 65535)), 1u);
+}
+int adj_face_blocks(const dugks_ctx* ctx) {
+    const dim3 d = adj_face_grid(ctx);
+    return int(d.x * d.y * d.z);
+}
+int adj_cell_blocks(const dugks_ctx* ctx) {
+    const dim3 d = adj_cell_grid(ctx);
+    return int(d.x * d.y);
+}
+// cells next to a Dirichlet wall (adj_wall_kernel), each counted once
+long long adj_wall_cells(const dugks_ctx* ctx) {
+    const long long nx = ctx->nx, ny = ctx->ny;
+    const bool xper = ctx->xper, yper = ctx->yper;
+    const long long nrc = yper ? 0 : (ny > 1 ? 2 : 1) * nx;
+    const long long nr = yper ? ny : std::max<long long>(0, ny - 2);
+    const long long ncc = xper ? 0 : (nx > 1 ? 2 : 1) * nr;
+    return nrc + ncc;
+}
+int adj_wall_blocks(const dugks_ctx* ctx) { return int((adj_wall_cells(ctx) + kAdjThreads - 1) / kAdjThreads); }
 
 dugks_status adj_alloc(dugks_ctx* ctx) {
     if (ctx->adj_ax) return DUGKS_OK;
@@ -422,7 +444,8 @@ dugks_status adj_alloc(dugks_ctx* ctx) {
         (e = cudaMalloc(&ctx->adj_ay, Q * nyf * ctx->elem)) != cudaSuccess ||
         (e = cudaMalloc(&ctx->adj_p, Q * size_t(ctx->nx) * ctx->ny * ctx->elem)) != cudaSuccess ||
         (e = cudaMalloc(&ctx->adj_phi, size_t(ctx->nx) * ctx->ny * ctx->elem)) != cudaSuccess ||
-        (e = cudaMalloc(&ctx->adj_partial, sizeof(double) * size_t(adj_face_blocks(ctx) + adj_cell_blocks(ctx)))) !=
+        (e = cudaMalloc(&ctx->adj_partial,
+                        sizeof(double) * size_t(adj_face_blocks(ctx) + adj_cell_blocks(ctx) + adj_wall_blocks(ctx)))) !=
             cudaSuccess ||
         (e = cudaMalloc(&ctx->adj_dalpha, sizeof(double))) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaMalloc(adjoint buffers)");
@@ -449,9 +472,11 @@ cudaError_t launch_adjoint_step(dugks_ctx* ctx, const void* f, const void* mu, v
     const int fb = adj_face_blocks(ctx), cb = adj_cell_blocks(ctx);
     const long long ncell = (long long)ctx->nx * ctx->ny;
     adj_p_kernel<T, NC><<<int(std::min<long long>((ncell + 255) / 256, 65535)), 256, 0, ctx->stream>>>(a, k, g);
-    adj_face_kernel<T, NC><<<fb, 128, 0, ctx->stream>>>(a, k, ka, g);
-    adj_cell_kernel<T, NC><<<cb, 128, 0, ctx->stream>>>(a, k, ka, g, fb);
-    adj_sum_kernel<<<1, 256, 0, ctx->stream>>>(ctx->adj_partial, fb + cb, 3.0 / (ctx->c * ctx->c), dj_dalpha);
+    adj_face_kernel<T, NC><<<adj_face_grid(ctx), kAdjThreads, 0, ctx->stream>>>(a, k, ka, g);
+    adj_cell_kernel<T, NC><<<adj_cell_grid(ctx), kAdjThreads, 0, ctx->stream>>>(a, k, ka, g, fb);
+    const int wb = adj_wall_blocks(ctx);
+    if (wb > 0) adj_wall_kernel<T, NC><<<wb, kAdjThreads, 0, ctx->stream>>>(a, k, ka, g, fb + cb);
+    adj_sum_kernel<<<1, 1024, 0, ctx->stream>>>(ctx->adj_partial, fb + cb + wb, 3.0 / (ctx->c * ctx->c), dj_dalpha);
     return cudaGetLastError();
 }
 
