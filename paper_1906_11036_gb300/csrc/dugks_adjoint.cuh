@@ -41,7 +41,8 @@ struct AdjArgs {
     T* Ay;             // y-face adjoints [Q][ny+1][nx]
     T* P;              // forward fbar^+ of every cell [Q][ny][nx] (adj_p_kernel)
     T* phi;            // forward phi of every cell [ny][nx]
-    double* partial;   // per-block partial sums of dJ/dlambda (faces, then cells)
+    double* partial;   // per-block partial sums of dJ/dlambda (faces, cells, wall cells)
+    int accumulate;    // 1: add to the partials (a reverse sweep sums them once at its end); 0: overwrite
 };
 
 // Forward P = fbar^+ (Eq. 2.21) and phi of every cell, once per adjoint step.
@@ -108,7 +109,7 @@ __device__ __forceinline__ void dfeq_all(const AdjConsts<T, NC>& ka, T phi, T (&
 }
 
 template <typename T>
-__device__ __forceinline__ void block_partial(double v, double* out) {
+__device__ __forceinline__ void block_partial(double v, double* out, int accumulate) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     __shared__ double ws[32];
@@ -117,7 +118,7 @@ __device__ __forceinline__ void block_partial(double v, double* out) {
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < int(blockDim.x >> 5); ++w) s += ws[w];
-        *out = s;
+        *out = accumulate ? *out + s : s;  // each block owns its slot: no race
     }
 }
 
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(128) adj_face_kernel(const StepArgs<T, NC> a, 
             if (!(per && fidx == n)) djdl += double(s);  // a periodic face is counted once in dJ/dlambda
         }
     }
-    block_partial<T>(djdl, g.partial + (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+    block_partial<T>(djdl, g.partial + (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x, g.accumulate);
 }
 
 // Grid (ceil(nx/blockDim.x), rows): threads along j, blocks over rows kr.
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(128, 4) adj_cell_kernel(const StepArgs<T, NC> 
             for (int i = 0; i < Q; ++i) g.lam[i * cplane + t] = fma(ka.a_bp, Pb[i], fma(ka.a_tp, mu[i], phibar));
         }
     }
-    block_partial<T>(djdl, g.partial + face_blocks + blockIdx.y * gridDim.x + blockIdx.x);
+    block_partial<T>(djdl, g.partial + face_blocks + blockIdx.y * gridDim.x + blockIdx.x, g.accumulate);
 }
 
 // Cells next to a Dirichlet wall.  The mirrored NEE ghost beyond the wall has
@@ -394,7 +395,7 @@ __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs<T, NC> a, 
 #pragma unroll
         for (int i = 0; i < Q; ++i) g.lam[i * cplane + c] += fma(ka.a_bp, PG[i], dphibar);
     }
-    block_partial<T>(djdl, g.partial + first_partial + blockIdx.x);
+    block_partial<T>(djdl, g.partial + first_partial + blockIdx.x, g.accumulate);
 }
 
 // *dj_dalpha += (sum of the partials) / c_s^2, in a fixed order (one block of 1024).

@@ -435,6 +435,7 @@ long long adj_wall_cells(const dugks_ctx* ctx) {
     return nrc + ncc;
 }
 int adj_wall_blocks(const dugks_ctx* ctx) { return int((adj_wall_cells(ctx) + kAdjThreads - 1) / kAdjThreads); }
+int adj_partials(const dugks_ctx* ctx) { return adj_face_blocks(ctx) + adj_cell_blocks(ctx) + adj_wall_blocks(ctx); }
 
 dugks_status adj_alloc(dugks_ctx* ctx) {
     if (ctx->adj_ax) return DUGKS_OK;
@@ -445,13 +446,23 @@ dugks_status adj_alloc(dugks_ctx* ctx) {
         (e = cudaMalloc(&ctx->adj_p, Q * size_t(ctx->nx) * ctx->ny * ctx->elem)) != cudaSuccess ||
         (e = cudaMalloc(&ctx->adj_phi, size_t(ctx->nx) * ctx->ny * ctx->elem)) != cudaSuccess ||
         (e = cudaMalloc(&ctx->adj_partial,
-                        sizeof(double) * size_t(adj_face_blocks(ctx) + adj_cell_blocks(ctx) + adj_wall_blocks(ctx)))) !=
+                        sizeof(double) * size_t(adj_partials(ctx)))) !=
             cudaSuccess ||
         (e = cudaMalloc(&ctx->adj_dalpha, sizeof(double))) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaMalloc(adjoint buffers)");
     return DUGKS_OK;
 }
 
+
+// *dj_dalpha += (sum of the block partials) / c_s^2
+cudaError_t launch_adj_sum(dugks_ctx* ctx, double* dj_dalpha) {
+    adj_sum_kernel<<<1, 1024, 0, ctx->stream>>>(ctx->adj_partial, adj_partials(ctx), 3.0 / (ctx->c * ctx->c), dj_dalpha);
+    return cudaGetLastError();
+}
+
+// One adjoint step.  dj_dalpha != nullptr: the step's partials overwrite the
+// partial buffer and are summed into *dj_dalpha; nullptr: they are added to the
+// partial buffer (a reverse sweep zeroes it first and sums it at the end).
 template <typename T, int NC>
 cudaError_t launch_adjoint_step(dugks_ctx* ctx, const void* f, const void* mu, void* lam, double* dj_dalpha) {
     StepArgs<T, NC> a = make_args<T, NC>(ctx, 0);
@@ -469,6 +480,7 @@ cudaError_t launch_adjoint_step(dugks_ctx* ctx, const void* f, const void* mu, v
     g.P = static_cast<T*>(ctx->adj_p);
     g.phi = static_cast<T*>(ctx->adj_phi);
     g.partial = ctx->adj_partial;
+    g.accumulate = dj_dalpha ? 0 : 1;
     const int fb = adj_face_blocks(ctx), cb = adj_cell_blocks(ctx);
     const long long ncell = (long long)ctx->nx * ctx->ny;
     adj_p_kernel<T, NC><<<int(std::min<long long>((ncell + 255) / 256, 65535)), 256, 0, ctx->stream>>>(a, k, g);
@@ -476,7 +488,7 @@ cudaError_t launch_adjoint_step(dugks_ctx* ctx, const void* f, const void* mu, v
     adj_cell_kernel<T, NC><<<adj_cell_grid(ctx), kAdjThreads, 0, ctx->stream>>>(a, k, ka, g, fb);
     const int wb = adj_wall_blocks(ctx);
     if (wb > 0) adj_wall_kernel<T, NC><<<wb, kAdjThreads, 0, ctx->stream>>>(a, k, ka, g, fb + cb);
-    adj_sum_kernel<<<1, 1024, 0, ctx->stream>>>(ctx->adj_partial, fb + cb + wb, 3.0 / (ctx->c * ctx->c), dj_dalpha);
+    if (dj_dalpha) return launch_adj_sum(ctx, dj_dalpha);
     return cudaGetLastError();
 }
 
@@ -992,7 +1004,8 @@ dugks_status dugks_adjoint(dugks_ctx* ctx, const void* phi0_dev, long long nstep
         if ((st = dugks_save_state(ctx, ckpt[s])) != DUGKS_OK) { release(); return st; }
         if ((st = dugks_step(ctx, std::min(K, nsteps - s * K))) != DUGKS_OK) { release(); return st; }
     }
-    if ((e = cudaMemsetAsync(ctx->adj_dalpha, 0, sizeof(double), ctx->stream)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(ctx->adj_dalpha, 0, sizeof(double), ctx->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(ctx->adj_partial, 0, sizeof(double) * size_t(adj_partials(ctx)), ctx->stream)) != cudaSuccess)
         return fail(e, "cudaMemsetAsync");
     const long long n = (long long)ctx->nx * ctx->ny;
     const int blocks = int(std::min<long long>((n + 255) / 256, 65535));
@@ -1013,11 +1026,12 @@ dugks_status dugks_adjoint(dugks_ctx* ctx, const void* phi0_dev, long long nstep
             if (q + 1 < ns && (st = dugks_step(ctx, 1)) != DUGKS_OK) { release(); return st; }
         }
         for (long long q = ns - 1; q >= 0; --q) {
-            if ((e = launch_adjoint_step_any(ctx, seg[q], lam[cur], lam[1 - cur], ctx->adj_dalpha)) != cudaSuccess)
+            if ((e = launch_adjoint_step_any(ctx, seg[q], lam[cur], lam[1 - cur], nullptr)) != cudaSuccess)
                 return fail(e, "adjoint step");
             cur ^= 1;
         }
     }
+    if ((e = launch_adj_sum(ctx, ctx->adj_dalpha)) != cudaSuccess) return fail(e, "adjoint sum");
     e = ctx->precision == 32 ? launch_init_adjoint<float>(ctx, phi0_dev, lam[cur], grad_phi0_dev)
                              : launch_init_adjoint<double>(ctx, phi0_dev, lam[cur], grad_phi0_dev);
     if (e != cudaSuccess) return fail(e, "init adjoint");
