@@ -81,7 +81,11 @@ typedef struct {
  * D(phi) = d(phi) I, with b(phi) = sum_{k<nb} b[k] phi^k and
  * d(phi) = sum_{k<nd} d[k] phi^k; alpha > 0 is the diffusion coefficient and
  * fixes the relaxation time lambda = alpha / c_s^2 (Section 3).  The
- * auxiliary moment is C = u u * int_0^phi b'(s)^2 ds, or C = 0 if c_zero. */
+ * auxiliary moment is C = u u * int_0^phi b'(s)^2 ds, or C = 0 if c_zero.
+ * With d_tensor = 1, D is the symmetric tensor [[dxx, dxy], [dxy, dyy]](phi)
+ * (each entry a polynomial with ndt <= 8 coefficients; d and nd are ignored),
+ * as in Examples 4.4 (D = K phi / kappa) and 4.5 (D = diag(phi^nx, phi^ny)).
+ * A zero-initialised tail keeps the isotropic D. */
 typedef struct {
     double u[2];
     int nb;
@@ -90,6 +94,9 @@ typedef struct {
     int nd;
     double d[8];
     int c_zero;
+    int d_tensor;
+    int ndt;
+    double dxx[8], dxy[8], dyy[8];
 } dugks_coef;
 
 typedef struct {
@@ -107,6 +114,8 @@ typedef struct {
     int block_threads;      /* threads per block of the step kernel */
     int grid_blocks;        /* blocks per launch of the step kernel */
     long long state_bytes;  /* bytes of one ftilde buffer (two are held) */
+    double time;            /* time of the current state (source terms only; see dugks_set_source) */
+    int nsrc;               /* source terms set */
 } dugks_info_t;
 
 /* Validate a setup on the host only (no CUDA call).  Returns DUGKS_OK,
@@ -173,6 +182,28 @@ dugks_status dugks_sync(dugks_ctx *ctx);
 
 /* Sizes and launch shape of a context. */
 dugks_status dugks_info(const dugks_ctx *ctx, dugks_info_t *out);
+
+/* ---- source terms ----------------------------------------------------------
+ * Source F of Eq. 2.1 in the form F(x, t, phi) = sum_{k<nterms} exp(rate[k] t)
+ * phi^power[k] S_k(x), S_k sampled at cell centres, with the source
+ * distributions of Eq. 2.3: F_i = w_i F and, as Remark 3 reduces R_i for
+ * B = u b(phi) and C = int B'B' dphi, R_i = w_i c_i.u b'(phi) F / c_s^2.
+ * They enter the interface evolution of Eq. 2.18 and the update of Eq. 2.12;
+ * the time derivatives there are the backward differences (S^n - S^{n-1})/dt
+ * (S^{-1} = S^0 on the first step after dugks_set_source, dugks_init_phi or
+ * dugks_load_state).
+ *
+ * fields_dev: device, [nterms][ny][nx] contiguous, precision's element type,
+ * copied into library-owned memory (the caller may free it after the call
+ * returns; the copy is ordered on the context's stream).  rate, power: host
+ * arrays of nterms; 0 <= power[k] <= 15; nterms in 0..8 (0 removes the
+ * source).  t0 is the time of the current state and of every later
+ * dugks_init_phi; each step advances it by dt (dugks_info_t.time).
+ * Errors: DUGKS_ERR_ARG (bad counts, null pointers, non-finite rates or t0),
+ * DUGKS_ERR_UNSUPPORTED (C = 0, or the naive kernel), DUGKS_ERR_NOMEM.
+ * The adjoint and batched entry points refuse a context with a source. */
+dugks_status dugks_set_source(dugks_ctx *ctx, int nterms, const double *rate, const int *power,
+                              const void *fields_dev, double t0);
 
 /* ---- adjoint (gradients) -------------------------------------------------
  * Discrete adjoint of the step of Section 2 (reverse mode of Eqs. 2.9,

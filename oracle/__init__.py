@@ -13,6 +13,10 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
                         and Cole-Hopf closed forms with second-order
                         convergence, plane-wave decay, conservation,
                         Dirichlet steady states, symmetry
+  sources (step_src)    exact rational stepper with F and R, discrete mass
+                        balance, uniform growth, Examples 4.1 / 4.5 closed forms
+  tensor D              second-moment identity of Eq. 2.7, Example 4.4
+                        anisotropic Gaussian hills
 """
 from __future__ import annotations
 
@@ -49,6 +53,11 @@ class _Problem(ctypes.Structure):
         ("alpha", ctypes.c_double),
         ("nd", ctypes.c_int), ("d", ctypes.c_double * 8),
         ("c_zero", ctypes.c_int), ("dt", ctypes.c_double),
+        ("d_tensor", ctypes.c_int), ("ndt", ctypes.c_int),
+        ("dxx", ctypes.c_double * 8), ("dxy", ctypes.c_double * 8), ("dyy", ctypes.c_double * 8),
+        ("t0", ctypes.c_double),
+        ("nsrc", ctypes.c_int), ("src_rate", ctypes.c_double * 8), ("src_pow", ctypes.c_int * 8),
+        ("src_field", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -72,6 +81,10 @@ def lib():
         L.oracle_max_threads.restype = ctypes.c_int
         L.oracle_equilibrium_deriv.argtypes = [P, ctypes.c_double, dp]
         L.oracle_adjoint_step.argtypes = [P, dp, dp, dp, dp]
+        L.oracle_step_src.argtypes = [P, dp, dp, ctypes.c_double, dp, dp, dp, dp, ctypes.c_int]
+        L.oracle_source.argtypes = [P, ctypes.c_long, ctypes.c_double, ctypes.c_double]
+        L.oracle_source.restype = ctypes.c_double
+        L.oracle_source_distributions.argtypes = [P, ctypes.c_double, ctypes.c_double, dp, dp]
         _lib = L
     return _lib
 
@@ -108,6 +121,29 @@ class Oracle:
             s.d[k] = float(v)
         s.c_zero = int(bool(problem.c_zero))
         s.dt = float(problem.dt)
+        if problem.d_tensor is not None:
+            dt3 = [tuple(map(float, x)) for x in problem.d_tensor]
+            ndt = max(len(x) for x in dt3)
+            if len(dt3) != 3 or ndt > 8:
+                raise ValueError("d_tensor = (dxx, dxy, dyy), at most 8 coefficients each")
+            s.d_tensor, s.ndt = 1, ndt
+            for arr, x in zip((s.dxx, s.dxy, s.dyy), dt3):
+                for k, v in enumerate(x):
+                    arr[k] = v
+        s.t0 = float(problem.t0)
+        src = tuple(problem.source)
+        if len(src) > 8:
+            raise ValueError("at most 8 source terms")
+        self._src = None
+        if src:
+            self._src = np.ascontiguousarray(np.stack([np.asarray(t.field, dtype=np.float64) for t in src]))
+            if self._src.shape[1:] != (s.ny, s.nx):
+                raise ValueError("source fields must be [ny][nx]")
+            s.nsrc = len(src)
+            for k, t in enumerate(src):
+                s.src_rate[k] = float(t.rate)
+                s.src_pow[k] = int(t.power)
+            s.src_field = _ptr(self._src)
         self.s = s
         self.L = lib()
         self.nx, self.ny = s.nx, s.ny
@@ -158,6 +194,34 @@ class Oracle:
         if rc != 0:
             raise RuntimeError(f"oracle_run failed ({rc})")
         return f
+
+    def step_src(self, f: np.ndarray, t: float, R_prev=None, F_prev=None, threads: int = 0):
+        """One step with sources at time t given R_i^{n-1}, F_i^{n-1} (None on the
+        first step); returns (f^{n+1}, R_i^n, F_i^n), all [Q][ny][nx]."""
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        out, R, F = np.empty_like(f), np.empty_like(f), np.empty_like(f)
+        null = ctypes.POINTER(ctypes.c_double)()
+        rp = _ptr(np.ascontiguousarray(R_prev, dtype=np.float64)) if R_prev is not None else null
+        fp = _ptr(np.ascontiguousarray(F_prev, dtype=np.float64)) if F_prev is not None else null
+        keep = (R_prev, F_prev)  # noqa: F841
+        rc = self.L.oracle_step_src(ctypes.byref(self.s), _ptr(f), _ptr(out), float(t), rp, fp, _ptr(R), _ptr(F),
+                                    int(threads))
+        if rc != 0:
+            raise RuntimeError(f"oracle_step_src failed ({rc})")
+        return out, R, F
+
+    def source(self, phi: np.ndarray, t: float) -> np.ndarray:
+        """F(x_c, t, phi) at every cell (Eq. 2.1 source)."""
+        phi = np.asarray(phi, dtype=np.float64)
+        out = np.empty((self.ny, self.nx))
+        for c in range(self.nx * self.ny):
+            out.flat[c] = self.L.oracle_source(ctypes.byref(self.s), c, float(t), float(phi.flat[c]))
+        return out
+
+    def source_distributions(self, phi: float, F: float):
+        R, Fi = np.zeros(Q), np.zeros(Q)
+        self.L.oracle_source_distributions(ctypes.byref(self.s), float(phi), float(F), _ptr(R), _ptr(Fi))
+        return R, Fi
 
     def adjoint_step(self, f: np.ndarray, mu: np.ndarray):
         """(lam, dJ/dalpha) for one step at state f given mu = dJ/d f^{n+1}."""

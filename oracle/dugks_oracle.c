@@ -14,10 +14,12 @@
  *   2. feq_i(phi)                                         (Eq. 2.3)
  *   3. fbp = fbar^+ (Eq. 2.21) and ftp = ftilde^+ (Eq. 2.13)
  *   4. ghost / halo cells (periodic wrap, or the Dirichlet reading below)
- *   5. x-faces: value and slopes (Eqs. 2.19, 2.20), fbar at x_b (Eq. 2.26),
- *      phi_b = sum_i fbar_i, feq(phi_b), f at the face (Eq. 2.22), flux (Eq. 2.9)
+ *   5. x-faces: value and slopes (Eqs. 2.19, 2.20), fbar at x_b (Eq. 2.26,
+ *      or Eq. 2.18 with sources), phi_b = sum_i fbar_i, feq(phi_b), f at the
+ *      face (Eq. 2.22), flux (Eq. 2.9)
  *   6. y-faces likewise
- *   7. cell update ft^{n+1} = ftp - dt/|V| J (Eq. 2.12 without sources)
+ *   7. cell update ft^{n+1} = ftp - dt/|V| J (Eq. 2.12, with its source terms
+ *      when a source F is given)
  *
  * Readings of points the paper leaves open (all shared with the CUDA path,
  * never its code):
@@ -26,7 +28,16 @@
  *     w_5..w_8 = 1/36.
  *   - lambda = alpha / c_s^2 (Chapman-Enskog result, Section 3), h = dt/2.
  *   - The auxiliary moment C = u u * int_0^phi b'(s)^2 ds (Remark 3) for
- *     B = u b(phi), or C = 0 when requested; D = d(phi) I.
+ *     B = u b(phi), or C = 0 when requested; D = d(phi) I, or a symmetric
+ *     tensor with polynomial entries [[dxx, dxy], [dxy, dyy]](phi).
+ *   - Source F(x, t, phi) = sum_k exp(rate_k t) phi^pow_k S_k(x), S_k sampled
+ *     at cell centres.  R_i follows Remark 3 (B = B(phi), C = int B'B' dphi):
+ *     R_i = w_i c_i . B'(phi) F / c_s^2; sources are refused with C = 0.
+ *   - The time derivatives of R_i and F_i in Eqs. 2.12 and 2.18 use the
+ *     backward difference (S^n - S^{n-1}) / dt (the explicit form the text
+ *     after Eq. 2.13 describes); on the first step S^{-1} = S^0.
+ *   - At a Dirichlet wall the ghost cell's source distributions equal those
+ *     of the interior cell next to it.
  *   - 2-D reconstruction at an x-face between cells j and j+1 (Eq. 2.20 is
  *     only given in 1-D): normal slope g_n = (P_{j+1}-P_j)/(x_{j+1}-x_j),
  *     value P_j + (x_b-x_j) g_n, tangential slope g_t = (1-w) G_j + w G_{j+1}
@@ -78,6 +89,14 @@ typedef struct {
     double d[8];      /* D(phi) = d(phi) I, d(phi) = sum_k d[k] phi^k */
     int c_zero;       /* 1: C = 0 instead of u u int b'^2 */
     double dt;
+    int d_tensor;     /* 1: D = [[dxx, dxy], [dxy, dyy]](phi) instead of d(phi) I */
+    int ndt;          /* coefficients in each of dxx, dxy, dyy */
+    double dxx[8], dxy[8], dyy[8];
+    double t0;        /* time of the state given to oracle_step / oracle_run */
+    int nsrc;         /* source terms: F = sum_k exp(rate_k t) phi^pow_k S_k(x) */
+    double src_rate[8];
+    int src_pow[8];
+    const double *src_field; /* [nsrc][ny][nx], S_k at the cell centres */
 } oracle_problem;
 
 /* ------------------------------------------------------------------ */
@@ -106,17 +125,37 @@ static double aux_moment_scalar(const oracle_problem *p, double phi) {
 }
 
 /* Eq. 2.3: feq_i = w_i [phi + c_i.B/cs^2 + (cs^2 D + C - cs^2 phi I):(c_i c_i - cs^2 I)/(2 cs^4)] */
+/* D(phi) as a 2x2 tensor: d(phi) I, or the polynomial tensor entries. */
+static void diffusion_tensor(const oracle_problem *p, double phi, double D[2][2]) {
+    if (p->d_tensor) {
+        D[0][0] = poly(p->ndt, p->dxx, phi);
+        D[0][1] = D[1][0] = poly(p->ndt, p->dxy, phi);
+        D[1][1] = poly(p->ndt, p->dyy, phi);
+    } else {
+        const double dv = poly(p->nd, p->d, phi);
+        D[0][0] = D[1][1] = dv;
+        D[0][1] = D[1][0] = 0.0;
+    }
+}
+
+/* derivative of a polynomial given by n coefficients */
+static double poly_deriv(int n, const double *a, double x) {
+    double s = 0.0, pw = 1.0;
+    for (int k = 1; k < n; k++) { s += k * a[k] * pw; pw *= x; }
+    return s;
+}
+
 void oracle_equilibrium(const oracle_problem *p, double phi, double *feq) {
     const double cs2 = p->c * p->c / 3.0;
     const double bv = poly(p->nb, p->b, phi);
-    const double dv = poly(p->nd, p->d, phi);
     const double cv = p->c_zero ? 0.0 : aux_moment_scalar(p, phi);
-    double B[2], T[2][2];
+    double B[2], T[2][2], D[2][2];
+    diffusion_tensor(p, phi, D);
     for (int a = 0; a < 2; a++) B[a] = p->u[a] * bv;
     for (int a = 0; a < 2; a++)
         for (int e = 0; e < 2; e++) {
             double delta = (a == e) ? 1.0 : 0.0;
-            T[a][e] = cs2 * dv * delta + p->u[a] * p->u[e] * cv - cs2 * phi * delta;
+            T[a][e] = cs2 * D[a][e] + p->u[a] * p->u[e] * cv - cs2 * phi * delta;
         }
     for (int i = 0; i < Q; i++) {
         double ci[2] = {CX[i] * p->c, CY[i] * p->c};
@@ -131,20 +170,26 @@ void oracle_equilibrium(const oracle_problem *p, double phi, double *feq) {
     }
 }
 
-/* d feq_i / d phi, term by term from Eq. 2.3: B' = u b', D' = d' I, C' = u u b'^2. */
+/* d feq_i / d phi, term by term from Eq. 2.3: B' = u b', D' entrywise, C' = u u b'^2. */
 void oracle_equilibrium_deriv(const oracle_problem *p, double phi, double *dfeq) {
     const double cs2 = p->c * p->c / 3.0;
-    double db = 0.0, dd = 0.0, pw = 1.0;
-    for (int k = 1; k < p->nb; k++) { db += k * p->b[k] * pw; pw *= phi; }
-    pw = 1.0;
-    for (int k = 1; k < p->nd; k++) { dd += k * p->d[k] * pw; pw *= phi; }
+    const double db = poly_deriv(p->nb, p->b, phi);
+    double dD[2][2];
+    if (p->d_tensor) {
+        dD[0][0] = poly_deriv(p->ndt, p->dxx, phi);
+        dD[0][1] = dD[1][0] = poly_deriv(p->ndt, p->dxy, phi);
+        dD[1][1] = poly_deriv(p->ndt, p->dyy, phi);
+    } else {
+        dD[0][0] = dD[1][1] = poly_deriv(p->nd, p->d, phi);
+        dD[0][1] = dD[1][0] = 0.0;
+    }
     const double dc = p->c_zero ? 0.0 : db * db;
     double dB[2], dT[2][2];
     for (int a = 0; a < 2; a++) dB[a] = p->u[a] * db;
     for (int a = 0; a < 2; a++)
         for (int e = 0; e < 2; e++) {
             double delta = (a == e) ? 1.0 : 0.0;
-            dT[a][e] = cs2 * dd * delta + p->u[a] * p->u[e] * dc - cs2 * delta;
+            dT[a][e] = cs2 * dD[a][e] + p->u[a] * p->u[e] * dc - cs2 * delta;
         }
     for (int i = 0; i < Q; i++) {
         double ci[2] = {CX[i] * p->c, CY[i] * p->c};
@@ -179,6 +224,27 @@ double oracle_face_original(const oracle_problem *p, const double *fbar, double 
     for (int i = 0; i < Q; i++)
         f[i] = 2.0 * lam / (2.0 * lam + h) * fbar[i] + h / (2.0 * lam + h) * feqb[i];
     return phib;
+}
+
+/* Eq. 2.1 source at cell c: F = sum_k exp(rate_k t) phi^pow_k S_k(x_c). */
+double oracle_source(const oracle_problem *p, long c, double t, double phi) {
+    const size_t n = (size_t)p->nx * p->ny;
+    double s = 0.0;
+    for (int k = 0; k < p->nsrc; k++)
+        s += exp(p->src_rate[k] * t) * pow(phi, (double)p->src_pow[k]) * p->src_field[(size_t)k * n + (size_t)c];
+    return s;
+}
+
+/* Eq. 2.3 source distributions at one cell: F_i = w_i F, and R_i = w_i c_i.(dB/dt + div C)/c_s^2,
+ * which Remark 3 turns into R_i = w_i c_i.B'(phi) F / c_s^2 for B = u b(phi), C = int B'B' dphi. */
+void oracle_source_distributions(const oracle_problem *p, double phi, double F, double *R, double *Fi) {
+    const double cs2 = p->c * p->c / 3.0;
+    const double db = poly_deriv(p->nb, p->b, phi);
+    for (int i = 0; i < Q; i++) {
+        const double ciBp = (CX[i] * p->c * p->u[0] + CY[i] * p->c * p->u[1]) * db;
+        R[i] = WT[i] * ciBp * F / cs2;
+        Fi[i] = WT[i] * F;
+    }
 }
 
 /* ------------------------------------------------------------------ */
@@ -231,6 +297,10 @@ typedef struct {
     double *ftp;          /* [Q][ny][nx] */
     double *fx;           /* x-face flux c_ix f_i: [Q][ny][nx+1] */
     double *fy;           /* y-face flux c_iy f_i: [Q][ny+1][nx] */
+    /* with sources: */
+    double *sr, *sf;      /* R_i + h/2 dR_i/dt and F_i + h/2 dF_i/dt: [Q][ey][ex] with halo */
+    double *rn, *fn;      /* R_i^n and F_i^n: [Q][ny][nx] */
+    double *rp, *fp;      /* R_i^{n-1} and F_i^{n-1} (history kept by oracle_run) */
 } workspace;
 
 static int ws_alloc(workspace *w, const oracle_problem *p) {
@@ -249,6 +319,15 @@ static int ws_alloc(workspace *w, const oracle_problem *p) {
     w->fx = malloc(sizeof(double) * Q * (size_t)p->ny * (p->nx + 1));
     w->fy = malloc(sizeof(double) * Q * (size_t)(p->ny + 1) * p->nx);
     if (!w->xc || !w->yc || !w->phi || !w->feq || !w->fbp || !w->ftp || !w->fx || !w->fy) return -1;
+    if (p->nsrc > 0) {
+        w->sr = malloc(sizeof(double) * Q * ne);
+        w->sf = malloc(sizeof(double) * Q * ne);
+        w->rn = malloc(sizeof(double) * Q * n);
+        w->fn = malloc(sizeof(double) * Q * n);
+        w->rp = malloc(sizeof(double) * Q * n);
+        w->fp = malloc(sizeof(double) * Q * n);
+        if (!w->sr || !w->sf || !w->rn || !w->fn || !w->rp || !w->fp) return -1;
+    }
     /* extended centre coordinates: interior centres are face midpoints; ghost
      * centres are periodic images or mirror images across the wall. */
     const double Lx = p->xf[p->nx] - p->xf[0], Ly = p->yf[p->ny] - p->yf[0];
@@ -274,9 +353,12 @@ static int ws_alloc(workspace *w, const oracle_problem *p) {
 static void ws_free(workspace *w) {
     free(w->xc); free(w->yc); free(w->phi); free(w->feq);
     free(w->fbp); free(w->ftp); free(w->fx); free(w->fy);
+    free(w->sr); free(w->sf); free(w->rn); free(w->fn); free(w->rp); free(w->fp);
 }
 
-#define EXT(w, i, k, j) ((w)->fbp[((size_t)(i) * (w)->ey + (size_t)(k)) * (w)->ex + (size_t)(j)])
+/* element (i, k, j) of an extended [Q][ey][ex] array */
+#define EXTA(w, X, i, k, j) ((X)[((size_t)(i) * (w)->ey + (size_t)(k)) * (w)->ex + (size_t)(j)])
+#define EXT(w, i, k, j) EXTA(w, (w)->fbp, i, k, j)
 
 /* NEE ghost of the reading above: interior cell (ji, ki) in extended
  * indices, ghost at (jg, kg), wall value phiw. */
@@ -327,28 +409,91 @@ static void fill_halo(const oracle_problem *p, workspace *w) {
         }
 }
 
-/* Central difference of fbar^+ in y at extended cell (j, k), velocity i. */
-static double grad_y(const workspace *w, int i, int k, int j) {
-    return (EXT(w, i, k + 1, j) - EXT(w, i, k - 1, j)) / (w->yc[k + 1] - w->yc[k - 1]);
+/* Central difference of an extended array X in y at extended cell (j, k), velocity i. */
+static double grad_y(const workspace *w, const double *X, int i, int k, int j) {
+    return (EXTA(w, X, i, k + 1, j) - EXTA(w, X, i, k - 1, j)) / (w->yc[k + 1] - w->yc[k - 1]);
 }
-static double grad_x(const workspace *w, int i, int k, int j) {
-    return (EXT(w, i, k, j + 1) - EXT(w, i, k, j - 1)) / (w->xc[j + 1] - w->xc[j - 1]);
+static double grad_x(const workspace *w, const double *X, int i, int k, int j) {
+    return (EXTA(w, X, i, k, j + 1) - EXTA(w, X, i, k, j - 1)) / (w->xc[j + 1] - w->xc[j - 1]);
 }
 
-static void step_ws(const oracle_problem *p, workspace *w, const double *f_in, double *f_out,
-                    int nthreads) {
+/* Eqs. 2.19 and 2.20 at x-face jf (between extended cells jf and jf+1) of row ke:
+ * X(x_b - c_i h) = X(x_b) - h c_i . grad X(x_b), for the extended array X. */
+static double recon_xface(const oracle_problem *p, const workspace *w, const double *X, int i, int ke, int jf) {
+    const int jl = jf, jr = jf + 1, xper = p->bc[WALL_W] == BC_PERIODIC;
+    const double h = 0.5 * p->dt, xb = p->xf[jf];
+    const double dxc = w->xc[jr] - w->xc[jl];
+    const double wgt = (xb - w->xc[jl]) / dxc;
+    const double gn = (EXTA(w, X, i, ke, jr) - EXTA(w, X, i, ke, jl)) / dxc; /* Eq. 2.20 slope */
+    const double val = EXTA(w, X, i, ke, jl) + (xb - w->xc[jl]) * gn;        /* Eq. 2.20 value */
+    double gt;
+    if (!xper && jf == 0)
+        gt = grad_y(w, X, i, ke, jr); /* west wall: interior cell only */
+    else if (!xper && jf == p->nx)
+        gt = grad_y(w, X, i, ke, jl); /* east wall */
+    else
+        gt = (1.0 - wgt) * grad_y(w, X, i, ke, jl) + wgt * grad_y(w, X, i, ke, jr);
+    return val - h * (CX[i] * p->c * gn + CY[i] * p->c * gt);
+}
+
+/* y-face kf (between extended rows kf and kf+1) of column je, likewise. */
+static double recon_yface(const oracle_problem *p, const workspace *w, const double *X, int i, int kf, int je) {
+    const int kl = kf, kr = kf + 1, yper = p->bc[WALL_S] == BC_PERIODIC;
+    const double h = 0.5 * p->dt, yb = p->yf[kf];
+    const double dyc = w->yc[kr] - w->yc[kl];
+    const double wgt = (yb - w->yc[kl]) / dyc;
+    const double gn = (EXTA(w, X, i, kr, je) - EXTA(w, X, i, kl, je)) / dyc;
+    const double val = EXTA(w, X, i, kl, je) + (yb - w->yc[kl]) * gn;
+    double gt;
+    if (!yper && kf == 0)
+        gt = grad_x(w, X, i, kr, je);
+    else if (!yper && kf == p->ny)
+        gt = grad_x(w, X, i, kl, je);
+    else
+        gt = (1.0 - wgt) * grad_x(w, X, i, kl, je) + wgt * grad_x(w, X, i, kr, je);
+    return val - h * (CX[i] * p->c * gt + CY[i] * p->c * gn);
+}
+
+/* Halo of a source array: periodic images, or at a Dirichlet wall a copy of
+ * the interior cell next to it (the reading in the header). */
+static void fill_source_halo(const oracle_problem *p, workspace *w, double *X) {
+    const int nx = p->nx, ny = p->ny;
+    const int xper = p->bc[WALL_W] == BC_PERIODIC, yper = p->bc[WALL_S] == BC_PERIODIC;
+    for (int i = 0; i < Q; i++) {
+        for (int j = 1; j <= nx; j++) {
+            EXTA(w, X, i, 0, j) = EXTA(w, X, i, yper ? ny : 1, j);
+            EXTA(w, X, i, ny + 1, j) = EXTA(w, X, i, yper ? 1 : ny, j);
+        }
+        for (int k = 0; k <= ny + 1; k++) {
+            EXTA(w, X, i, k, 0) = EXTA(w, X, i, k, xper ? nx : 1);
+            EXTA(w, X, i, k, nx + 1) = EXTA(w, X, i, k, xper ? 1 : nx);
+        }
+        if (!xper && !yper) {
+            EXTA(w, X, i, 0, 0) = NAN;
+            EXTA(w, X, i, 0, nx + 1) = NAN;
+            EXTA(w, X, i, ny + 1, 0) = NAN;
+            EXTA(w, X, i, ny + 1, nx + 1) = NAN;
+        }
+    }
+}
+
+/* One step at time t.  With sources, R_prev / F_prev hold R_i^{n-1}, F_i^{n-1}
+ * ([Q][ny][nx]; NULL on the first step) and R_i^n, F_i^n are left in w->rn, w->fn. */
+static void step_ws(const oracle_problem *p, workspace *w, const double *f_in, double *f_out, double t,
+                    const double *R_prev, const double *F_prev, int nthreads) {
     const int nx = p->nx, ny = p->ny;
     const size_t n = (size_t)nx * ny;
-    const double h = 0.5 * p->dt;
+    const double h = 0.5 * p->dt, dt = p->dt;
     const double lam = relax_time(p);
-    (void)lam;
+    const int src = p->nsrc > 0;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #else
     (void)nthreads;
 #endif
 
-    /* 1-3: phi, feq, fbar^+, ftilde^+ per cell */
+    /* 1-3: phi, feq, fbar^+, ftilde^+ per cell; with sources also F, R_i, F_i (Eq. 2.3)
+     * and their interface combinations S_i + h/2 dS_i/dt (Eq. 2.18) */
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < ny; k++)
         for (int j = 0; j < nx; j++) {
@@ -363,32 +508,38 @@ static void step_ws(const oracle_problem *p, workspace *w, const double *f_in, d
                 w->ftp[i * n + c] = ftp[i];
                 EXT(w, i, k + 1, j + 1) = fbp[i];
             }
+            if (src) {
+                double R[Q], Fi[Q];
+                oracle_source_distributions(p, phi, oracle_source(p, (long)c, t, phi), R, Fi);
+                for (int i = 0; i < Q; i++) {
+                    const double Rp = R_prev ? R_prev[i * n + c] : R[i];
+                    const double Fp = F_prev ? F_prev[i * n + c] : Fi[i];
+                    w->rn[i * n + c] = R[i];
+                    w->fn[i * n + c] = Fi[i];
+                    EXTA(w, w->sr, i, k + 1, j + 1) = R[i] + 0.5 * h * (R[i] - Rp) / dt;
+                    EXTA(w, w->sf, i, k + 1, j + 1) = Fi[i] + 0.5 * h * (Fi[i] - Fp) / dt;
+                }
+            }
         }
     /* 4: ghosts */
     fill_halo(p, w);
-    const int xper = p->bc[WALL_W] == BC_PERIODIC, yper = p->bc[WALL_S] == BC_PERIODIC;
+    if (src) {
+        fill_source_halo(p, w, w->sr);
+        fill_source_halo(p, w, w->sf);
+    }
+    /* weight of R in Eq. 2.18 */
+    const double wr = 2.0 * lam * h / (2.0 * lam + h);
 
     /* 5: x-faces jf = 0..nx between extended cells jf (left) and jf+1 (right) */
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < ny; k++)
         for (int jf = 0; jf <= nx; jf++) {
-            const int jl = jf, jr = jf + 1, ke = k + 1;
-            const double xb = p->xf[jf];
-            const double dxc = w->xc[jr] - w->xc[jl];
-            const double wgt = (xb - w->xc[jl]) / dxc;
             double fbar[Q], f[Q];
             for (int i = 0; i < Q; i++) {
-                double gn = (EXT(w, i, ke, jr) - EXT(w, i, ke, jl)) / dxc;     /* Eq. 2.20 slope */
-                double val = EXT(w, i, ke, jl) + (xb - w->xc[jl]) * gn;        /* Eq. 2.20 value */
-                double gt;
-                if (!xper && jf == 0)
-                    gt = grad_y(w, i, ke, jr);           /* west wall: interior cell only */
-                else if (!xper && jf == nx)
-                    gt = grad_y(w, i, ke, jl);           /* east wall */
-                else
-                    gt = (1.0 - wgt) * grad_y(w, i, ke, jl) + wgt * grad_y(w, i, ke, jr);
                 /* Eq. 2.19 + Eq. 2.26: fbar(x_b, t+h) = fbar^+(x_b) - h c_i . grad fbar^+(x_b) */
-                fbar[i] = val - h * (CX[i] * p->c * gn + CY[i] * p->c * gt);
+                fbar[i] = recon_xface(p, w, w->fbp, i, k + 1, jf);
+                /* Eq. 2.18: + 2lh/(2l+h) [R_i + h/2 dR_i/dt] + h [F_i + h/2 dF_i/dt] at x_b - c_i h */
+                if (src) fbar[i] += wr * recon_xface(p, w, w->sr, i, k + 1, jf) + h * recon_xface(p, w, w->sf, i, k + 1, jf);
             }
             oracle_face_original(p, fbar, f);
             for (int i = 0; i < Q; i++)
@@ -399,29 +550,18 @@ static void step_ws(const oracle_problem *p, workspace *w, const double *f_in, d
 #pragma omp parallel for schedule(static)
     for (int kf = 0; kf <= ny; kf++)
         for (int j = 0; j < nx; j++) {
-            const int kl = kf, kr = kf + 1, je = j + 1;
-            const double yb = p->yf[kf];
-            const double dyc = w->yc[kr] - w->yc[kl];
-            const double wgt = (yb - w->yc[kl]) / dyc;
             double fbar[Q], f[Q];
             for (int i = 0; i < Q; i++) {
-                double gn = (EXT(w, i, kr, je) - EXT(w, i, kl, je)) / dyc;
-                double val = EXT(w, i, kl, je) + (yb - w->yc[kl]) * gn;
-                double gt;
-                if (!yper && kf == 0)
-                    gt = grad_x(w, i, kr, je);
-                else if (!yper && kf == ny)
-                    gt = grad_x(w, i, kl, je);
-                else
-                    gt = (1.0 - wgt) * grad_x(w, i, kl, je) + wgt * grad_x(w, i, kr, je);
-                fbar[i] = val - h * (CX[i] * p->c * gt + CY[i] * p->c * gn);
+                fbar[i] = recon_yface(p, w, w->fbp, i, kf, j + 1);
+                if (src) fbar[i] += wr * recon_yface(p, w, w->sr, i, kf, j + 1) + h * recon_yface(p, w, w->sf, i, kf, j + 1);
             }
             oracle_face_original(p, fbar, f);
             for (int i = 0; i < Q; i++)
                 w->fy[((size_t)i * (ny + 1) + kf) * nx + j] = CY[i] * p->c * f[i];
         }
 
-    /* 7: cell update, Eq. 2.12 with J = sum over faces of (c_i . n) f_i |S| */
+    /* 7: cell update, Eq. 2.12 with J = sum over faces of (c_i . n) f_i |S|, plus
+     * dt (S_i^n + dt/2 dS_i/dt) for S = R, F with dS/dt = (S^n - S^{n-1}) / dt */
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < ny; k++)
         for (int j = 0; j < nx; j++) {
@@ -434,28 +574,54 @@ static void step_ws(const oracle_problem *p, workspace *w, const double *f_in, d
                 double fn = w->fy[((size_t)i * (ny + 1) + k + 1) * nx + j];
                 double fs = w->fy[((size_t)i * (ny + 1) + k) * nx + j];
                 double J = (fe - fw) * dyk + (fn - fs) * dxj;
-                f_out[i * n + c] = w->ftp[i * n + c] - p->dt / area * J;
+                double v = w->ftp[i * n + c] - p->dt / area * J;
+                if (src) {
+                    const double R = w->rn[i * n + c], Fi = w->fn[i * n + c];
+                    const double Rp = R_prev ? R_prev[i * n + c] : R;
+                    const double Fp = F_prev ? F_prev[i * n + c] : Fi;
+                    v += dt * (R + 0.5 * dt * (R - Rp) / dt) + dt * (Fi + 0.5 * dt * (Fi - Fp) / dt);
+                }
+                f_out[i * n + c] = v;
             }
         }
 }
 
 static int valid(const oracle_problem *p) {
     if (p->nx <= 0 || p->ny <= 0 || p->nb > 8 || p->nd > 8 || p->nb < 0 || p->nd < 0) return 0;
+    if (p->d_tensor && (p->ndt < 0 || p->ndt > 8)) return 0;
+    if (p->nsrc < 0 || p->nsrc > 8 || (p->nsrc > 0 && (!p->src_field || p->c_zero))) return 0;
     if ((p->bc[WALL_W] == BC_PERIODIC) != (p->bc[WALL_E] == BC_PERIODIC)) return 0;
     if ((p->bc[WALL_S] == BC_PERIODIC) != (p->bc[WALL_N] == BC_PERIODIC)) return 0;
     return p->alpha > 0.0 && p->c > 0.0 && p->dt > 0.0;
 }
 
+/* One step of the state at time p->t0 (with sources: the first step, no history). */
 int oracle_step(const oracle_problem *p, const double *f_in, double *f_out, int nthreads) {
     workspace ws;
     if (!valid(p)) return -2;
     if (ws_alloc(&ws, p) != 0) { ws_free(&ws); return -1; }
-    step_ws(p, &ws, f_in, f_out, nthreads);
+    step_ws(p, &ws, f_in, f_out, p->t0, NULL, NULL, nthreads);
     ws_free(&ws);
     return 0;
 }
 
-/* n steps in place on f (ping-pong through a scratch copy). */
+/* One step with sources at time t, given R_i^{n-1}, F_i^{n-1} (NULL: first step);
+ * R_i^n, F_i^n are written to R_out, F_out ([Q][ny][nx]). */
+int oracle_step_src(const oracle_problem *p, const double *f_in, double *f_out, double t, const double *R_prev,
+                    const double *F_prev, double *R_out, double *F_out, int nthreads) {
+    workspace ws;
+    if (!valid(p) || p->nsrc <= 0) return -2;
+    if (ws_alloc(&ws, p) != 0) { ws_free(&ws); return -1; }
+    step_ws(p, &ws, f_in, f_out, t, R_prev, F_prev, nthreads);
+    const size_t sz = sizeof(double) * Q * (size_t)p->nx * p->ny;
+    memcpy(R_out, ws.rn, sz);
+    memcpy(F_out, ws.fn, sz);
+    ws_free(&ws);
+    return 0;
+}
+
+/* n steps in place on f from time p->t0 (ping-pong through a scratch copy);
+ * with sources the R, F history starts at the first step. */
 int oracle_run(const oracle_problem *p, double *f, long nsteps, int nthreads) {
     const size_t sz = sizeof(double) * Q * (size_t)p->nx * p->ny;
     workspace ws;
@@ -463,8 +629,13 @@ int oracle_run(const oracle_problem *p, double *f, long nsteps, int nthreads) {
     double *tmp = malloc(sz);
     if (!tmp || ws_alloc(&ws, p) != 0) { free(tmp); ws_free(&ws); return -1; }
     for (long s = 0; s < nsteps; s++) {
-        step_ws(p, &ws, f, tmp, nthreads);
+        const int hist = p->nsrc > 0 && s > 0;
+        step_ws(p, &ws, f, tmp, p->t0 + (double)s * p->dt, hist ? ws.rp : NULL, hist ? ws.fp : NULL, nthreads);
         memcpy(f, tmp, sz);
+        if (p->nsrc > 0) {
+            memcpy(ws.rp, ws.rn, sz);
+            memcpy(ws.fp, ws.fn, sz);
+        }
     }
     ws_free(&ws);
     free(tmp);
@@ -493,7 +664,7 @@ int oracle_max_threads(void) {
  */
 int oracle_adjoint_step(const oracle_problem *p, const double *f_in, const double *mu, double *lam,
                         double *dj_dalpha) {
-    if (!valid(p)) return -2;
+    if (!valid(p) || p->nsrc > 0) return -2; /* the adjoint covers the step without sources */
     workspace ws, *w = &ws;
     if (ws_alloc(w, p) != 0) { ws_free(w); return -1; }
     const int nx = p->nx, ny = p->ny, ex = nx + 2, ey = ny + 2;
@@ -542,9 +713,9 @@ int oracle_adjoint_step(const oracle_problem *p, const double *f_in, const doubl
                 double gn = (EXT(w, i, ke, jr) - EXT(w, i, ke, jl)) / dxc;
                 double val = EXT(w, i, ke, jl) + (xb - w->xc[jl]) * gn;
                 double gt;
-                if (wallW) gt = grad_y(w, i, ke, jr);
-                else if (wallE) gt = grad_y(w, i, ke, jl);
-                else gt = (1.0 - wgt) * grad_y(w, i, ke, jl) + wgt * grad_y(w, i, ke, jr);
+                if (wallW) gt = grad_y(w, w->fbp, i, ke, jr);
+                else if (wallE) gt = grad_y(w, w->fbp, i, ke, jl);
+                else gt = (1.0 - wgt) * grad_y(w, w->fbp, i, ke, jl) + wgt * grad_y(w, w->fbp, i, ke, jr);
                 fbar[i] = val - h * (CX[i] * p->c * gn + CY[i] * p->c * gt);
                 gtl[i] = wallW ? 0.0 : (wallE ? 1.0 : 1.0 - wgt); /* weight of the left G */
                 gtr[i] = wallE ? 0.0 : (wallW ? 1.0 : wgt);       /* weight of the right G */
@@ -594,9 +765,9 @@ int oracle_adjoint_step(const oracle_problem *p, const double *f_in, const doubl
                 double gn = (EXT(w, i, kr, je) - EXT(w, i, kl, je)) / dyc;
                 double val = EXT(w, i, kl, je) + (yb - w->yc[kl]) * gn;
                 double gt;
-                if (wallS) gt = grad_x(w, i, kr, je);
-                else if (wallN) gt = grad_x(w, i, kl, je);
-                else gt = (1.0 - wgt) * grad_x(w, i, kl, je) + wgt * grad_x(w, i, kr, je);
+                if (wallS) gt = grad_x(w, w->fbp, i, kr, je);
+                else if (wallN) gt = grad_x(w, w->fbp, i, kl, je);
+                else gt = (1.0 - wgt) * grad_x(w, w->fbp, i, kl, je) + wgt * grad_x(w, w->fbp, i, kr, je);
                 fbar[i] = val - h * (CX[i] * p->c * gt + CY[i] * p->c * gn);
                 gtl[i] = wallS ? 0.0 : (wallN ? 1.0 : 1.0 - wgt);
                 gtr[i] = wallN ? 0.0 : (wallS ? 1.0 : wgt);

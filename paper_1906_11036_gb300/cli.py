@@ -21,7 +21,9 @@ import numpy as np
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(prog="python -m paper_1906_11036_gb300.cli")
-    ap.add_argument("--workload", default="nonuniform", choices=["gaussian_hill", "burgers", "nonuniform"])
+    from . import inputs as _inputs
+
+    ap.add_argument("--workload", default="nonuniform", choices=sorted(_inputs.PRESETS))
     ap.add_argument("--n", type=int, default=None, help="cells per side (default: the preset's)")
     ap.add_argument("--steps", type=int, default=None, help="time steps (default: the preset's)")
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])

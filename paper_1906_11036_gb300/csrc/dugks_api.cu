@@ -72,6 +72,20 @@ struct dugks_ctx {
     void* adj_phi = nullptr;  // forward phi [ny][nx]
     double* adj_partial = nullptr;
     double* adj_dalpha = nullptr;
+    // source terms (dugks_set_source)
+    double ux = 0, uy = 0;
+    int nb = 0;
+    double bcoef[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int c_zero = 0;
+    int nsrc = 0;
+    double src_rate[8];
+    int src_power[8];
+    void* src_field = nullptr;            // S_k [nsrc][ny][nx], precision's type
+    void* hist[2] = {nullptr, nullptr};   // phi^{n-1} (read) / phi^n (written), alternating with cur
+    bool src_first = true;
+    double t = 0, t0 = 0;   // time of the state; source start time
+    double tbase = 0;       // t = tbase + tsteps * dt (tbase set by set_source, init_phi, load_state)
+    long long tsteps = 0;
     std::string last_error;
 };
 
@@ -309,10 +323,46 @@ dugks_status plan_fused(dugks_ctx* ctx) {
     return DUGKS_OK;
 }
 
+// Launch arguments of the source terms for the step from ctx->t (Eqs. 2.3, 2.12, 2.18).
+template <typename T>
+SrcArgs<T> make_src_args(const dugks_ctx* ctx) {
+    SrcArgs<T> sa{};
+    sa.nterms = ctx->nsrc;
+    sa.first = ctx->src_first ? 1 : 0;
+    for (int q = 0; q < ctx->nsrc; ++q) {
+        sa.power[q] = ctx->src_power[q];
+        sa.en[q] = T(std::exp(ctx->src_rate[q] * ctx->t));
+        sa.ep[q] = ctx->src_first ? sa.en[q] : T(std::exp(ctx->src_rate[q] * (ctx->t - ctx->dt)));
+    }
+    sa.ndb = std::max(0, ctx->nb - 1);  // b'(phi) = sum_m (m+1) b_{m+1} phi^m
+    for (int m = 0; m + 1 < ctx->nb; ++m) sa.db[m] = T(double(m + 1) * ctx->bcoef[m + 1]);
+    const double cs2 = ctx->c * ctx->c / 3.0, h = 0.5 * ctx->dt, lam = ctx->lambda;
+    const double wr = 2.0 * lam * h / (2.0 * lam + h);  // weight of R in Eq. 2.18
+    const double wts[Q] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    for (int i = 0; i < Q; ++i) {
+        const double cu = ctx->c * (EX(i) * ctx->ux + EY(i) * ctx->uy) / cs2;  // c_i.u / c_s^2
+        sa.kP_g[i] = T(wr * wts[i] * cu);
+        sa.kP_f[i] = T(h * wts[i]);
+        sa.kU_g[i] = T(ctx->dt * wts[i] * cu);
+        sa.kU_f[i] = T(ctx->dt * wts[i]);
+    }
+    sa.field = static_cast<const T*>(ctx->src_field);
+    sa.fplane = (long long)ctx->nx * ctx->ny;
+    sa.hin = static_cast<const T*>(ctx->hist[ctx->cur]);
+    sa.hout = static_cast<T*>(ctx->hist[ctx->cur ^ 1]);
+    return sa;
+}
+
 template <typename T, int NC>
 cudaError_t launch_step(dugks_ctx* ctx) {
     const StepArgs<T, NC> a = make_args<T, NC>(ctx, ctx->cur);
     const Consts<T, NC> k = make_consts<T, NC>(ctx);
+    if (ctx->nsrc > 0) {  // the scalar fused kernel with the source terms
+        dim3 grid(ctx->nstrips, ctx->nseg);
+        fused_step_src<T, NC><<<grid, 32, fused_smem(ctx), ctx->stream>>>(ctx->tmap[ctx->cur], a, k, ctx->seg_rows,
+                                                                         ctx->stages, make_src_args<T>(ctx));
+        return cudaGetLastError();
+    }
     if (ctx->kernel == DUGKS_KERNEL_NAIVE) {
         dim3 grid((ctx->nx + 127) / 128, std::min(ctx->ny, 65535));
         naive_step<T, NC><<<grid, 128, 0, ctx->stream>>>(a, k);
@@ -369,7 +419,7 @@ void free_ctx(dugks_ctx* ctx) {
     cudaGetDevice(&prev);
     cudaSetDevice(ctx->device);
     for (void* p : {ctx->buf[0], ctx->buf[1], ctx->fxm, ctx->fym, ctx->cxm, ctx->cym, ctx->adj_ax, ctx->adj_ay,
-                    ctx->adj_p, ctx->adj_phi,
+                    ctx->adj_p, ctx->adj_phi, ctx->src_field, ctx->hist[0], ctx->hist[1],
                     static_cast<void*>(ctx->adj_partial), static_cast<void*>(ctx->adj_dalpha)})
         if (p) cudaFree(p);
     for (void* p : {static_cast<void*>(ctx->dxv), static_cast<void*>(ctx->dyv), static_cast<void*>(ctx->staging),
@@ -654,6 +704,11 @@ dugks_status dugks_check_config(const dugks_mesh* mesh, const dugks_vset* vset, 
     if (mesh->nx > (1 << 30) || mesh->ny > (1 << 30)) return DUGKS_ERR_ARG;
     if (vset->kind != DUGKS_D2Q9) return DUGKS_ERR_ARG;
     if (coef->nb < 0 || coef->nb > 8 || coef->nd < 0 || coef->nd > 8) return DUGKS_ERR_ARG;
+    if (coef->d_tensor != 0 && coef->d_tensor != 1) return DUGKS_ERR_ARG;
+    if (coef->d_tensor && (coef->ndt < 0 || coef->ndt > 8)) return DUGKS_ERR_ARG;
+    if (coef->d_tensor &&
+        (!finite_all(coef->dxx, coef->ndt) || !finite_all(coef->dxy, coef->ndt) || !finite_all(coef->dyy, coef->ndt)))
+        return DUGKS_ERR_CONFIG;
     for (int w = 0; w < 4; ++w)
         if (mesh->bc[w] != DUGKS_BC_PERIODIC && mesh->bc[w] != DUGKS_BC_DIRICHLET) return DUGKS_ERR_ARG;
     if ((mesh->bc[0] == DUGKS_BC_PERIODIC) != (mesh->bc[1] == DUGKS_BC_PERIODIC)) return DUGKS_ERR_ARG;
@@ -709,6 +764,11 @@ dugks_status dugks_create(const dugks_mesh* mesh, const dugks_vset* vset, const 
     ctx->yf.assign(mesh->yf, mesh->yf + mesh->ny + 1);
     ctx->c = vset->c;
     ctx->dt = dt;
+    ctx->ux = coef->u[0];
+    ctx->uy = coef->u[1];
+    ctx->nb = coef->nb;
+    for (int m = 0; m < coef->nb; ++m) ctx->bcoef[m] = coef->b[m];
+    ctx->c_zero = coef->c_zero;
     ctx->stream = static_cast<cudaStream_t>(o.stream);
     ctx->elem = ctx->precision == 32 ? sizeof(float) : sizeof(double);
 
@@ -737,16 +797,28 @@ dugks_status dugks_create(const dugks_mesh* mesh, const dugks_vset* vset, const 
     const double wts[Q] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
     const double ux = coef->u[0], uy = coef->u[1], c = vset->c;
     int maxdeg = 1;
+    // A tensor D adds D:(e_i e_i c^2 - c_s^2 I)/(2 c_s^2) = [(3 ex^2 - 1) dxx + 6 ex ey dxy + (3 ey^2 - 1) dyy]/2
+    // in place of (3|e_i|^2 - 2)/2 d; the -phi part keeps the isotropic form.
     for (int i = 0; i < Q; ++i) {
         const double eu = EX(i) * ux + EY(i) * uy;
         const double e2 = double(EX(i) * EX(i) + EY(i) * EY(i));
         const double kb = 3.0 * eu / c, kd = (3.0 * e2 - 2.0) / 2.0;
+        const double kxx = (3.0 * EX(i) * EX(i) - 1.0) / 2.0, kyy = (3.0 * EY(i) * EY(i) - 1.0) / 2.0;
+        const double kxy = 3.0 * EX(i) * EY(i);
         const double kc = (9.0 * eu * eu - 3.0 * (ux * ux + uy * uy)) / (2.0 * c * c);
         for (int m = 0; m < NC_LARGE; ++m) {
             const double bm = m < coef->nb ? coef->b[m] : 0.0;
-            const double dm = m < coef->nd ? coef->d[m] : 0.0;
             const double one = m == 1 ? 1.0 : 0.0;
-            const double v = wts[i] * (one + kb * bm + kd * (dm - one) + kc * cint[m]);
+            double dpart;
+            if (coef->d_tensor) {
+                const double xx = m < coef->ndt ? coef->dxx[m] : 0.0, xy = m < coef->ndt ? coef->dxy[m] : 0.0;
+                const double yy = m < coef->ndt ? coef->dyy[m] : 0.0;
+                dpart = kxx * xx + kxy * xy + kyy * yy - kd * one;
+            } else {
+                const double dm = m < coef->nd ? coef->d[m] : 0.0;
+                dpart = kd * (dm - one);
+            }
+            const double v = wts[i] * (one + kb * bm + dpart + kc * cint[m]);
             ctx->feq_coef[i][m] = v;
             if (v != 0.0) maxdeg = std::max(maxdeg, m);
         }
@@ -842,6 +914,9 @@ dugks_status dugks_init_phi(dugks_ctx* ctx, const void* phi0_dev) {
                                          : launch_init<double, double>(ctx, static_cast<const double*>(phi0_dev));
     CK(e);
     ctx->steps_done = 0;
+    ctx->t = ctx->tbase = ctx->t0;
+    ctx->tsteps = 0;
+    ctx->src_first = true;
     return DUGKS_OK;
 }
 
@@ -855,6 +930,9 @@ dugks_status dugks_init_phi_host(dugks_ctx* ctx, const double* phi0_host) {
     CK(e);
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->steps_done = 0;
+    ctx->t = ctx->tbase = ctx->t0;
+    ctx->tsteps = 0;
+    ctx->src_first = true;
     return DUGKS_OK;
 }
 
@@ -865,6 +943,9 @@ dugks_status dugks_step(dugks_ctx* ctx, long long n) {
         CK(launch_step_any(ctx));
         ctx->cur ^= 1;
         ++ctx->steps_done;
+        ++ctx->tsteps;
+        ctx->t = ctx->tbase + double(ctx->tsteps) * ctx->dt;
+        ctx->src_first = false;
     }
     return DUGKS_OK;
 }
@@ -914,6 +995,9 @@ dugks_status dugks_load_state(dugks_ctx* ctx, const void* f_dev_in) {
     CK(cudaMemcpy2DAsync(ctx->buf[ctx->cur], size_t(ctx->pitch) * ctx->elem, f_dev_in, size_t(ctx->nx) * ctx->elem,
                          size_t(ctx->nx) * ctx->elem, size_t(Q) * ctx->ny, cudaMemcpyDeviceToDevice, ctx->stream));
     ctx->steps_done = 0;
+    ctx->src_first = true;  // the state carries no source history; time is kept
+    ctx->tbase = ctx->t;
+    ctx->tsteps = 0;
     return DUGKS_OK;
 }
 
@@ -951,12 +1035,58 @@ dugks_status dugks_info(const dugks_ctx* ctx, dugks_info_t* out) {
     out->grid_blocks = ctx->kernel == DUGKS_KERNEL_NAIVE ? ((ctx->nx + 127) / 128) * std::min(ctx->ny, 65535)
                                                          : ctx->nstrips * ctx->nseg;
     out->state_bytes = (long long)Q * ctx->plane * (long long)ctx->elem;
+    out->time = ctx->t;
+    out->nsrc = ctx->nsrc;
+    return DUGKS_OK;
+}
+
+dugks_status dugks_set_source(dugks_ctx* ctx, int nterms, const double* rate, const int* power, const void* fields_dev,
+                              double t0) {
+    if (!ctx || nterms < 0 || nterms > 8 || !std::isfinite(t0)) return DUGKS_ERR_ARG;
+    if (nterms > 0 && (!rate || !power || !fields_dev)) return DUGKS_ERR_ARG;
+    for (int q = 0; q < nterms; ++q)
+        if (!std::isfinite(rate[q]) || power[q] < 0 || power[q] > 15) return DUGKS_ERR_ARG;
+    if (nterms > 0 && ctx->c_zero) {
+        ctx->last_error = "source terms need C = int B'B' dphi (Remark 3)";
+        return DUGKS_ERR_UNSUPPORTED;
+    }
+    if (nterms > 0 && ctx->kernel == DUGKS_KERNEL_NAIVE) {
+        ctx->last_error = "source terms run on the fused kernel only";
+        return DUGKS_ERR_UNSUPPORTED;
+    }
+    DeviceGuard guard(ctx->device);
+    const size_t cells = size_t(ctx->nx) * ctx->ny;
+    if (nterms > 0) {
+        CK(cudaStreamSynchronize(ctx->stream));  // the old fields may still be read by queued steps
+        if (ctx->src_field) { cudaFree(ctx->src_field); ctx->src_field = nullptr; }
+        cudaError_t e = cudaMalloc(&ctx->src_field, size_t(nterms) * cells * ctx->elem);
+        if (e != cudaSuccess) { ctx->src_field = nullptr; return cuda_fail(ctx, e, "cudaMalloc(source fields)"); }
+        for (int b = 0; b < 2; ++b)
+            if (!ctx->hist[b]) {
+                e = cudaMalloc(&ctx->hist[b], cells * ctx->elem);
+                if (e != cudaSuccess) { ctx->hist[b] = nullptr; return cuda_fail(ctx, e, "cudaMalloc(source history)"); }
+            }
+        CK(cudaMemcpyAsync(ctx->src_field, fields_dev, size_t(nterms) * cells * ctx->elem, cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        for (int q = 0; q < nterms; ++q) {
+            ctx->src_rate[q] = rate[q];
+            ctx->src_power[q] = power[q];
+        }
+    }
+    ctx->nsrc = nterms;
+    ctx->t0 = ctx->t = ctx->tbase = t0;
+    ctx->tsteps = 0;
+    ctx->src_first = true;
     return DUGKS_OK;
 }
 
 dugks_status dugks_adjoint_step(dugks_ctx* ctx, const void* f_dev, const void* mu_dev, void* lam_dev,
                                 double* dj_dalpha_dev) {
     if (!ctx || !f_dev || !mu_dev || !lam_dev || !dj_dalpha_dev) return DUGKS_ERR_ARG;
+    if (ctx->nsrc > 0) {
+        ctx->last_error = "the adjoint covers the step without source terms";
+        return DUGKS_ERR_UNSUPPORTED;
+    }
     DeviceGuard guard(ctx->device);
     dugks_status st = adj_alloc(ctx);
     if (st != DUGKS_OK) return st;
@@ -968,6 +1098,10 @@ dugks_status dugks_adjoint(dugks_ctx* ctx, const void* phi0_dev, long long nstep
                            const void* grad_phiN_dev, void* grad_phi0_dev, double* grad_alpha_out) {
     if (!ctx || !phi0_dev || !grad_phiN_dev || !grad_phi0_dev || nsteps < 0 || checkpoint_every < 1)
         return DUGKS_ERR_ARG;
+    if (ctx->nsrc > 0) {
+        ctx->last_error = "the adjoint covers the step without source terms";
+        return DUGKS_ERR_UNSUPPORTED;
+    }
     DeviceGuard guard(ctx->device);
     dugks_status st = adj_alloc(ctx);
     if (st != DUGKS_OK) return st;

@@ -36,6 +36,73 @@ struct StepArgs {
     int* err;            // device error word (bit 0: TMA wait timed out)
 };
 
+// Source F(x, t, phi) = sum_k exp(rate_k t) phi^power_k S_k(x) (Eq. 2.1) with
+// R_i = w_i c_i.u b'(phi) F / c_s^2 (Eq. 2.3 as Remark 3 reduces it for
+// C = int B'B' dphi).  The time derivatives in Eqs. 2.12 and 2.18 are the
+// backward differences (S^n - S^{n-1}) / dt, so per cell
+//   at the interface (Eq. 2.18): S + h/2 dS/dt = S^n + (S^n - S^{n-1}) / 4,
+//   in the update    (Eq. 2.12): S + dt/2 dS/dt = (3 S^n - S^{n-1}) / 2.
+// Both enter linearly: the interface term is added to P = fbar^+ before the
+// face reconstruction (Eqs. 2.19, 2.20 are linear and identical for fbar^+,
+// R and F), the update term to Fp = ftilde^+.  S^{n-1} comes from
+// phi^{n-1}, kept in a history buffer.
+template <typename T>
+struct SrcArgs {
+    int nterms;
+    int first;            // 1: no history yet (S^{n-1} = S^n)
+    int power[8];
+    T en[8], ep[8];       // exp(rate_k t_n), exp(rate_k t_{n-1})
+    T db[8];              // b'(phi) coefficients, lowest order first
+    int ndb;
+    T kP_g[Q], kP_f[Q];   // per velocity: 2lh/(2l+h) w_i c_i.u / c_s^2 and h w_i
+    T kU_g[Q], kU_f[Q];   // per velocity: dt w_i c_i.u / c_s^2 and dt w_i
+    const T* field;       // S_k, [nterms][ny][nx] contiguous
+    long long fplane;     // nx * ny
+    const T* hin;         // phi^{n-1} [ny][nx]
+    T* hout;              // phi^n [ny][nx]
+};
+
+// L1 prefetch of the source fields and the history of cell c (a few rows ahead of use)
+template <typename T>
+__device__ __forceinline__ void prefetch_source(const SrcArgs<T>& sa, long long c) {
+    for (int q = 0; q < sa.nterms; ++q)
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(sa.field + q * sa.fplane + c));
+    if (!sa.first) asm volatile("prefetch.global.L1 [%0];" ::"l"(sa.hin + c));
+}
+
+// adds the source terms of cell c (index into the [ny][nx] arrays) with phi^n = phi;
+// S^{n-1} from phi^{n-1} (on the first step the host passes ep = en and phi^{n-1} = phi^n)
+template <typename T>
+__device__ __forceinline__ void add_source(const SrcArgs<T>& sa, long long c, T phi, T (&P)[Q], T (&Fp)[Q],
+                                           bool write_hist) {
+    const T phio = sa.first ? phi : sa.hin[c];
+    if (write_hist) sa.hout[c] = phi;
+    T Fn = T(0), Fo = T(0);
+    for (int q = 0; q < sa.nterms; ++q) {
+        const T S = sa.field[q * sa.fplane + c];
+        T xn = sa.en[q] * S, xo = sa.ep[q] * S;
+        for (int m = 0; m < sa.power[q]; ++m) {
+            xn *= phi;
+            xo *= phio;
+        }
+        Fn += xn;
+        Fo += xo;
+    }
+    T dn = T(0), dO = T(0);  // b'(phi^n), b'(phi^{n-1})
+    for (int m = sa.ndb - 1; m >= 0; --m) {
+        dn = fma(dn, phi, sa.db[m]);
+        dO = fma(dO, phio, sa.db[m]);
+    }
+    const T gn = dn * Fn, go = dO * Fo;
+    const T Ft = Fn + T(0.25) * (Fn - Fo), gt = gn + T(0.25) * (gn - go);
+    const T Fa = T(1.5) * Fn - T(0.5) * Fo, ga = T(1.5) * gn - T(0.5) * go;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        P[i] += fma(sa.kP_g[i], gt, sa.kP_f[i] * Ft);
+        Fp[i] += fma(sa.kU_g[i], ga, sa.kU_f[i] * Fa);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // naive cross-check kernel
 // ---------------------------------------------------------------------------
@@ -197,10 +264,10 @@ __device__ __forceinline__ T hf_i(const Consts<T, NC>& k, int i, T x) {
     return s;
 }
 
-template <typename T, int NC, bool EDGE>
+template <typename T, int NC, bool EDGE, bool SRC>
 __device__ __forceinline__ void warp_rows(const CUtensorMap* tin, const StepArgs<T, NC>& a, const Consts<T, NC>& k,
                                           unsigned char* stages, uint64_t* bars, const int S, const int lane,
-                                          const int xw, const int y0, const int y1) {
+                                          const int xw, const int y0, const int y1, const SrcArgs<T>* sa) {
     using L = WarpLayout<T>;
     const int nx = a.nx, ny = a.ny;
     const int j = xw - 1 + lane;
@@ -294,6 +361,10 @@ __device__ __forceinline__ void warp_rows(const CUtensorMap* tin, const StepArgs
 #pragma unroll
         for (int i = 0; i < Q; ++i) Fp[i] = fma(k.third, P[i] - ft[i], P[i]);
         const bool ghost_row = !a.yper && (r < 0 || r >= ny);
+        if (SRC && !(EDGE && role == ROLE_OUT)) {  // a ghost takes the source of the interior cell it mirrors
+            if (r + 4 <= y1) prefetch_source(*sa, (long long)src_row(r + 4) * nx + scol);
+            add_source(*sa, (long long)src_row(r) * nx + scol, phi, P, Fp, updates && r >= y0 && r < y1);
+        }
         if (ghost_row || ghost_col) {
             const T bv = ghost_col ? bvx : (r < 0 ? k.bcv[2] : k.bcv[3]);
             T fe[Q], fg[Q];
@@ -446,8 +517,32 @@ __global__ void __launch_bounds__(32) fused_step(const __grid_constant__ CUtenso
     }
     __syncwarp();
     const bool edge = xw - 1 < 0 || xw + L::WI >= a.nx;
-    if (edge) warp_rows<T, NC, true>(&tin, a, k, smem, bars, S, lane, xw, y0, y1);
-    else warp_rows<T, NC, false>(&tin, a, k, smem, bars, S, lane, xw, y0, y1);
+    if (edge) warp_rows<T, NC, true, false>(&tin, a, k, smem, bars, S, lane, xw, y0, y1, nullptr);
+    else warp_rows<T, NC, false, false>(&tin, a, k, smem, bars, S, lane, xw, y0, y1, nullptr);
+}
+
+// the fused step with the source terms F and R (same grid and shared memory as fused_step)
+template <typename T, int NC>
+__global__ void __launch_bounds__(32) fused_step_src(const __grid_constant__ CUtensorMap tin, const StepArgs<T, NC> a,
+                                                     const Consts<T, NC> k, const int seg_rows, const int S,
+                                                     const __grid_constant__ SrcArgs<T> sa) {
+    using L = WarpLayout<T>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + size_t(S) * L::STAGE_BYTES);
+    const int lane = threadIdx.x;
+    const int xw = blockIdx.x * L::WI;
+    const int y0 = blockIdx.y * seg_rows;
+    const int y1 = min(y0 + seg_rows, a.ny);
+    if (y0 >= a.ny || xw >= a.nx) return;
+    if (lane == 0) {
+        for (int q = 0; q < S; ++q) mbar_init(&bars[q], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const bool edge = xw - 1 < 0 || xw + L::WI >= a.nx;
+    if (edge) warp_rows<T, NC, true, true>(&tin, a, k, smem, bars, S, lane, xw, y0, y1, &sa);
+    else warp_rows<T, NC, false, true>(&tin, a, k, smem, bars, S, lane, xw, y0, y1, &sa);
 }
 
 // ---------------------------------------------------------------------------

@@ -40,7 +40,8 @@ class VSet(ctypes.Structure):
 class Coef(ctypes.Structure):
     _fields_ = [("u", ctypes.c_double * 2), ("nb", ctypes.c_int), ("b", ctypes.c_double * 8),
                 ("alpha", ctypes.c_double), ("nd", ctypes.c_int), ("d", ctypes.c_double * 8),
-                ("c_zero", ctypes.c_int)]
+                ("c_zero", ctypes.c_int), ("d_tensor", ctypes.c_int), ("ndt", ctypes.c_int),
+                ("dxx", ctypes.c_double * 8), ("dxy", ctypes.c_double * 8), ("dyy", ctypes.c_double * 8)]
 
 
 class Options(ctypes.Structure):
@@ -52,7 +53,8 @@ class Info(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("pitch", ctypes.c_longlong), ("steps_done", ctypes.c_longlong), ("dt", ctypes.c_double),
                 ("lam", ctypes.c_double), ("cfl", ctypes.c_double), ("block_threads", ctypes.c_int),
-                ("grid_blocks", ctypes.c_int), ("state_bytes", ctypes.c_longlong)]
+                ("grid_blocks", ctypes.c_int), ("state_bytes", ctypes.c_longlong), ("time", ctypes.c_double),
+                ("nsrc", ctypes.c_int)]
 
 
 _lib = None
@@ -80,6 +82,7 @@ def library():
         L.dugks_sync.argtypes = [vp]
         L.dugks_info.argtypes = [vp, P(Info)]
         L.dugks_adjoint_step.argtypes = [vp, vp, vp, vp, vp]
+        L.dugks_set_source.argtypes = [vp, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int), vp, ctypes.c_double]
         L.dugks_adjoint.argtypes = [vp, vp, ctypes.c_longlong, ctypes.c_int, vp, vp, P(ctypes.c_double)]
         L.dugks_phi_mass_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp]
         L.dugks_batch_create.argtypes = [ctypes.c_int, P(Mesh), P(VSet), P(Coef), P(ctypes.c_double), P(Options),
@@ -100,6 +103,7 @@ def library():
         for name in ("dugks_check_config", "dugks_create", "dugks_destroy", "dugks_init_phi", "dugks_init_phi_host",
                      "dugks_step", "dugks_get_phi", "dugks_get_phi_host", "dugks_save_state", "dugks_load_state",
                      "dugks_set_stream", "dugks_sync", "dugks_info", "dugks_adjoint_step", "dugks_adjoint",
+                     "dugks_set_source",
                      "dugks_phi_mass_noalloc", "dugks_batch_create", "dugks_batch_destroy", "dugks_batch_init_phi",
                      "dugks_batch_step", "dugks_batch_get_phi", "dugks_batch_save_state", "dugks_batch_sync",
                      "dugks_batch_autotune"):
@@ -136,6 +140,14 @@ def marshal(problem: inputs.Problem):
     for k, x in enumerate(problem.d):
         c.d[k] = float(x)
     c.c_zero = int(bool(problem.c_zero))
+    if problem.d_tensor is not None:
+        dt3 = [tuple(map(float, x)) for x in problem.d_tensor]
+        if len(dt3) != 3 or max(len(x) for x in dt3) > 8:
+            raise ValueError("d_tensor = (dxx, dxy, dyy), at most 8 coefficients each")
+        c.d_tensor, c.ndt = 1, max(len(x) for x in dt3)
+        for arr, x in zip((c.dxx, c.dxy, c.dyy), dt3):
+            for k, val in enumerate(x):
+                arr[k] = val
     return m, v, c, (xf, yf)
 
 
@@ -175,6 +187,8 @@ class Solver:
         self.h = h
         self.L = L
         self.nx, self.ny = m.nx, m.ny
+        if problem.source:
+            self.set_source(problem.source, problem.t0)
 
     # -- helpers --------------------------------------------------------------
     def _check(self, st, where):
@@ -213,6 +227,23 @@ class Solver:
 
     def step(self, n: int = 1):
         self._check(self.L.dugks_step(self.h, int(n)), "dugks_step")
+
+    def set_source(self, terms, t0: float = 0.0):
+        """Source F = sum_k exp(rate_k t) phi^power_k S_k(x) (inputs.SourceTerm list; empty removes it)."""
+        terms = tuple(terms)
+        n = len(terms)
+        rate = (ctypes.c_double * max(n, 1))(*[float(t.rate) for t in terms])
+        power = (ctypes.c_int * max(n, 1))(*[int(t.power) for t in terms])
+        fields = None
+        if n:
+            fields = self.torch.tensor(np.stack([np.asarray(t.field, dtype=np.float64) for t in terms]),
+                                       dtype=self.dtype, device=self.device).contiguous()
+            assert tuple(fields.shape) == (n, self.ny, self.nx)
+            self.torch.cuda.current_stream(self.device).synchronize()  # the fields are on the device before the copy
+        self._check(self.L.dugks_set_source(self.h, n, rate, power,
+                                            ctypes.c_void_p(fields.data_ptr()) if n else None, float(t0)),
+                    "dugks_set_source")
+        self._src_keep = fields  # the library copies on its stream; keep until that copy ran
 
     def get_phi(self, out=None, mass: bool = False):
         """phi as a CUDA tensor [ny, nx]; with mass=True also returns M (synchronises)."""

@@ -32,6 +32,15 @@ DIRICHLET = 1
 WALLS = ("W", "E", "S", "N")
 
 
+@dataclass(frozen=True)
+class SourceTerm:
+    """One term exp(rate t) phi^power S(x) of the source F (S: [ny][nx] array)."""
+
+    rate: float
+    power: int
+    field: np.ndarray
+
+
 @dataclass
 class Problem:
     """A complete description of one NCDE instance (pure data).
@@ -39,6 +48,12 @@ class Problem:
     B(phi) = u * b(phi), D(phi) = d(phi) I with b, d polynomials given by
     their coefficients (lowest order first); C = u u * int_0^phi b'(s)^2 ds
     unless ``c_zero``.  ``bc`` and ``bc_value`` are ordered W, E, S, N.
+
+    ``d_tensor`` = (dxx, dxy, dyy), each a coefficient tuple, replaces d(phi) I
+    by the symmetric tensor [[dxx, dxy], [dxy, dyy]](phi).  ``source`` is a
+    tuple of SourceTerm: F(x, t, phi) = sum_k exp(rate_k t) phi^power_k S_k(x)
+    with S_k an [ny][nx] array sampled at the cell centres (Eq. 2.1); ``t0``
+    is the time of the initial state.
     """
 
     xf: np.ndarray
@@ -52,6 +67,9 @@ class Problem:
     d: tuple = (0.0, 1.0)
     c_zero: bool = False
     dt: float = 0.0
+    d_tensor: tuple | None = None
+    source: tuple = ()
+    t0: float = 0.0
     steps: int = 0
     name: str = ""
     meta: dict = field(default_factory=dict)
@@ -198,8 +216,84 @@ def batched(n: int = 256, seed: int = 7, steps: int = 1000, sides=(64, 128, 256,
     return out
 
 
+def cde_source(n: int = 200, pe: float = 100.0, t_end: float = 3.0, cfl: float = 0.5,
+               c: float = 1.0) -> tuple[Problem, np.ndarray]:
+    """Section 4, Example 4.1: isotropic CDE with constant u = (0.1, 0.1) and the
+    source of Eq. 4.1.3 on the periodic box [0, 2]^2; alpha = L u_x / Pe with
+    L = 2; B = phi u, C = phi u u, D = phi I; phi0 = sin(pi (x + y)).  The exact
+    solution (Eq. 4.1.5) is in meta["exact"](t)."""
+    ux = uy = 0.1
+    alpha = 2.0 * ux / pe
+    xf = uniform_faces(n, 0.0, 2.0)
+    xc = 0.5 * (xf[1:] + xf[:-1])
+    X, Y = np.meshgrid(xc, xc)
+    rate = 1.0 - 2.0 * np.pi ** 2 * alpha
+    S = np.sin(np.pi * (X + Y)) + np.pi * (ux + uy) * np.cos(np.pi * (X + Y))
+    dt = cfl_dt(xf, xf, c, cfl)
+    p = Problem(xf=xf, yf=xf.copy(), c=c, u=(ux, uy), b=(0.0, 1.0), alpha=alpha, d=(0.0, 1.0), dt=dt,
+                source=(SourceTerm(rate, 0, S),), steps=int(round(t_end / dt)),
+                name=f"cde_source_{n}x{n}_pe{pe:g}",
+                meta={"pe": pe, "cfl": cfl, "exact": lambda t: np.exp(rate * t) * np.sin(np.pi * (X + Y))})
+    return p, np.sin(np.pi * (X + Y))
+
+
+def nonlinear_source(n: int = 400, pe: float = 100.0, t_end: float = 3.0, cfl: float = 0.5, c: float = 1.0,
+                     u=(0.1, 0.1), m: int = 2, nx_: int = 2, ny_: int = 3, A: float = 1.0,
+                     kappa: float = 1.1) -> tuple[Problem, np.ndarray]:
+    """Section 4, Example 4.5: B = phi^m u, D = diag(phi^nx, phi^ny), the source of
+    Eq. 4.5.3, periodic [0, 1]^2, exact solution kappa - exp(-A t) cos(2 pi x)
+    cos(2 pi y) (Eq. 4.5.4, meta["exact"]).  The example does not state u; it is
+    read as (0.1, 0.1) as in Example 4.1, with alpha = L u_x / Pe, L = 1.
+    C = m^2 phi^(2m-1)/(2m-1) u u is the Remark 3 choice.  The source is
+    expanded into terms exp(rate t) phi^p S(x)."""
+    ux, uy = float(u[0]), float(u[1])
+    alpha = 1.0 * ux / pe
+    xf = uniform_faces(n)
+    xc = 0.5 * (xf[1:] + xf[:-1])
+    X, Y = np.meshgrid(xc, xc)
+    sx, cx, sy, cy = np.sin(2 * np.pi * X), np.cos(2 * np.pi * X), np.sin(2 * np.pi * Y), np.cos(2 * np.pi * Y)
+    cc = cx * cy
+    pi2 = np.pi ** 2
+    src = (SourceTerm(-A, 0, A * cc),
+           SourceTerm(-2 * A, nx_ - 2, -4 * nx_ * (nx_ - 1) * pi2 * alpha * sx ** 2 * cy ** 2),
+           SourceTerm(-A, nx_ - 1, -4 * nx_ * pi2 * alpha * cc),
+           SourceTerm(-2 * A, ny_ - 2, -4 * ny_ * (ny_ - 1) * pi2 * alpha * sy ** 2 * cx ** 2),
+           SourceTerm(-A, ny_ - 1, -4 * ny_ * pi2 * alpha * cc),
+           SourceTerm(-A, m - 1, 2 * np.pi * m * (ux * sx * cy + uy * cx * sy)))
+    dt = cfl_dt(xf, xf, c, cfl)
+    p = Problem(xf=xf, yf=xf.copy(), c=c, u=(ux, uy), b=tuple([0.0] * m + [1.0]), alpha=alpha, d=(0.0,),
+                d_tensor=(tuple([0.0] * nx_ + [1.0]), (0.0,), tuple([0.0] * ny_ + [1.0])), dt=dt, source=src,
+                steps=int(round(t_end / dt)), name=f"nonlinear_source_{n}x{n}_pe{pe:g}",
+                meta={"pe": pe, "cfl": cfl, "exact": lambda t: kappa - np.exp(-A * t) * cc})
+    return p, kappa - cc
+
+
+ANISO_K = {"isotropic": ((1.0, 0.0), (0.0, 1.0)), "diagonal": ((1.0, 0.0), (0.0, 2.0)),
+           "full": ((1.0, 1.0), (1.0, 2.0))}
+
+
+def gaussian_hill_aniso(n: int = 400, kind: str = "full", t_end: float = 10.0, cfl: float = 0.5,
+                        c: float = 1.0) -> tuple[Problem, np.ndarray]:
+    """Section 4, Example 4.4: Gaussian hill on the periodic box [-1, 1]^2 with
+    u = (0.01, 0.01), kappa = alpha = 1e-3 and D = K phi / kappa for the three
+    tensors K of Eq. 4.4.5 (times 1e-3); sigma0^2 = 0.01, peak 1 at the origin."""
+    K = ANISO_K[kind]
+    xf = uniform_faces(n, -1.0, 1.0)
+    dt = cfl_dt(xf, xf, c, cfl)
+    p = Problem(xf=xf, yf=xf.copy(), c=c, u=(0.01, 0.01), b=(0.0, 1.0), alpha=1e-3, d=(0.0,),
+                d_tensor=((0.0, K[0][0]), (0.0, K[0][1]), (0.0, K[1][1])), dt=dt,
+                steps=int(round(t_end / dt)), name=f"gaussian_hill_{kind}_{n}x{n}",
+                meta={"cfl": cfl, "K": K, "sigma0_sq": 0.01})
+    xc, yc = p.centres()
+    X, Y = np.meshgrid(xc, yc)
+    return p, np.exp(-(X ** 2 + Y ** 2) / (2 * 0.01))
+
+
 PRESETS = {
     "gaussian_hill": gaussian_hill,
     "burgers": burgers,
     "nonuniform": nonuniform,
+    "cde_source": cde_source,
+    "nonlinear_source": nonlinear_source,
+    "gaussian_hill_aniso": gaussian_hill_aniso,
 }

@@ -23,3 +23,13 @@ def oracle_threads() -> int:
 @pytest.fixture(scope="session")
 def nthreads():
     return oracle_threads()
+
+
+def pytest_collection_modifyitems(config, items):
+    """Tests marked slow (minutes of oracle time each) run only with DUGKS_SLOW=1."""
+    if os.environ.get("DUGKS_SLOW") == "1":
+        return
+    skip = pytest.mark.skip(reason="slow oracle run; set DUGKS_SLOW=1")
+    for item in items:
+        if "slow" in item.keywords:
+            item.add_marker(skip)

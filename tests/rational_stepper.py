@@ -14,6 +14,15 @@ Shared readings (the same as the oracle's, since the paper is silent):
 cells' central differences, and the mirrored ghost with non-equilibrium
 extrapolation at Dirichlet walls (interior cell's tangential slope at a wall
 face).
+
+Optional extensions: a symmetric tensor D with polynomial entries (Eq. 2.3
+contracted entry by entry), and a time-independent source F(x, phi) =
+sum_k phi^p_k S_k(x) (rate 0 keeps the arithmetic rational), with
+R_i = w_i c_i.B'(phi) F / c_s^2 (Remark 3), the interface evolution of
+Eq. 2.18 (each of fbar^+, R, F reconstructed at the characteristic foot) and
+the update of Eq. 2.12; the time derivatives are backward differences over
+the previous step (none on the first step), and a ghost cell carries the
+source distributions of the interior cell it mirrors.
 """
 from fractions import Fraction as Fr
 
@@ -45,7 +54,7 @@ def _poly_integral(a):
 
 
 class RationalDUGKS:
-    def __init__(self, xf, yf, bc, bc_value, c, u, b, alpha, d, c_zero, dt):
+    def __init__(self, xf, yf, bc, bc_value, c, u, b, alpha, d, c_zero, dt, d_tensor=None, source=()):
         self.xf = [Fr(v) for v in xf]
         self.yf = [Fr(v) for v in yf]
         self.nx, self.ny = len(xf) - 1, len(yf) - 1
@@ -64,6 +73,10 @@ class RationalDUGKS:
         self.h = self.dt / 2
         self.xper = bc[0] == 0
         self.yper = bc[2] == 0
+        self.dt3 = None if d_tensor is None else [[Fr(v) for v in e] for e in d_tensor]
+        # source terms (power, field[k][j] as Fractions)
+        self.src = [(int(pw), [[Fr(v) for v in row] for row in fld]) for pw, fld in source]
+        self.hist = None  # R_i, F_i of the previous step per cell
 
     # Eq. 2.3 in expanded form: contraction of (cs2 d - cs2 phi) I + C uu with (c c - cs2 I)
     def feq(self, phi):
@@ -74,9 +87,22 @@ class RationalDUGKS:
         for (ex, ey), w in zip(CVEC, WEIGHT):
             cu = c * (ex * self.u[0] + ey * self.u[1])
             cc = c * c * (ex * ex + ey * ey)
-            contraction = cs2 * (dv - phi) * (cc - 2 * cs2) + cv * (cu * cu - cs2 * uu)
+            if self.dt3 is None:
+                contraction = cs2 * (dv - phi) * (cc - 2 * cs2) + cv * (cu * cu - cs2 * uu)
+            else:  # cs2 D:(c c - cs2 I) with D = [[xx, xy], [xy, yy]], then the -cs2 phi I part
+                xx, xy, yy = (_poly_eval(e, phi) for e in self.dt3)
+                cx, cy = c * ex, c * ey
+                dd = xx * cx * cx + 2 * xy * cx * cy + yy * cy * cy - cs2 * (xx + yy)
+                contraction = cs2 * dd - cs2 * phi * (cc - 2 * cs2) + cv * (cu * cu - cs2 * uu)
             out.append(w * (phi + cu * bv / cs2 + contraction / (2 * cs2 * cs2)))
         return out
+
+    def sources(self, j, k, phi):
+        """(R_i, F_i) at interior cell (j, k) (Eq. 2.3; R by Remark 3)."""
+        F = sum(fld[k][j] * phi ** pw for pw, fld in self.src)
+        dbv = _poly_eval(_poly_deriv(self.b), phi)
+        R = [w * self.c * (ex * self.u[0] + ey * self.u[1]) * dbv * F / self.cs2 for (ex, ey), w in zip(CVEC, WEIGHT)]
+        return R, [w * F for w in WEIGHT]
 
     def init(self, phi0):
         return [[self.feq(Fr(phi0[k][j])) for j in range(self.nx)] for k in range(self.ny)]
@@ -120,6 +146,39 @@ class RationalDUGKS:
                                for a, q in zip(ft[k][j], e)]
                 phi[(j, k)], feq[(j, k)] = p, e
 
+        # sources at t_n and their values S + h/2 dS/dt for Eq. 2.18, dS/dt = (S^n - S^{n-1}) / dt
+        cur, sr, sf = {}, {}, {}
+        if self.src:
+            for k in range(ny):
+                for j in range(nx):
+                    R, F = self.sources(j, k, phi[(j, k)])
+                    Rp, Fp = self.hist[(j, k)] if self.hist is not None else (R, F)
+                    cur[(j, k)] = (R, F)
+                    sr[(j, k)] = [a + h / 2 * (a - b) / dt for a, b in zip(R, Rp)]
+                    sf[(j, k)] = [a + h / 2 * (a - b) / dt for a, b in zip(F, Fp)]
+
+        def interior(j, k):
+            """(ji, ki) of the interior cell behind extended cell (j, k), and whether (j, k) is a ghost."""
+            if self.xper:
+                j %= nx
+            if self.yper:
+                k %= ny
+            if 0 <= j < nx and 0 <= k < ny:
+                return j, k, False
+            ji = min(max(j, 0), nx - 1)
+            ki = min(max(k, 0), ny - 1)
+            if (ji != j) and (ki != k):
+                raise AssertionError("corner ghost requested")
+            return ji, ki, True
+
+        def SR(j, k):
+            ji, ki, _ = interior(j, k)
+            return sr[(ji, ki)]
+
+        def SF(j, k):
+            ji, ki, _ = interior(j, k)
+            return sf[(ji, ki)]
+
         def P(j, k):
             """fbar^+ at extended cell (j, k): interior, periodic image or NEE ghost."""
             if self.xper:
@@ -146,13 +205,58 @@ class RationalDUGKS:
             # Eq. 2.15 inverted at the face: f = (2 lam fbar + h feq) / (2 lam + h)
             return [(2 * lam * a + h * q) / (2 * lam + h) for a, q in zip(fbar_b, eb)]
 
-        def gy(j, k):
+        def gy(j, k, G=P):
             return [(a - b) / (self._centre_y(k + 1) - self._centre_y(k - 1))
-                    for a, b in zip(P(j, k + 1), P(j, k - 1))]
+                    for a, b in zip(G(j, k + 1), G(j, k - 1))]
 
-        def gx(j, k):
+        def gx(j, k, G=P):
             return [(a - b) / (self._centre_x(j + 1) - self._centre_x(j - 1))
-                    for a, b in zip(P(j + 1, k), P(j - 1, k))]
+                    for a, b in zip(G(j + 1, k), G(j - 1, k))]
+
+        def xface_foot(G, jf, k):
+            """G at the characteristic foot x_b - c_i h of x-face jf (Eqs. 2.19, 2.20), per velocity."""
+            jl, jr = jf - 1, jf
+            xl, xr, xb = self._centre_x(jl), self._centre_x(jr), self.xf[jf]
+            Gl, Gr = G(jl, k), G(jr, k)
+            w = (xb - xl) / (xr - xl)
+            if not self.xper and jf == 0:
+                gt = gy(jr, k, G)
+            elif not self.xper and jf == nx:
+                gt = gy(jl, k, G)
+            else:
+                gl, gr = gy(jl, k, G), gy(jr, k, G)
+                gt = [(1 - w) * a + w * b for a, b in zip(gl, gr)]
+            out = []
+            for i, (ex, ey) in enumerate(CVEC):
+                gn = (Gr[i] - Gl[i]) / (xr - xl)
+                out.append((1 - w) * Gl[i] + w * Gr[i] - h * self.c * (ex * gn + ey * gt[i]))
+            return out
+
+        def yface_foot(G, j, kf):
+            kl, kr = kf - 1, kf
+            yl, yr, yb = self._centre_y(kl), self._centre_y(kr), self.yf[kf]
+            Gl, Gr = G(j, kl), G(j, kr)
+            w = (yb - yl) / (yr - yl)
+            if not self.yper and kf == 0:
+                gt = gx(j, kr, G)
+            elif not self.yper and kf == ny:
+                gt = gx(j, kl, G)
+            else:
+                gl, gr = gx(j, kl, G), gx(j, kr, G)
+                gt = [(1 - w) * a + w * b for a, b in zip(gl, gr)]
+            out = []
+            for i, (ex, ey) in enumerate(CVEC):
+                gn = (Gr[i] - Gl[i]) / (yr - yl)
+                out.append((1 - w) * Gl[i] + w * Gr[i] - h * self.c * (ex * gt[i] + ey * gn))
+            return out
+
+        wr = 2 * lam * h / (2 * lam + h)  # weight of R in Eq. 2.18
+
+        def add_sources(fb, foot, *where):
+            if not self.src:
+                return fb
+            r, f = foot(SR, *where), foot(SF, *where)
+            return [a + wr * b + h * q for a, b, q in zip(fb, r, f)]
 
         fluxx, fluxy = {}, {}
         for k in range(ny):
@@ -175,7 +279,7 @@ class RationalDUGKS:
                     gn = (Pr[i] - Pl[i]) / (xr - xl)
                     val = (1 - w) * Pl[i] + w * Pr[i]
                     fb.append(val - h * self.c * (ex * gn + ey * gt[i]))
-                fluxx[(jf, k)] = face_f(fb)
+                fluxx[(jf, k)] = face_f(add_sources(fb, xface_foot, jf, k))
         for kf in range(ny + 1):
             for j in range(nx):
                 kl, kr = kf - 1, kf
@@ -194,7 +298,7 @@ class RationalDUGKS:
                     gn = (Pr[i] - Pl[i]) / (yr - yl)
                     val = (1 - w) * Pl[i] + w * Pr[i]
                     fb.append(val - h * self.c * (ex * gt[i] + ey * gn))
-                fluxy[(j, kf)] = face_f(fb)
+                fluxy[(j, kf)] = face_f(add_sources(fb, yface_foot, j, kf))
         out = []
         for k in range(ny):
             row = []
@@ -206,9 +310,15 @@ class RationalDUGKS:
                     # Eq. 2.12: flux through the four faces, outward normals
                     J = (ex * self.c * (fluxx[(j + 1, k)][i] - fluxx[(j, k)][i]) * dy
                          + ey * self.c * (fluxy[(j, k + 1)][i] - fluxy[(j, k)][i]) * dx)
-                    cell.append(ftp[(j, k)][i] - dt / (dx * dy) * J)
+                    v = ftp[(j, k)][i] - dt / (dx * dy) * J
+                    if self.src:  # Eq. 2.12: dt (S + dt/2 dS/dt) for S = R_i, F_i
+                        (R, F), (Rp, Fp) = cur[(j, k)], (self.hist[(j, k)] if self.hist is not None else cur[(j, k)])
+                        v += dt * (R[i] + dt / 2 * (R[i] - Rp[i]) / dt) + dt * (F[i] + dt / 2 * (F[i] - Fp[i]) / dt)
+                    cell.append(v)
                 row.append(cell)
             out.append(row)
+        if self.src:
+            self.hist = cur
         return out
 
     @staticmethod

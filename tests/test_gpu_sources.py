@@ -1,0 +1,150 @@
+"""Source terms (dugks_set_source) and tensor diffusion on the GPU against the
+FP64 oracle (whose source terms test_oracle_sources.py pins to an exact
+rational stepper and to Table 4_1_1 of the paper).
+
+Tolerances as for the plain step: FP64 rel-L2 1e-12, FP32 rel-L2 2e-5."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import Oracle  # noqa: E402
+from paper_1906_11036_gb300 import inputs as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def _walls_source(nx, ny):
+    xf, yf = I.tanh_faces(nx, 1.5), I.tanh_faces(ny, 1.5)
+    p = I.Problem(xf=xf, yf=yf, bc=(I.DIRICHLET,) * 4, bc_value=(1.2, 0.6, 0.9, 0.7), c=4.0, u=(0.3, -0.2),
+                  b=(0.0, 0.0, 0.5), alpha=0.02, d=(0.1, 1.0), dt=I.cfl_dt(xf, yf, 4.0, 0.4))
+    xc, yc = p.centres()
+    X, Y = np.meshgrid(xc, yc)
+    src = (I.SourceTerm(-0.5, 0, np.sin(2 * np.pi * X) * np.cos(np.pi * Y)),
+           I.SourceTerm(0.3, 1, 0.2 * np.cos(3 * X + Y)),
+           I.SourceTerm(0.0, 2, -0.1 * np.ones_like(X)))
+    return p.with_(source=src, t0=0.25), I.smooth_phi0(xc, yc, seed=6)
+
+
+def _mixed_tensor(nx, ny):
+    xf, yf = I.uniform_faces(nx), I.tanh_faces(ny, 1.5)
+    p = I.Problem(xf=xf, yf=yf, bc=(I.PERIODIC,) * 2 + (I.DIRICHLET,) * 2, bc_value=(0, 0, 1.1, 0.8), c=2.0,
+                  u=(0.2, 0.1), b=(0.0, 1.0), alpha=0.01, d=(0.0,),
+                  d_tensor=((0.0, 1.0), (0.0, 0.4), (0.2, 0.0, 1.0)), dt=I.cfl_dt(xf, yf, 2.0, 0.4))
+    xc, yc = p.centres()
+    X, Y = np.meshgrid(xc, yc)
+    return p.with_(source=(I.SourceTerm(0.0, 1, 0.3 * np.sin(2 * np.pi * X)),)), I.smooth_phi0(xc, yc, seed=8)
+
+
+CASES = {
+    "cde_source_40": lambda: I.cde_source(40),
+    "nonlinear_source_45": lambda: I.nonlinear_source(45),
+    "walls_source_70x45": lambda: _walls_source(70, 45),
+    "tensor_source_37x61": lambda: _mixed_tensor(37, 61),
+    "aniso_hill_full_50": lambda: I.gaussian_hill_aniso(50, "full"),
+    "tiny_source_3x3": lambda: I.cde_source(3),
+}
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _gpu_run(p, phi0, prec, chunks):
+    from paper_1906_11036_gb300.dugks import Solver
+
+    s = Solver(p, precision=prec)
+    s.init_phi(torch.tensor(phi0, device="cuda"))
+    for n in chunks:
+        s.step(n)
+    phi = s.get_phi().double().cpu().numpy()
+    info = s.info()
+    s.close()
+    return phi, info
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("name", list(CASES))
+def test_sources_match_oracle(name, prec):
+    p, phi0 = CASES[name]()
+    steps = 30
+    o = Oracle(p)
+    ref = o.phi(o.run(o.init(phi0), steps))
+    phi, info = _gpu_run(p, phi0, prec, [steps])
+    tol = 1e-12 if prec == 64 else 2e-5
+    assert _rel(phi, ref) <= tol, _rel(phi, ref)
+    assert abs(info["time"] - (p.t0 + steps * p.dt)) <= 1e-12 * max(1.0, abs(info["time"]))
+
+
+def test_history_carries_across_step_calls():
+    """step(5); step(7) is step(12): the phi^{n-1} history persists between calls."""
+    p, phi0 = _walls_source(33, 29)
+    a, _ = _gpu_run(p, phi0, 64, [5, 7])
+    b, _ = _gpu_run(p, phi0, 64, [12])
+    assert np.array_equal(a, b)
+    o = Oracle(p)
+    assert _rel(a, o.phi(o.run(o.init(phi0), 12))) <= 1e-12
+
+
+def test_load_state_restarts_the_history():
+    from paper_1906_11036_gb300.dugks import Solver
+
+    p, phi0 = I.nonlinear_source(32)
+    s = Solver(p, precision=64)
+    s.init_phi(torch.tensor(phi0, device="cuda"))
+    s.step(4)
+    f4 = s.save_state()
+    t4 = s.info()["time"]
+    s.load_state(f4)
+    s.step(3)
+    phi = s.get_phi().double().cpu().numpy()
+    s.close()
+    o = Oracle(p.with_(t0=t4))
+    ref = o.phi(o.run(f4.cpu().numpy(), 3))
+    assert _rel(phi, ref) <= 1e-12
+
+
+def test_example_4_1_on_the_gpu_reproduces_table_4_1_1():
+    """The FP64 GPU run of Example 4.1 (200^2, Pe = 100, t = 3) gives the GRE the
+    paper prints to every digit; the FP32 run within 1 % of it."""
+    g = json.load(open(GOLDEN))["ex41_table_4_1_1_dugks"]
+    p, phi0 = I.cde_source(200, 100.0)
+    exact = p.meta["exact"](p.steps * p.dt)
+    for prec, tol in ((64, None), (32, 0.01)):
+        phi, _ = _gpu_run(p, phi0, prec, [p.steps])
+        e = float(np.abs(phi - exact).sum() / np.abs(exact).sum())
+        ref = float(g["values"]["100"])
+        print(f"Example 4.1 GPU FP{prec}: GRE {e:.4e} (paper {ref:.3e})")
+        if tol is None:
+            assert abs(e - ref) <= 0.5e-7, e
+        else:
+            assert abs(e - ref) <= tol * ref, e
+
+
+def test_source_refusals():
+    from paper_1906_11036_gb300.dugks import DugksError, Solver
+
+    p, phi0 = I.cde_source(16)
+    with pytest.raises(DugksError):  # C = 0 has no Remark 3 form of R
+        Solver(p.with_(c_zero=True), precision=32)
+    s = Solver(p, precision=32)
+    s.init_phi(torch.tensor(phi0, device="cuda"))
+    with pytest.raises(DugksError):  # the adjoint covers the step without sources
+        s.adjoint_step(torch.zeros(9, 16, 16, device="cuda"), torch.zeros(9, 16, 16, device="cuda"))
+    s.set_source(())  # removing the source restores the plain step
+    assert s.info()["nsrc"] == 0
+    s.close()
