@@ -302,6 +302,43 @@ def batched_vs_single(steps: int = 100):
             "speedup": v_b / v_s, "tile_rows": rows, "unit": UNIT, "same_results": "bit-identical"}
 
 
+def sources_vs_plain(steps: int = 100):
+    """The source-term workload (Example 4.5 scaled to 2048^2: B = phi^2 u,
+    D = diag(phi^2, phi^3), six-term source F, FP32): per-step device time of the
+    step with F and R against the plain step on the same problem, and the
+    fraction of the measured HBM bandwidth its algorithmic bytes reach
+    (72 B/cell for ftilde + 4 B per source field + 8 B for the phi history)."""
+    import torch
+
+    from paper_1906_11036_gb300 import inputs as I
+    from paper_1906_11036_gb300.dugks import Solver
+
+    p, phi0 = I.nonlinear_source(2048)
+    cells = p.nx * p.ny
+    out = {"workload": f"{p.name} (Example 4.5 at 2048^2), FP32, {len(p.source)} source terms", "steps": steps}
+    for name, q in (("source", p), ("plain", p.with_(source=()))):
+        s = Solver(q, precision=32)
+        s.init_phi(torch.tensor(phi0, device="cuda"))
+        s.step(5)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.step(steps)
+        e1.record(s.stream)
+        e1.synchronize()
+        out[f"{name}_us_per_step"] = e0.elapsed_time(e1) / steps * 1e3
+        s.close()
+    peak, peak_kind = measured_peak()
+    alg = cells * (2 * Q * 4 + 4 * len(p.source) + 8)
+    out["source_value"] = cells * Q / (out["source_us_per_step"] * 1e-6)
+    out["unit"] = UNIT
+    out["algorithmic_bytes_per_step"] = alg
+    out["roofline_frac"] = alg / (out["source_us_per_step"] * 1e-6) / 1e9 / peak
+    out["peak_kind"] = peak_kind
+    out["source_to_plain_ratio"] = out["source_us_per_step"] / out["plain_us_per_step"]
+    return out
+
+
 def max_over_ranks(times, world: int, device="cpu"):
     """Element-wise maximum of per-rank timings over all ranks (the slowest
     replica sets the job's time); identity for a single process."""
@@ -340,6 +377,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-sources", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -416,6 +454,7 @@ def main():
     solver.close()
     adjoint = adjoint_ratio(args) if (world == 1 and not args.no_adjoint) else None
     batched = batched_vs_single() if (world == 1 and not args.no_batched) else None
+    sources = sources_vs_plain() if (world == 1 and not args.no_sources) else None
 
     t_dev, t_e2e = max_over_ranks([t_dev, t_e2e], world, device="cuda")
     if rank != 0:
@@ -446,6 +485,8 @@ def main():
         line["adjoint"] = adjoint
     if batched is not None:
         line["batched"] = batched
+    if sources is not None:
+        line["sources"] = sources
     if world == 1 and not args.no_cpu_baseline:
         import oracle
 
