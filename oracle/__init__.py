@@ -17,6 +17,8 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
                         balance, uniform growth, Examples 4.1 / 4.5 closed forms
   tensor D              second-moment identity of Eq. 2.7, Example 4.4
                         anisotropic Gaussian hills
+  Oracle3 (3-D)         exact rational 3-D stepper, D3Q15 / D3Q19 moments,
+                        3-D kinetic dispersion root, conservation, symmetry
 """
 from __future__ import annotations
 
@@ -28,6 +30,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dugks_oracle.c")
+_SRC3 = os.path.join(_HERE, "dugks3d_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -35,10 +38,11 @@ Q = 9
 
 
 def build(force: bool = False) -> str:
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC3))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC",
-                               "-o", tmp, _SRC, "-lm"])
+                               "-o", tmp, _SRC, _SRC3, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -58,6 +62,20 @@ class _Problem(ctypes.Structure):
         ("t0", ctypes.c_double),
         ("nsrc", ctypes.c_int), ("src_rate", ctypes.c_double * 8), ("src_pow", ctypes.c_int * 8),
         ("src_field", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+class _Problem3(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("xf", ctypes.POINTER(ctypes.c_double)), ("yf", ctypes.POINTER(ctypes.c_double)),
+        ("zf", ctypes.POINTER(ctypes.c_double)),
+        ("bc", ctypes.c_int * 6), ("bc_value", ctypes.c_double * 6),
+        ("lattice", ctypes.c_int), ("c", ctypes.c_double), ("u", ctypes.c_double * 3),
+        ("nb", ctypes.c_int), ("b", ctypes.c_double * 8),
+        ("alpha", ctypes.c_double),
+        ("nd", ctypes.c_int), ("d", ctypes.c_double * 8),
+        ("c_zero", ctypes.c_int), ("dt", ctypes.c_double),
     ]
 
 
@@ -82,6 +100,14 @@ def lib():
         L.oracle_equilibrium_deriv.argtypes = [P, ctypes.c_double, dp]
         L.oracle_adjoint_step.argtypes = [P, dp, dp, dp, dp]
         L.oracle_step_src.argtypes = [P, dp, dp, ctypes.c_double, dp, dp, dp, dp, ctypes.c_int]
+        P3 = ctypes.POINTER(_Problem3)
+        L.oracle3_equilibrium.argtypes = [P3, ctypes.c_double, dp]
+        L.oracle3_init.argtypes = [P3, dp, dp]
+        L.oracle3_phi.argtypes = [P3, dp, dp]
+        L.oracle3_mass.argtypes = [P3, dp]
+        L.oracle3_mass.restype = ctypes.c_double
+        L.oracle3_step.argtypes = [P3, dp, dp, ctypes.c_int]
+        L.oracle3_run.argtypes = [P3, dp, ctypes.c_long, ctypes.c_int]
         L.oracle_source.argtypes = [P, ctypes.c_long, ctypes.c_double, ctypes.c_double]
         L.oracle_source.restype = ctypes.c_double
         L.oracle_source_distributions.argtypes = [P, ctypes.c_double, ctypes.c_double, dp, dp]
@@ -279,3 +305,74 @@ class Oracle:
 
 def max_threads() -> int:
     return int(lib().oracle_max_threads())
+
+
+class Oracle3:
+    """The 3-D oracle (D3Q15 / D3Q19) for a ``paper_1906_11036_gb300.inputs.Problem3``;
+    arrays are [Q][nz][ny][nx] float64, phi [nz][ny][nx]."""
+
+    def __init__(self, problem):
+        self.p = problem
+        self._f = [np.ascontiguousarray(a, dtype=np.float64) for a in (problem.xf, problem.yf, problem.zf)]
+        s = _Problem3()
+        s.nx, s.ny, s.nz = (len(a) - 1 for a in self._f)
+        s.xf, s.yf, s.zf = (_ptr(a) for a in self._f)
+        for i in range(6):
+            s.bc[i] = int(problem.bc[i])
+            s.bc_value[i] = float(problem.bc_value[i])
+        s.lattice = int(problem.lattice)
+        s.c = float(problem.c)
+        for a in range(3):
+            s.u[a] = float(problem.u[a])
+        if len(problem.b) > 8 or len(problem.d) > 8:
+            raise ValueError("at most 8 polynomial coefficients")
+        s.nb = len(problem.b)
+        for k, v in enumerate(problem.b):
+            s.b[k] = float(v)
+        s.alpha = float(problem.alpha)
+        s.nd = len(problem.d)
+        for k, v in enumerate(problem.d):
+            s.d[k] = float(v)
+        s.c_zero = int(bool(problem.c_zero))
+        s.dt = float(problem.dt)
+        self.s = s
+        self.L = lib()
+        self.nx, self.ny, self.nz = s.nx, s.ny, s.nz
+        self.Q = int(problem.lattice)
+
+    def equilibrium(self, phi: float) -> np.ndarray:
+        out = np.zeros(self.Q)
+        self.L.oracle3_equilibrium(ctypes.byref(self.s), float(phi), _ptr(out))
+        return out
+
+    def init(self, phi0: np.ndarray) -> np.ndarray:
+        phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
+        assert phi0.shape == (self.nz, self.ny, self.nx)
+        f = np.zeros((self.Q, self.nz, self.ny, self.nx))
+        self.L.oracle3_init(ctypes.byref(self.s), _ptr(phi0), _ptr(f))
+        return f
+
+    def step(self, f: np.ndarray, threads: int = 0) -> np.ndarray:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        out = np.empty_like(f)
+        rc = self.L.oracle3_step(ctypes.byref(self.s), _ptr(f), _ptr(out), int(threads))
+        if rc != 0:
+            raise RuntimeError(f"oracle3_step failed ({rc})")
+        return out
+
+    def run(self, f: np.ndarray, nsteps: int, threads: int = 0) -> np.ndarray:
+        f = np.array(f, dtype=np.float64, order="C", copy=True)
+        rc = self.L.oracle3_run(ctypes.byref(self.s), _ptr(f), int(nsteps), int(threads))
+        if rc != 0:
+            raise RuntimeError(f"oracle3_run failed ({rc})")
+        return f
+
+    def phi(self, f: np.ndarray) -> np.ndarray:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        out = np.empty((self.nz, self.ny, self.nx))
+        self.L.oracle3_phi(ctypes.byref(self.s), _ptr(f), _ptr(out))
+        return out
+
+    def mass(self, f: np.ndarray) -> float:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        return float(self.L.oracle3_mass(ctypes.byref(self.s), _ptr(f)))

@@ -289,6 +289,90 @@ def gaussian_hill_aniso(n: int = 400, kind: str = "full", t_end: float = 10.0, c
     return p, np.exp(-(X ** 2 + Y ** 2) / (2 * 0.01))
 
 
+# ---------------------------------------------------------------------------
+# three dimensions (D3Q15 / D3Q19)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Problem3:
+    """One 3-D NCDE instance: B = u b(phi) with u in R^3, D = d(phi) I,
+    C = u u int_0^phi b'(s)^2 ds unless c_zero; ``lattice`` 15 (D3Q15, Eq. 2.28)
+    or 19 (D3Q19, Eq. 2.6).  ``bc`` / ``bc_value`` ordered W, E, S, N, B, T
+    (x low/high, y low/high, z low/high)."""
+
+    xf: np.ndarray
+    yf: np.ndarray
+    zf: np.ndarray
+    bc: tuple = (PERIODIC,) * 6
+    bc_value: tuple = (0.0,) * 6
+    lattice: int = 19
+    c: float = 1.0
+    u: tuple = (0.0, 0.0, 0.0)
+    b: tuple = (0.0, 1.0)
+    alpha: float = 0.01
+    d: tuple = (0.0, 1.0)
+    c_zero: bool = False
+    dt: float = 0.0
+    steps: int = 0
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nx(self) -> int:
+        return len(self.xf) - 1
+
+    @property
+    def ny(self) -> int:
+        return len(self.yf) - 1
+
+    @property
+    def nz(self) -> int:
+        return len(self.zf) - 1
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def centres(self):
+        return tuple(0.5 * (f[1:] + f[:-1]) for f in (self.xf, self.yf, self.zf))
+
+    def with_(self, **kw) -> "Problem3":
+        return replace(self, **kw)
+
+
+def cfl_dt3(xf, yf, zf, c: float, cfl: float) -> float:
+    """dt = CFL * min cell width / c (Remark 1)."""
+    return float(cfl * min(np.diff(xf).min(), np.diff(yf).min(), np.diff(zf).min()) / c)
+
+
+def burgers3d_phi0(xc, yc, zc, seed=2):
+    """1 + 0.2 sin 2pi x sin 2pi y sin 2pi z + 0.01 x (24 random low plane waves,
+    unit RMS); array [nz][ny][nx]."""
+    rng = np.random.default_rng(seed)
+    Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")
+    base = 1.0 + 0.2 * np.sin(2 * np.pi * X) * np.sin(2 * np.pi * Y) * np.sin(2 * np.pi * Z)
+    noise = np.zeros_like(X)
+    for _ in range(24):
+        k = rng.integers(-4, 5, size=3)
+        noise += rng.standard_normal() * np.cos(2 * np.pi * (k[0] * X + k[1] * Y + k[2] * Z) + rng.uniform(0, 2 * np.pi))
+    noise /= np.sqrt(np.mean(noise * noise))
+    return base + 0.01 * noise
+
+
+def burgers3d(n: int = 256, ny: int | None = None, nz: int | None = None, lattice: int = 19, steps: int = 500,
+              seed: int = 2, cfl: float = 0.4) -> tuple[Problem3, np.ndarray]:
+    """3-D periodic Burgers-type NCDE on [0,1]^3: B = (1,1,1) phi^2/2, D = phi I,
+    alpha = 0.005, c = 10, CFL 0.4 (the 2-D Burgers workload lifted to 3-D)."""
+    ny = n if ny is None else ny
+    nz = n if nz is None else nz
+    xf, yf, zf = uniform_faces(n), uniform_faces(ny), uniform_faces(nz)
+    p = Problem3(xf=xf, yf=yf, zf=zf, lattice=lattice, c=10.0, u=(1.0, 1.0, 1.0), b=(0.0, 0.0, 0.5),
+                 alpha=0.005, d=(0.0, 1.0), dt=cfl_dt3(xf, yf, zf, 10.0, cfl), steps=steps,
+                 name=f"burgers3d_d3q{lattice}_{n}x{ny}x{nz}", meta={"cfl": cfl, "seed": seed})
+    xc, yc, zc = p.centres()
+    return p, burgers3d_phi0(xc, yc, zc, seed)
+
+
 PRESETS = {
     "gaussian_hill": gaussian_hill,
     "burgers": burgers,
