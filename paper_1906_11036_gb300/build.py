@@ -1,7 +1,9 @@
 """Build of the CUDA library ``_lib/libdugks.so`` for sm_103a (GB300).
 
-nvcc, one translation unit, ``-gencode arch=compute_103a,code=sm_103a``; the
-library is rebuilt when a source or the header is newer than it.
+nvcc with ``-gencode arch=compute_103a,code=sm_103a``: the 2-D translation
+unit (``dugks_api.cu``) and the 3-D one (``dugks3d_api.cu``) compile to
+objects in parallel and link into one shared library; it is rebuilt when a
+source or a header is newer than it.
 """
 from __future__ import annotations
 
@@ -13,9 +15,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libdugks.so")
-SOURCES = [os.path.join(CSRC, "dugks_api.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("dugks_device.cuh", "dugks_kernels.cuh", "dugks_adjoint.cuh", "dugks_batch.cuh")] + [
-    os.path.join(ROOT, "include", "dugks.h")]
+SOURCES = [os.path.join(CSRC, "dugks_api.cu"), os.path.join(CSRC, "dugks3d_api.cu")]
+DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("dugks_device.cuh", "dugks_kernels.cuh", "dugks_adjoint.cuh",
+                                                  "dugks_batch.cuh", "dugks3d_kernels.cuh")] + [
+    os.path.join(ROOT, "include", "dugks.h"), os.path.join(ROOT, "include", "dugks3d.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,12 +40,22 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not stale():
         return LIB
     os.makedirs(LIBDIR, exist_ok=True)
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-o", tmp, *SOURCES]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.check_call(cmd)
+    tag = f".tmp{os.getpid()}"
+    objs, procs = [], []
+    for src in SOURCES:
+        obj = os.path.join(LIBDIR, os.path.basename(src) + tag + ".o")
+        cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c", "-o", obj, src]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        objs.append(obj)
+        procs.append((cmd, subprocess.Popen(cmd)))
+    failed = [cmd for cmd, pr in procs if pr.wait() != 0]
+    if failed:
+        raise subprocess.CalledProcessError(1, failed[0])
+    tmp = LIB + tag
+    subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
+    for obj in objs:
+        os.remove(obj)
     os.replace(tmp, LIB)
     return LIB
 

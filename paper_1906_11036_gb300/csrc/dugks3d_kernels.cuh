@@ -1,0 +1,333 @@
+// dugks3d_kernels.cuh -- the DUGKS step of Section 2 (arXiv:1906.11036) in
+// three dimensions with the D3Q15 (Eq. 2.28) or D3Q19 (Eq. 2.6) velocity set.
+//
+// step3d: one CTA of NW warps owns a tile of 30 columns (lanes 1..30 of each
+// warp; lanes 0 and 31 hold the x-halo) by NW-2 rows (warps 1..NW-2; warps 0
+// and NW-1 hold the y-halo) and marches up a segment of z-planes.  For every
+// plane it computes P = fbar^+ (Eq. 2.21) of all its cells into a three-plane
+// shared-memory ring, then each interior cell builds three faces from the ring:
+// its east x-face, its north y-face and its top z-face (Eqs. 2.19, 2.20, 2.26,
+// phi_b, Eq. 2.22).  The west x-face arrives from the lane to the left by a
+// warp shuffle, the south y-face from the row below through shared memory, and
+// the bottom z-face is the top face of the plane below, kept in registers.
+// The update (Eq. 2.12) reads ftilde of the cell again (an L1/L2 hit) to form
+// ftilde^+ = P + (P - ftilde)/3 (Eq. 2.23).
+//
+// Halo cells (periodic images, mirrored Dirichlet ghosts, or cells beyond the
+// domain) take their ftilde from the wrapped or clamped interior cell; a ghost
+// applies the non-equilibrium extrapolation P_g = feq(2 bv - phi) + P - feq(phi).
+// Cells beyond the domain only ever meet zero weights.
+#pragma once
+#include "dugks_device.cuh"
+
+namespace dugks3 {
+
+using dugks::CellM;
+using dugks::FaceM;
+
+// Direction components in units of c, rows x, y, z ('+' = 1, '-' = -1):
+// D3Q19 as Eq. 2.6 lists them, D3Q15 as Eq. 2.28.
+template <int QQ>
+__host__ __device__ constexpr char D3CH(int i, int a) {
+    return (QQ == 19 ? "0+-0000+-+-+--+0000"
+                       "000+-00+--+0000+-+-"
+                       "00000+-0000+-+-+--+"
+                     : "0+-0000+++----+"
+                       "000+-00++-+--+-"
+                       "00000+-+-++-+--")[a * QQ + i];
+}
+template <int QQ>
+__host__ __device__ constexpr int E3(int i, int a) {
+    return D3CH<QQ>(i, a) == '+' ? 1 : (D3CH<QQ>(i, a) == '-' ? -1 : 0);
+}
+
+// position of velocity i among those that cross a face normal to axis a (-1: parallel)
+template <int QQ>
+__host__ __device__ constexpr int XS3(int i, int a) {
+    if (E3<QQ>(i, a) == 0) return -1;
+    int s = 0;
+    for (int m = 0; m < i; ++m) s += E3<QQ>(m, a) != 0 ? 1 : 0;
+    return s;
+}
+
+constexpr int NCROSS = 10;  // velocities crossing a face of either lattice
+
+static_assert(E3<19>(11, 0) == 1 && E3<19>(11, 2) == 1 && E3<19>(17, 1) == 1 && E3<19>(17, 2) == -1, "D3Q19 table");
+static_assert(E3<15>(13, 0) == -1 && E3<15>(13, 1) == 1 && E3<15>(13, 2) == -1, "D3Q15 table");
+static_assert(XS3<19>(18, 2) == NCROSS - 1 && XS3<15>(14, 0) == NCROSS - 1, "crossing counts");
+
+template <typename T, int QQ, int NC>
+struct Consts3 {
+    T feq[QQ][NC];  // feq_i(phi) = sum_m feq[i][m] phi^m (ghosts)
+    T hbp[QQ][NC];  // b_bp feq[i][m]: P = a_bp ft + hbp_i(phi)
+    T hf[QQ][NC];   // b_f feq[i][m]: f = a_f fbar + hf_i(phi_b)
+    T a_bp, b_bp, a_f, third, hc;
+    T bcv[6];       // Dirichlet wall values W, E, S, N, B, T
+};
+
+template <typename T>
+struct Args3 {
+    const T* fin;
+    T* fout;
+    int nx, ny, nz;
+    long long plane;        // nx ny nz: elements per velocity, layout [Q][nz][ny][nx]
+    int per[3];             // periodic flags per axis
+    const FaceM<T>* fm[3];  // per axis, faces f = -1 .. n+1 at index f+1
+    const CellM<T>* cm[3];  // per axis, cells j = -1 .. n at index j+1
+    int zseg;               // planes per CTA segment
+};
+
+template <typename T, int QQ, int NC>
+__device__ __forceinline__ T horner3(const T (&c)[QQ][NC], int i, T x) {
+    T s = c[i][NC - 1];
+#pragma unroll
+    for (int m = NC - 2; m >= 0; --m) s = fma(s, x, c[i][m]);
+    return s;
+}
+
+// periodic wrap, or clamp into the domain
+__device__ __forceinline__ int wrapc(int j, int n, int per) {
+    if (per) {
+        j %= n;
+        return j < 0 ? j + n : j;
+    }
+    return min(max(j, 0), n - 1);
+}
+
+template <typename T, int QQ, int NC, int NW>
+__global__ void __launch_bounds__(NW * 32, 1) step3d(const Args3<T> a, const Consts3<T, QQ, NC> k) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sP = reinterpret_cast<T*>(smem_raw);  // [3][NW][QQ][32]: P of three planes
+    T* sY = sP + 3 * NW * QQ * 32;           // [NW][NCROSS][32]: north y-face f of each row
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x0 = blockIdx.x * 30, y0 = blockIdx.y * (NW - 2), z0 = blockIdx.z * a.zseg;
+    if (z0 >= a.nz) return;  // uniform over the CTA
+    const int z1 = min(z0 + a.zseg, a.nz);
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int j = x0 - 1 + lane, kk = y0 - 1 + w;
+    const int sj = wrapc(j, nx, a.per[0]), sk = wrapc(kk, ny, a.per[1]);
+    const bool gx = !a.per[0] && (j < 0 || j >= nx), gy = !a.per[1] && (kk < 0 || kk >= ny);
+    const int jm = min(max(j, -1), nx), km = min(max(kk, -1), ny);
+    const FaceM<T> fE = a.fm[0][jm + 2], fN = a.fm[1][km + 2];
+    const CellM<T> cxj = a.cm[0][jm + 1], cyk = a.cm[1][km + 1];
+    const bool interior_row = w >= 1 && w <= NW - 2;
+    const bool interior_col = lane >= 1 && lane <= 30;
+    const bool updates = interior_row && interior_col && j < nx && kk < ny;
+
+    auto Ps = [&](int slot, int ww, int i, int l) -> T { return sP[((slot * NW + ww) * QQ + i) * 32 + l]; };
+
+    // P of plane zz into ring slot `slot`
+    auto compute_P = [&](int zz, int slot) {
+        const int sz = wrapc(zz, nz, a.per[2]);
+        const bool gz = !a.per[2] && (zz < 0 || zz >= nz);
+        const long long c = ((long long)sz * ny + sk) * nx + sj;
+        T f[QQ];
+        T phi = T(0);
+#pragma unroll
+        for (int i = 0; i < QQ; ++i) {
+            f[i] = a.fin[i * a.plane + c];
+            phi += f[i];
+        }
+        T P[QQ];
+        T hs = T(0);
+#pragma unroll
+        for (int i = 1; i < QQ; ++i) {
+            const T h = horner3(k.hbp, i, phi);
+            P[i] = fma(k.a_bp, f[i], h);
+            hs += h;
+        }
+        P[0] = fma(k.a_bp, f[0], fma(k.b_bp, phi, -hs));  // rest velocity via the zeroth moment
+        if (gx || gy || gz) {  // mirrored ghost: P_g = feq(2 bv - phi) + P - feq(phi)
+            const T bv = gx ? (j < 0 ? k.bcv[0] : k.bcv[1])
+                            : (gy ? (kk < 0 ? k.bcv[2] : k.bcv[3]) : (zz < 0 ? k.bcv[4] : k.bcv[5]));
+            const T pg = T(2) * bv - phi;
+#pragma unroll
+            for (int i = 0; i < QQ; ++i) P[i] += horner3(k.feq, i, pg) - horner3(k.feq, i, phi);
+        }
+#pragma unroll
+        for (int i = 0; i < QQ; ++i) sP[((slot * NW + w) * QQ + i) * 32 + lane] = P[i];
+    };
+
+    // f of the velocities crossing the z-face between ring slots lo (below) and hi (above)
+    auto z_face = [&](int lo, int hi, const FaceM<T>& fz, T (&out)[NCROSS]) {
+        const int l1 = max(lane - 1, 0), l2 = min(lane + 1, 31);
+        const int w1 = max(w - 1, 0), w2 = min(w + 1, NW - 1);
+        T fb[QQ];
+        T phib = T(0);
+#pragma unroll
+        for (int i = 0; i < QQ; ++i) {
+            const int en = E3<QQ>(i, 2), ex = E3<QQ>(i, 0), ey = E3<QQ>(i, 1);
+            T v = ((T(1) - fz.w) + T(en) * fz.hcd) * Ps(lo, w, i, lane) + (fz.w - T(en) * fz.hcd) * Ps(hi, w, i, lane);
+            if (ex != 0) {
+                const T gl = (Ps(lo, w, i, l2) - Ps(lo, w, i, l1)) * cxj.ig;
+                const T gr = (Ps(hi, w, i, l2) - Ps(hi, w, i, l1)) * cxj.ig;
+                v -= T(ex) * k.hc * (fz.tl * gl + fz.tr * gr);
+            }
+            if (ey != 0) {
+                const T gl = (Ps(lo, w2, i, lane) - Ps(lo, w1, i, lane)) * cyk.ig;
+                const T gr = (Ps(hi, w2, i, lane) - Ps(hi, w1, i, lane)) * cyk.ig;
+                v -= T(ey) * k.hc * (fz.tl * gl + fz.tr * gr);
+            }
+            fb[i] = v;
+            phib += v;
+        }
+#pragma unroll
+        for (int i = 0; i < QQ; ++i)
+            if (XS3<QQ>(i, 2) >= 0) out[XS3<QQ>(i, 2)] = fma(k.a_f, fb[i], horner3(k.hf, i, phib));
+    };
+
+    // pipeline fill: planes z0-1 and z0, and the bottom face of plane z0
+    compute_P(z0 - 1, 0);
+    compute_P(z0, 1);
+    __syncthreads();
+    T fB[NCROSS];
+    if (interior_row) z_face(0, 1, a.fm[2][z0 + 1], fB);
+
+    for (int z = z0; z < z1; ++z) {
+        const int sm = (z - z0) % 3, so = (z - z0 + 1) % 3, sp = (z - z0 + 2) % 3;
+        compute_P(z + 1, sp);
+        __syncthreads();
+        const CellM<T> czl = a.cm[2][z + 1];
+        const int l1 = max(lane - 1, 0), l2 = min(lane + 1, 31);
+        const int w1 = max(w - 1, 0), w2 = min(w + 1, NW - 1);
+        // east x-face (lanes 0..30 of the interior rows)
+        T fEx[NCROSS], fNy[NCROSS], fTz[NCROSS];
+#pragma unroll
+        for (int s = 0; s < NCROSS; ++s) fEx[s] = fNy[s] = fTz[s] = T(0);
+        if (interior_row && lane <= 30) {
+            T fb[QQ];
+            T phib = T(0);
+#pragma unroll
+            for (int i = 0; i < QQ; ++i) {
+                const int en = E3<QQ>(i, 0), ey = E3<QQ>(i, 1), ez = E3<QQ>(i, 2);
+                T v = ((T(1) - fE.w) + T(en) * fE.hcd) * Ps(so, w, i, lane) +
+                      (fE.w - T(en) * fE.hcd) * Ps(so, w, i, lane + 1);
+                if (ey != 0) {
+                    const T gl = (Ps(so, w2, i, lane) - Ps(so, w1, i, lane)) * cyk.ig;
+                    const T gr = (Ps(so, w2, i, lane + 1) - Ps(so, w1, i, lane + 1)) * cyk.ig;
+                    v -= T(ey) * k.hc * (fE.tl * gl + fE.tr * gr);
+                }
+                if (ez != 0) {
+                    const T gl = (Ps(sp, w, i, lane) - Ps(sm, w, i, lane)) * czl.ig;
+                    const T gr = (Ps(sp, w, i, lane + 1) - Ps(sm, w, i, lane + 1)) * czl.ig;
+                    v -= T(ez) * k.hc * (fE.tl * gl + fE.tr * gr);
+                }
+                fb[i] = v;
+                phib += v;
+            }
+#pragma unroll
+            for (int i = 0; i < QQ; ++i)
+                if (XS3<QQ>(i, 0) >= 0) fEx[XS3<QQ>(i, 0)] = fma(k.a_f, fb[i], horner3(k.hf, i, phib));
+        }
+        // north y-face (rows 0..NW-2, lanes 1..30): shared with the row above as its south face
+        if (w <= NW - 2 && interior_col) {
+            T fb[QQ];
+            T phib = T(0);
+#pragma unroll
+            for (int i = 0; i < QQ; ++i) {
+                const int en = E3<QQ>(i, 1), ex = E3<QQ>(i, 0), ez = E3<QQ>(i, 2);
+                T v = ((T(1) - fN.w) + T(en) * fN.hcd) * Ps(so, w, i, lane) +
+                      (fN.w - T(en) * fN.hcd) * Ps(so, w + 1, i, lane);
+                if (ex != 0) {
+                    const T gl = (Ps(so, w, i, l2) - Ps(so, w, i, l1)) * cxj.ig;
+                    const T gr = (Ps(so, w + 1, i, l2) - Ps(so, w + 1, i, l1)) * cxj.ig;
+                    v -= T(ex) * k.hc * (fN.tl * gl + fN.tr * gr);
+                }
+                if (ez != 0) {
+                    const T gl = (Ps(sp, w, i, lane) - Ps(sm, w, i, lane)) * czl.ig;
+                    const T gr = (Ps(sp, w + 1, i, lane) - Ps(sm, w + 1, i, lane)) * czl.ig;
+                    v -= T(ez) * k.hc * (fN.tl * gl + fN.tr * gr);
+                }
+                fb[i] = v;
+                phib += v;
+            }
+#pragma unroll
+            for (int i = 0; i < QQ; ++i)
+                if (XS3<QQ>(i, 1) >= 0) {
+                    const T f = fma(k.a_f, fb[i], horner3(k.hf, i, phib));
+                    fNy[XS3<QQ>(i, 1)] = f;
+                    sY[(w * NCROSS + XS3<QQ>(i, 1)) * 32 + lane] = f;
+                }
+        }
+        // top z-face (interior rows)
+        if (interior_row) z_face(so, sp, a.fm[2][z + 2], fTz);
+        // west x-face: the east face of the lane to the left
+        T fWx[NCROSS];
+#pragma unroll
+        for (int s = 0; s < NCROSS; ++s) fWx[s] = __shfl_up_sync(0xffffffffu, fEx[s], 1);
+        __syncthreads();  // south faces in sY; every read of slot sm is done
+        if (updates) {
+            const long long c = ((long long)z * ny + kk) * nx + j;
+#pragma unroll
+            for (int i = 0; i < QQ; ++i) {
+                const T P = Ps(so, w, i, lane);
+                T v = fma(k.third, P - a.fin[i * a.plane + c], P);  // ftilde^+ (Eq. 2.23)
+                if (XS3<QQ>(i, 0) >= 0)
+                    v = fma(-T(E3<QQ>(i, 0)) * cxj.r, fEx[XS3<QQ>(i, 0)] - fWx[XS3<QQ>(i, 0)], v);
+                if (XS3<QQ>(i, 1) >= 0)
+                    v = fma(-T(E3<QQ>(i, 1)) * cyk.r, fNy[XS3<QQ>(i, 1)] - sY[((w - 1) * NCROSS + XS3<QQ>(i, 1)) * 32 + lane], v);
+                if (XS3<QQ>(i, 2) >= 0)
+                    v = fma(-T(E3<QQ>(i, 2)) * czl.r, fTz[XS3<QQ>(i, 2)] - fB[XS3<QQ>(i, 2)], v);
+                a.fout[i * a.plane + c] = v;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < NCROSS; ++s) fB[s] = fTz[s];
+    }
+}
+
+// phi = sum_i ftilde_i (optional output) and per-block partial sums of |V| phi in double
+template <typename T, int QQ>
+__global__ void __launch_bounds__(256) phi_mass3(const T* __restrict__ f, T* __restrict__ phi, int nx, int ny, int nz,
+                                                 const double* __restrict__ dxv, const double* __restrict__ dyv,
+                                                 const double* __restrict__ dzv, double* __restrict__ partial) {
+    const long long n = (long long)nx * ny * nz;
+    double acc = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int j = int(c % nx);
+        const long long r = c / nx;
+        const int kk = int(r % ny), l = int(r / ny);
+        T s = T(0);
+#pragma unroll
+        for (int i = 0; i < QQ; ++i) s += f[i * n + c];
+        if (phi) phi[c] = s;
+        acc += dxv[j] * dyv[kk] * dzv[l] * double(s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double ws[8];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < int(blockDim.x >> 5); ++q) s += ws[q];
+        partial[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(256) sum3(const double* __restrict__ partial, int n, double* __restrict__ out) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partial[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double ws[8];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < int(blockDim.x >> 5); ++q) s += ws[q];
+        *out = s;
+    }
+}
+
+// ftilde = feq(phi0) (opening of Section 4); phi0 [nz][ny][nx]
+template <typename T, int QQ, int NC, typename Tin>
+__global__ void init3(const Tin* __restrict__ phi0, T* __restrict__ f, long long n, const Consts3<T, QQ, NC> k) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const T p = T(phi0[c]);
+#pragma unroll
+        for (int i = 0; i < QQ; ++i) f[i * n + c] = horner3(k.feq, i, p);
+    }
+}
+
+}  // namespace dugks3

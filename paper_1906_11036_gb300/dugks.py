@@ -57,6 +57,28 @@ class Info(ctypes.Structure):
                 ("nsrc", ctypes.c_int)]
 
 
+class Mesh3(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("xf", ctypes.POINTER(ctypes.c_double)), ("yf", ctypes.POINTER(ctypes.c_double)),
+                ("zf", ctypes.POINTER(ctypes.c_double)), ("bc", ctypes.c_int * 6), ("bc_value", ctypes.c_double * 6)]
+
+
+class VSet3(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("c", ctypes.c_double)]
+
+
+class Coef3(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_double * 3), ("nb", ctypes.c_int), ("b", ctypes.c_double * 8),
+                ("alpha", ctypes.c_double), ("nd", ctypes.c_int), ("d", ctypes.c_double * 8), ("c_zero", ctypes.c_int)]
+
+
+class Info3(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("q", ctypes.c_int),
+                ("precision", ctypes.c_int), ("steps_done", ctypes.c_longlong), ("dt", ctypes.c_double),
+                ("lam", ctypes.c_double), ("cfl", ctypes.c_double), ("block_threads", ctypes.c_int),
+                ("grid", ctypes.c_int * 3), ("zseg", ctypes.c_int), ("state_bytes", ctypes.c_longlong)]
+
+
 _lib = None
 
 
@@ -96,6 +118,23 @@ def library():
         L.dugks_batch_autotune.argtypes = [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_float)]
         L.dugks_batch_last_error.argtypes = [vp]
         L.dugks_batch_last_error.restype = ctypes.c_char_p
+        P3 = P
+        L.dugks_3d_check_config.argtypes = [P3(Mesh3), P3(VSet3), P3(Coef3), ctypes.c_double]
+        L.dugks_3d_create.argtypes = [P3(Mesh3), P3(VSet3), P3(Coef3), ctypes.c_double, P(Options), P(vp)]
+        L.dugks_3d_destroy.argtypes = [vp]
+        L.dugks_3d_init_phi.argtypes = [vp, vp]
+        L.dugks_3d_step.argtypes = [vp, ctypes.c_longlong]
+        L.dugks_3d_get_phi.argtypes = [vp, vp, P(ctypes.c_double)]
+        L.dugks_3d_save_state.argtypes = [vp, vp]
+        L.dugks_3d_load_state.argtypes = [vp, vp]
+        L.dugks_3d_sync.argtypes = [vp]
+        L.dugks_3d_info.argtypes = [vp, P(Info3)]
+        L.dugks_3d_last_error.argtypes = [vp]
+        L.dugks_3d_last_error.restype = ctypes.c_char_p
+        for name in ("dugks_3d_check_config", "dugks_3d_create", "dugks_3d_destroy", "dugks_3d_init_phi",
+                     "dugks_3d_step", "dugks_3d_get_phi", "dugks_3d_save_state", "dugks_3d_load_state",
+                     "dugks_3d_sync", "dugks_3d_info"):
+            getattr(L, name).restype = ctypes.c_int
         L.dugks_status_string.argtypes = [ctypes.c_int]
         L.dugks_status_string.restype = ctypes.c_char_p
         L.dugks_last_error.argtypes = [vp]
@@ -432,3 +471,112 @@ def run_fn():
 
     return DugksRun
 
+
+
+def marshal3(problem):
+    """inputs.Problem3 -> (Mesh3, VSet3, Coef3, keepalive arrays)."""
+    f = [np.ascontiguousarray(a, dtype=np.float64) for a in (problem.xf, problem.yf, problem.zf)]
+    m = Mesh3()
+    m.nx, m.ny, m.nz = (len(a) - 1 for a in f)
+    m.xf, m.yf, m.zf = (_dptr(a) for a in f)
+    for i in range(6):
+        m.bc[i] = int(problem.bc[i])
+        m.bc_value[i] = float(problem.bc_value[i])
+    v = VSet3()
+    v.kind, v.c = int(problem.lattice), float(problem.c)
+    c = Coef3()
+    for a in range(3):
+        c.u[a] = float(problem.u[a])
+    if len(problem.b) > 8 or len(problem.d) > 8:
+        raise ValueError("at most 8 polynomial coefficients")
+    c.nb = len(problem.b)
+    for k, x in enumerate(problem.b):
+        c.b[k] = float(x)
+    c.alpha = float(problem.alpha)
+    c.nd = len(problem.d)
+    for k, x in enumerate(problem.d):
+        c.d[k] = float(x)
+    c.c_zero = int(bool(problem.c_zero))
+    return m, v, c, f
+
+
+class Solver3:
+    """One 3-D NCDE instance (inputs.Problem3, D3Q15 or D3Q19) advanced by the CUDA step."""
+
+    def __init__(self, problem, precision: int = 32, stream=None, device: int | None = None):
+        import torch
+
+        self.torch = torch
+        self.problem = problem
+        self.precision = int(precision)
+        self.dtype = torch.float32 if self.precision == 32 else torch.float64
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        L = library()
+        m, v, c, keep = marshal3(problem)
+        o = Options()
+        o.precision, o.kernel = self.precision, KERNELS["fused"]
+        o.stream = ctypes.c_void_p(stream.cuda_stream)
+        o.device = self.device.index
+        h = ctypes.c_void_p()
+        st = L.dugks_3d_create(ctypes.byref(m), ctypes.byref(v), ctypes.byref(c), float(problem.dt), ctypes.byref(o),
+                               ctypes.byref(h))
+        if st != OK:
+            raise DugksError(st, "dugks_3d_create")
+        self.h, self.L = h, L
+        self.nx, self.ny, self.nz, self.Q = m.nx, m.ny, m.nz, v.kind
+
+    def _check(self, st, where):
+        if st != OK:
+            raise DugksError(st, where, self.L.dugks_3d_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.dugks_3d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_phi(self, phi0):
+        """phi0: tensor or array [nz, ny, nx]."""
+        t = self.torch.as_tensor(phi0).to(device=self.device, dtype=self.dtype).contiguous()
+        assert tuple(t.shape) == (self.nz, self.ny, self.nx)
+        self._keep = t
+        self._check(self.L.dugks_3d_init_phi(self.h, ctypes.c_void_p(t.data_ptr())), "dugks_3d_init_phi")
+
+    def step(self, n: int = 1):
+        self._check(self.L.dugks_3d_step(self.h, int(n)), "dugks_3d_step")
+
+    def get_phi(self, mass: bool = False):
+        out = self.torch.empty((self.nz, self.ny, self.nx), dtype=self.dtype, device=self.device)
+        m = ctypes.c_double(0.0)
+        self._check(self.L.dugks_3d_get_phi(self.h, ctypes.c_void_p(out.data_ptr()), ctypes.byref(m) if mass else None),
+                    "dugks_3d_get_phi")
+        return (out, m.value) if mass else out
+
+    def save_state(self):
+        out = self.torch.empty((self.Q, self.nz, self.ny, self.nx), dtype=self.dtype, device=self.device)
+        self._check(self.L.dugks_3d_save_state(self.h, ctypes.c_void_p(out.data_ptr())), "dugks_3d_save_state")
+        return out
+
+    def load_state(self, f):
+        t = f.to(device=self.device, dtype=self.dtype).contiguous()
+        assert tuple(t.shape) == (self.Q, self.nz, self.ny, self.nx)
+        self._keep_state = t
+        self._check(self.L.dugks_3d_load_state(self.h, ctypes.c_void_p(t.data_ptr())), "dugks_3d_load_state")
+
+    def sync(self):
+        self._check(self.L.dugks_3d_sync(self.h), "dugks_3d_sync")
+
+    def info(self) -> dict:
+        i = Info3()
+        self._check(self.L.dugks_3d_info(self.h, ctypes.byref(i)), "dugks_3d_info")
+        out = {f: getattr(i, f) for f, _ in Info3._fields_}
+        out["grid"] = tuple(i.grid)
+        return out
