@@ -339,6 +339,43 @@ def sources_vs_plain(steps: int = 100):
     return out
 
 
+def three_d(n: int = 256, steps: int = 20):
+    """The 3-D step (periodic Burgers-type workload on n^3 cells, FP32) with the
+    D3Q19 and D3Q15 velocity sets: device time per step (CUDA events on the
+    solver's stream, state of 2 x Q x 4 B per cell, larger than L2 at 256^3),
+    cell-velocity updates/s, and the fraction of the measured HBM bandwidth that
+    the algorithmic bytes (read and write ftilde once: 8 Q B per cell) reach."""
+    import torch
+
+    from paper_1906_11036_gb300 import inputs as I
+    from paper_1906_11036_gb300.dugks import Solver3
+
+    peak, peak_kind = measured_peak()
+    out = {}
+    for q in (19, 15):
+        p, phi0 = I.burgers3d(n, lattice=q)
+        s = Solver3(p, precision=32)
+        s.init_phi(phi0)
+        s.step(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.step(steps)
+        e1.record(s.stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / steps * 1e-3
+        _, mass = s.get_phi(mass=True)
+        info = s.info()
+        s.close()
+        cells = p.cells
+        alg = cells * q * 8
+        out[f"d3q{q}"] = {"workload": p.name, "steps": steps, "us_per_step": t * 1e6, "value": cells * q / t,
+                          "unit": UNIT, "algorithmic_bytes_per_step": alg, "achieved_gbs": alg / t / 1e9,
+                          "roofline_frac": alg / t / 1e9 / peak, "peak_kind": peak_kind, "mass": mass,
+                          "grid": list(info["grid"]), "zseg": info["zseg"], "block": info["block_threads"]}
+    return out
+
+
 def max_over_ranks(times, world: int, device="cpu"):
     """Element-wise maximum of per-rank timings over all ranks (the slowest
     replica sets the job's time); identity for a single process."""
@@ -378,6 +415,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-sources", action="store_true")
+    ap.add_argument("--no-3d", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -455,6 +493,7 @@ def main():
     adjoint = adjoint_ratio(args) if (world == 1 and not args.no_adjoint) else None
     batched = batched_vs_single() if (world == 1 and not args.no_batched) else None
     sources = sources_vs_plain() if (world == 1 and not args.no_sources) else None
+    d3 = three_d() if (world == 1 and not args.no_3d) else None
 
     t_dev, t_e2e = max_over_ranks([t_dev, t_e2e], world, device="cuda")
     if rank != 0:
@@ -487,6 +526,8 @@ def main():
         line["batched"] = batched
     if sources is not None:
         line["sources"] = sources
+    if d3 is not None:
+        line["three_d"] = d3
     if world == 1 and not args.no_cpu_baseline:
         import oracle
 
