@@ -2,6 +2,7 @@
 
     python -m paper_1906_11036_gb300.cli --workload nonuniform --n 2048 --steps 5 [--precision 32]
     python -m paper_1906_11036_gb300.cli --workload burgers --n 512 --steps 40 --adjoint 20
+    python -m paper_1906_11036_gb300.cli --workload burgers3d --n 128 --steps 5 [--lattice 15]
 
 Builds the library if needed, initialises ftilde = feq(phi0) and runs the
 requested number of DUGKS time steps through the C ABI, then prints the
@@ -23,7 +24,8 @@ def main(argv=None) -> int:
     ap = argparse.ArgumentParser(prog="python -m paper_1906_11036_gb300.cli")
     from . import inputs as _inputs
 
-    ap.add_argument("--workload", default="nonuniform", choices=sorted(_inputs.PRESETS))
+    ap.add_argument("--workload", default="nonuniform", choices=sorted(_inputs.PRESETS) + ["burgers3d"])
+    ap.add_argument("--lattice", type=int, default=19, choices=[15, 19], help="3-D velocity set")
     ap.add_argument("--n", type=int, default=None, help="cells per side (default: the preset's)")
     ap.add_argument("--steps", type=int, default=None, help="time steps (default: the preset's)")
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
@@ -38,6 +40,24 @@ def main(argv=None) -> int:
     from .dugks import Solver
 
     build.build()
+    if a.workload == "burgers3d":  # the 3-D step (D3Q15 / D3Q19)
+        from .dugks import Solver3
+
+        p, phi0 = inputs.burgers3d(256 if a.n is None else a.n, lattice=a.lattice)
+        steps = p.steps if a.steps is None else a.steps
+        s = Solver3(p, precision=a.precision)
+        s.init_phi(phi0)
+        _, m0 = s.get_phi(mass=True)
+        t0 = time.perf_counter()
+        s.step(steps)
+        phi, m = s.get_phi(mass=True)
+        info = s.info()
+        s.close()
+        print(json.dumps({"workload": p.name, "steps": steps, "precision": a.precision, "mass0": m0, "mass": m,
+                          "phi_min": float(phi.min()), "phi_max": float(phi.max()),
+                          "seconds": time.perf_counter() - t0, "block": info["block_threads"],
+                          "grid": list(info["grid"]), "zseg": info["zseg"]}))
+        return 0
     maker = inputs.PRESETS[a.workload]
     p, phi0 = maker() if a.n is None else maker(a.n)
     steps = p.steps if a.steps is None else a.steps

@@ -159,7 +159,7 @@ Args3<T> args3(const dugks_3d_ctx* ctx) {
 
 template <typename T, int QQ, int NC, int NW>
 constexpr size_t smem3() {
-    return size_t(3 * NW * QQ * 32 + NW * NCROSS * 32) * sizeof(T);
+    return size_t(3 * NW * QQ * 32 + NW * NCROSS * 32 + 3 * NW * 4 * 32 + NW * QQ * 32) * sizeof(T);
 }
 
 template <typename T, int QQ, int NC, int NW>

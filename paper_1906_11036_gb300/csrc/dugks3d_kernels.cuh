@@ -13,6 +13,18 @@
 // The update (Eq. 2.12) reads ftilde of the cell again (an L1/L2 hit) to form
 // ftilde^+ = P + (P - ftilde)/3 (Eq. 2.23).
 //
+// ftilde of the next plane is prefetched with cp.async into per-thread
+// shared-memory slots while the faces of the current plane are computed; a
+// thread refills its slots only after it has consumed their contents.
+//
+// Only the velocities that cross a face need their reconstructed fbar; the
+// interface phi_b = sum_i fbar_i follows from the moments M0 = sum_i P_i and
+// M_a = sum_i e_a P_i of the two cells (the reconstruction is linear):
+//   phi_b = (1-w) M0_L + w M0_R + hcd (Mn_L - Mn_R)
+//           - hc [tl sum_t d_t M_t (L) + tr sum_t d_t M_t (R)]
+// with d_t the same central differences along the tangential axes t.  Each
+// cell stores its four moments next to P.
+//
 // Halo cells (periodic images, mirrored Dirichlet ghosts, or cells beyond the
 // domain) take their ftilde from the wrapped or clamped interior cell; a ghost
 // applies the non-equilibrium extrapolation P_g = feq(2 bv - phi) + P - feq(phi).
@@ -99,6 +111,8 @@ __global__ void __launch_bounds__(NW * 32, 1) step3d(const Args3<T> a, const Con
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sP = reinterpret_cast<T*>(smem_raw);  // [3][NW][QQ][32]: P of three planes
     T* sY = sP + 3 * NW * QQ * 32;           // [NW][NCROSS][32]: north y-face f of each row
+    T* sM = sY + NW * NCROSS * 32;           // [3][NW][4][32]: moments M0, Mx, My, Mz of P
+    T* sF = sM + 3 * NW * 4 * 32;            // [NW][QQ][32]: ftilde of the next plane (cp.async)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int x0 = blockIdx.x * 30, y0 = blockIdx.y * (NW - 2), z0 = blockIdx.z * a.zseg;
     if (z0 >= a.nz) return;  // uniform over the CTA
@@ -115,19 +129,33 @@ __global__ void __launch_bounds__(NW * 32, 1) step3d(const Args3<T> a, const Con
     const bool updates = interior_row && interior_col && j < nx && kk < ny;
 
     auto Ps = [&](int slot, int ww, int i, int l) -> T { return sP[((slot * NW + ww) * QQ + i) * 32 + l]; };
+    auto Ms = [&](int slot, int ww, int m, int l) -> T { return sM[((slot * NW + ww) * 4 + m) * 32 + l]; };
 
-    // P of plane zz into ring slot `slot`
-    auto compute_P = [&](int zz, int slot) {
-        const int sz = wrapc(zz, nz, a.per[2]);
+    // start the copy of this thread's ftilde of plane zz into its slots of sF
+    auto prefetch = [&](int zz) {
+        const long long c = ((long long)wrapc(zz, nz, a.per[2]) * ny + sk) * nx + sj;
+#pragma unroll
+        for (int i = 0; i < QQ; ++i) {
+            const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(sF + (w * QQ + i) * 32 + lane));
+            asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(a.fin + i * a.plane + c),
+                         "n"(int(sizeof(T))));
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+
+    // P of plane zz (already prefetched into sF) into ring slot `slot`; then prefetch plane `next`
+    auto compute_P = [&](int zz, int slot, int next) {
         const bool gz = !a.per[2] && (zz < 0 || zz >= nz);
-        const long long c = ((long long)sz * ny + sk) * nx + sj;
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         T f[QQ];
         T phi = T(0);
 #pragma unroll
         for (int i = 0; i < QQ; ++i) {
-            f[i] = a.fin[i * a.plane + c];
+            f[i] = sF[(w * QQ + i) * 32 + lane];
             phi += f[i];
         }
+        // phi depends on every slot value, so the slots are free again
+        prefetch(next);
         T P[QQ];
         T hs = T(0);
 #pragma unroll
@@ -144,18 +172,35 @@ __global__ void __launch_bounds__(NW * 32, 1) step3d(const Args3<T> a, const Con
 #pragma unroll
             for (int i = 0; i < QQ; ++i) P[i] += horner3(k.feq, i, pg) - horner3(k.feq, i, phi);
         }
+        T m0 = T(0), mx = T(0), my = T(0), mz = T(0);
 #pragma unroll
-        for (int i = 0; i < QQ; ++i) sP[((slot * NW + w) * QQ + i) * 32 + lane] = P[i];
+        for (int i = 0; i < QQ; ++i) {
+            sP[((slot * NW + w) * QQ + i) * 32 + lane] = P[i];
+            m0 += P[i];
+            if (E3<QQ>(i, 0) != 0) mx += T(E3<QQ>(i, 0)) * P[i];
+            if (E3<QQ>(i, 1) != 0) my += T(E3<QQ>(i, 1)) * P[i];
+            if (E3<QQ>(i, 2) != 0) mz += T(E3<QQ>(i, 2)) * P[i];
+        }
+        T* M = sM + (slot * NW + w) * 4 * 32 + lane;
+        M[0] = m0;
+        M[32] = mx;
+        M[64] = my;
+        M[96] = mz;
     };
 
     // f of the velocities crossing the z-face between ring slots lo (below) and hi (above)
     auto z_face = [&](int lo, int hi, const FaceM<T>& fz, T (&out)[NCROSS]) {
         const int l1 = max(lane - 1, 0), l2 = min(lane + 1, 31);
         const int w1 = max(w - 1, 0), w2 = min(w + 1, NW - 1);
-        T fb[QQ];
-        T phib = T(0);
+        const T phib = (T(1) - fz.w) * Ms(lo, w, 0, lane) + fz.w * Ms(hi, w, 0, lane) +
+                       fz.hcd * (Ms(lo, w, 3, lane) - Ms(hi, w, 3, lane)) -
+                       k.hc * (fz.tl * ((Ms(lo, w, 1, l2) - Ms(lo, w, 1, l1)) * cxj.ig +
+                                        (Ms(lo, w2, 2, lane) - Ms(lo, w1, 2, lane)) * cyk.ig) +
+                               fz.tr * ((Ms(hi, w, 1, l2) - Ms(hi, w, 1, l1)) * cxj.ig +
+                                        (Ms(hi, w2, 2, lane) - Ms(hi, w1, 2, lane)) * cyk.ig));
 #pragma unroll
         for (int i = 0; i < QQ; ++i) {
+            if (XS3<QQ>(i, 2) < 0) continue;
             const int en = E3<QQ>(i, 2), ex = E3<QQ>(i, 0), ey = E3<QQ>(i, 1);
             T v = ((T(1) - fz.w) + T(en) * fz.hcd) * Ps(lo, w, i, lane) + (fz.w - T(en) * fz.hcd) * Ps(hi, w, i, lane);
             if (ex != 0) {
@@ -168,24 +213,21 @@ __global__ void __launch_bounds__(NW * 32, 1) step3d(const Args3<T> a, const Con
                 const T gr = (Ps(hi, w2, i, lane) - Ps(hi, w1, i, lane)) * cyk.ig;
                 v -= T(ey) * k.hc * (fz.tl * gl + fz.tr * gr);
             }
-            fb[i] = v;
-            phib += v;
+            out[XS3<QQ>(i, 2)] = fma(k.a_f, v, horner3(k.hf, i, phib));
         }
-#pragma unroll
-        for (int i = 0; i < QQ; ++i)
-            if (XS3<QQ>(i, 2) >= 0) out[XS3<QQ>(i, 2)] = fma(k.a_f, fb[i], horner3(k.hf, i, phib));
     };
 
     // pipeline fill: planes z0-1 and z0, and the bottom face of plane z0
-    compute_P(z0 - 1, 0);
-    compute_P(z0, 1);
+    prefetch(z0 - 1);
+    compute_P(z0 - 1, 0, z0);
+    compute_P(z0, 1, z0 + 1);
     __syncthreads();
     T fB[NCROSS];
     if (interior_row) z_face(0, 1, a.fm[2][z0 + 1], fB);
 
     for (int z = z0; z < z1; ++z) {
         const int sm = (z - z0) % 3, so = (z - z0 + 1) % 3, sp = (z - z0 + 2) % 3;
-        compute_P(z + 1, sp);
+        compute_P(z + 1, sp, z + 2);
         __syncthreads();
         const CellM<T> czl = a.cm[2][z + 1];
         const int l1 = max(lane - 1, 0), l2 = min(lane + 1, 31);
@@ -195,59 +237,59 @@ __global__ void __launch_bounds__(NW * 32, 1) step3d(const Args3<T> a, const Con
 #pragma unroll
         for (int s = 0; s < NCROSS; ++s) fEx[s] = fNy[s] = fTz[s] = T(0);
         if (interior_row && lane <= 30) {
-            T fb[QQ];
-            T phib = T(0);
+            const int lr = lane + 1;
+            const T phib = (T(1) - fE.w) * Ms(so, w, 0, lane) + fE.w * Ms(so, w, 0, lr) +
+                           fE.hcd * (Ms(so, w, 1, lane) - Ms(so, w, 1, lr)) -
+                           k.hc * (fE.tl * ((Ms(so, w2, 2, lane) - Ms(so, w1, 2, lane)) * cyk.ig +
+                                            (Ms(sp, w, 3, lane) - Ms(sm, w, 3, lane)) * czl.ig) +
+                                   fE.tr * ((Ms(so, w2, 2, lr) - Ms(so, w1, 2, lr)) * cyk.ig +
+                                            (Ms(sp, w, 3, lr) - Ms(sm, w, 3, lr)) * czl.ig));
 #pragma unroll
             for (int i = 0; i < QQ; ++i) {
+                if (XS3<QQ>(i, 0) < 0) continue;
                 const int en = E3<QQ>(i, 0), ey = E3<QQ>(i, 1), ez = E3<QQ>(i, 2);
-                T v = ((T(1) - fE.w) + T(en) * fE.hcd) * Ps(so, w, i, lane) +
-                      (fE.w - T(en) * fE.hcd) * Ps(so, w, i, lane + 1);
+                T v = ((T(1) - fE.w) + T(en) * fE.hcd) * Ps(so, w, i, lane) + (fE.w - T(en) * fE.hcd) * Ps(so, w, i, lr);
                 if (ey != 0) {
                     const T gl = (Ps(so, w2, i, lane) - Ps(so, w1, i, lane)) * cyk.ig;
-                    const T gr = (Ps(so, w2, i, lane + 1) - Ps(so, w1, i, lane + 1)) * cyk.ig;
+                    const T gr = (Ps(so, w2, i, lr) - Ps(so, w1, i, lr)) * cyk.ig;
                     v -= T(ey) * k.hc * (fE.tl * gl + fE.tr * gr);
                 }
                 if (ez != 0) {
                     const T gl = (Ps(sp, w, i, lane) - Ps(sm, w, i, lane)) * czl.ig;
-                    const T gr = (Ps(sp, w, i, lane + 1) - Ps(sm, w, i, lane + 1)) * czl.ig;
+                    const T gr = (Ps(sp, w, i, lr) - Ps(sm, w, i, lr)) * czl.ig;
                     v -= T(ez) * k.hc * (fE.tl * gl + fE.tr * gr);
                 }
-                fb[i] = v;
-                phib += v;
+                fEx[XS3<QQ>(i, 0)] = fma(k.a_f, v, horner3(k.hf, i, phib));
             }
-#pragma unroll
-            for (int i = 0; i < QQ; ++i)
-                if (XS3<QQ>(i, 0) >= 0) fEx[XS3<QQ>(i, 0)] = fma(k.a_f, fb[i], horner3(k.hf, i, phib));
         }
         // north y-face (rows 0..NW-2, lanes 1..30): shared with the row above as its south face
         if (w <= NW - 2 && interior_col) {
-            T fb[QQ];
-            T phib = T(0);
+            const int wu = w + 1;
+            const T phib = (T(1) - fN.w) * Ms(so, w, 0, lane) + fN.w * Ms(so, wu, 0, lane) +
+                           fN.hcd * (Ms(so, w, 2, lane) - Ms(so, wu, 2, lane)) -
+                           k.hc * (fN.tl * ((Ms(so, w, 1, l2) - Ms(so, w, 1, l1)) * cxj.ig +
+                                            (Ms(sp, w, 3, lane) - Ms(sm, w, 3, lane)) * czl.ig) +
+                                   fN.tr * ((Ms(so, wu, 1, l2) - Ms(so, wu, 1, l1)) * cxj.ig +
+                                            (Ms(sp, wu, 3, lane) - Ms(sm, wu, 3, lane)) * czl.ig));
 #pragma unroll
             for (int i = 0; i < QQ; ++i) {
+                if (XS3<QQ>(i, 1) < 0) continue;
                 const int en = E3<QQ>(i, 1), ex = E3<QQ>(i, 0), ez = E3<QQ>(i, 2);
-                T v = ((T(1) - fN.w) + T(en) * fN.hcd) * Ps(so, w, i, lane) +
-                      (fN.w - T(en) * fN.hcd) * Ps(so, w + 1, i, lane);
+                T v = ((T(1) - fN.w) + T(en) * fN.hcd) * Ps(so, w, i, lane) + (fN.w - T(en) * fN.hcd) * Ps(so, wu, i, lane);
                 if (ex != 0) {
                     const T gl = (Ps(so, w, i, l2) - Ps(so, w, i, l1)) * cxj.ig;
-                    const T gr = (Ps(so, w + 1, i, l2) - Ps(so, w + 1, i, l1)) * cxj.ig;
+                    const T gr = (Ps(so, wu, i, l2) - Ps(so, wu, i, l1)) * cxj.ig;
                     v -= T(ex) * k.hc * (fN.tl * gl + fN.tr * gr);
                 }
                 if (ez != 0) {
                     const T gl = (Ps(sp, w, i, lane) - Ps(sm, w, i, lane)) * czl.ig;
-                    const T gr = (Ps(sp, w + 1, i, lane) - Ps(sm, w + 1, i, lane)) * czl.ig;
+                    const T gr = (Ps(sp, wu, i, lane) - Ps(sm, wu, i, lane)) * czl.ig;
                     v -= T(ez) * k.hc * (fN.tl * gl + fN.tr * gr);
                 }
-                fb[i] = v;
-                phib += v;
+                const T f = fma(k.a_f, v, horner3(k.hf, i, phib));
+                fNy[XS3<QQ>(i, 1)] = f;
+                sY[(w * NCROSS + XS3<QQ>(i, 1)) * 32 + lane] = f;
             }
-#pragma unroll
-            for (int i = 0; i < QQ; ++i)
-                if (XS3<QQ>(i, 1) >= 0) {
-                    const T f = fma(k.a_f, fb[i], horner3(k.hf, i, phib));
-                    fNy[XS3<QQ>(i, 1)] = f;
-                    sY[(w * NCROSS + XS3<QQ>(i, 1)) * 32 + lane] = f;
-                }
         }
         // top z-face (interior rows)
         if (interior_row) z_face(so, sp, a.fm[2][z + 2], fTz);
@@ -274,6 +316,7 @@ __global__ void __launch_bounds__(NW * 32, 1) step3d(const Args3<T> a, const Con
 #pragma unroll
         for (int s = 0; s < NCROSS; ++s) fB[s] = fTz[s];
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");  // the last prefetch lands before exit
 }
 
 // phi = sum_i ftilde_i (optional output) and per-block partial sums of |V| phi in double
