@@ -7,14 +7,15 @@
 // step contracted with mu (alpha enters through lambda = alpha / c_s^2 in the
 // weights of Eqs. 2.13, 2.21 and 2.22).
 //
-//   adj_face_kernel : per face, recomputes the forward face value fbar
-//     (Eqs. 2.19, 2.20, 2.26), phi_b and feq(phi_b), takes the adjoint g of
-//     the face flux from the two cells that use it (Eq. 2.12) and returns the
-//     adjoint of fbar through Eq. 2.22: A_i = a_f g_i + b_f sum_m g_m feq_m'(phi_b).
-//   adj_cell_kernel : per cell, gathers the adjoint of P = fbar^+ from the
-//     faces whose reconstruction used it (normal weights and the transposed
-//     central differences of the tangential slopes) and transposes Eqs. 2.21
-//     and 2.13 and phi = sum f.
+//   adj_p_kernel : forward P = fbar^+ and phi of every cell.
+//   adj_tile_kernel, per tile of cells: (faces) recomputes the forward face
+//     value fbar (Eqs. 2.19, 2.20, 2.26), phi_b and feq(phi_b), takes the
+//     adjoint g of the face flux from the two cells that use it (Eq. 2.12) and
+//     forms the adjoint of fbar through Eq. 2.22:
+//     A_i = a_f g_i + b_f sum_m g_m feq_m'(phi_b); (cells) gathers the adjoint
+//     of P from the faces whose reconstruction used it (normal weights and the
+//     transposed central differences of the tangential slopes) and transposes
+//     Eqs. 2.21 and 2.13 and phi = sum f.
 //   adj_wall_kernel : per cell next to a Dirichlet wall, folds the adjoint of
 //     the mirrored NEE ghost beyond the wall back into the cell (linear in the
 //     ghost's adjoint, so it is added to lam afterwards).
@@ -122,176 +123,11 @@ __device__ __forceinline__ void block_partial(double v, double* out, int accumul
     }
 }
 
-// Grid (ceil((nx+1)/blockDim.x), rows, 2): blockIdx.z = 0 for x-faces (threads
-// along jf, rows kc), 1 for y-faces (threads along jc, rows kf).
-template <typename T, int NC>
-__global__ void __launch_bounds__(128) adj_face_kernel(const StepArgs<T, NC> a, const Consts<T, NC> k,
-                                                       const AdjConsts<T, NC> ka, const AdjArgs<T> g) {
-    const int nx = a.nx, ny = a.ny;
-    const bool xface = blockIdx.z == 0;
-    const long long cplane = (long long)nx * ny;
-    const long long aplane = xface ? (long long)(nx + 1) * ny : (long long)nx * (ny + 1);
-    const int along = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nalong = xface ? nx + 1 : nx, nrows = xface ? ny : ny + 1;
-    const int n = xface ? nx : ny, nt = xface ? ny : nx;  // extents along the face normal and tangent
-    const bool per = xface ? a.xper : a.yper, tper = xface ? a.yper : a.xper;
-    const T bvL = xface ? k.bcv[0] : k.bcv[2], bvR = xface ? k.bcv[1] : k.bcv[3];
-    const T bvm = xface ? k.bcv[2] : k.bcv[0], bvp = xface ? k.bcv[3] : k.bcv[1];
-    double djdl = 0.0;
-    if (along < nalong) {
-        for (int row = blockIdx.y; row < nrows; row += gridDim.y) {
-            const int fidx = xface ? along : row;  // face index along its normal
-            const int tc = xface ? row : along;    // tangential index of its two cells
-            auto cell = [&](int inorm, int itan) -> long long {
-                return xface ? (long long)itan * nx + inorm : (long long)inorm * nx + itan;
-            };
-            const Nb L = nb_index(fidx - 1, n, per), R = nb_index(fidx, n, per);
-            const Nb Tm = nb_index(tc - 1, nt, tper), Tp = nb_index(tc + 1, nt, tper);
-            const FaceM<T> m = xface ? a.fx[fidx + 1] : a.fy[fidx + 1];
-            const T ig = xface ? a.cy[tc + 1].ig : a.cx[tc + 1].ig;
-            // forward: P of the two cells and their tangential slopes (none for a ghost)
-            T PL[Q], PR[Q], GL[Q], GR[Q], tA[Q], tB[Q];
-            load_P(k, g, cplane, cell(L.i, tc), L.ghost, bvL, PL);
-            load_P(k, g, cplane, cell(R.i, tc), R.ghost, bvR, PR);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) { GL[i] = T(0); GR[i] = T(0); }
-            if (!L.ghost) {
-                load_P(k, g, cplane, cell(L.i, Tp.i), Tp.ghost, bvp, tA);
-                load_P(k, g, cplane, cell(L.i, Tm.i), Tm.ghost, bvm, tB);
-#pragma unroll
-                for (int i = 0; i < Q; ++i) GL[i] = (tA[i] - tB[i]) * ig;
-            }
-            if (!R.ghost) {
-                load_P(k, g, cplane, cell(R.i, Tp.i), Tp.ghost, bvp, tA);
-                load_P(k, g, cplane, cell(R.i, Tm.i), Tm.ghost, bvm, tB);
-#pragma unroll
-                for (int i = 0; i < Q; ++i) GR[i] = (tA[i] - tB[i]) * ig;
-            }
-            T fb[Q];
-            T phib = T(0);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const T en = T(xface ? EX(i) : EY(i)), et = T(xface ? EY(i) : EX(i));
-                fb[i] = ((T(1) - m.w) + en * m.hcd) * PL[i] - et * k.hc * m.tl * GL[i] + (m.w - en * m.hcd) * PR[i] -
-                        et * k.hc * m.tr * GR[i];
-                phib += fb[i];
-            }
-            T fe[Q], dfe[Q];
-            feq_all(k, phib, fe);
-            dfeq_all(ka, phib, dfe);
-            // the two cells that use this face's flux (both neighbours for a periodic boundary face)
-            const long long offL = cell(L.i, tc), offR = cell(R.i, tc);
-            const T rL = L.ghost ? T(0) : (xface ? a.cx[L.i + 1].r : a.cy[L.i + 1].r);
-            const T rR = R.ghost ? T(0) : (xface ? a.cx[R.i + 1].r : a.cy[R.i + 1].r);
-            T gv[Q];
-            T sg = T(0);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const T en = T(xface ? EX(i) : EY(i));
-                T v = T(0);
-                if (en != T(0)) {
-                    if (!R.ghost) v += rR * g.mu[i * cplane + offR];
-                    if (!L.ghost) v -= rL * g.mu[i * cplane + offL];
-                    v *= en;
-                }
-                gv[i] = v;
-                sg += v * dfe[i];
-            }
-            T* A = xface ? g.Ax + (long long)row * (nx + 1) + along : g.Ay + (long long)row * nx + along;
-            T s = T(0);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                A[i * aplane] = fma(ka.a_f, gv[i], ka.b_f * sg);
-                s += gv[i] * fma(ka.da_f, fb[i], ka.db_f * fe[i]);
-            }
-            if (!(per && fidx == n)) djdl += double(s);  // a periodic face is counted once in dJ/dlambda
-        }
-    }
-    block_partial<T>(djdl, g.partial + (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x, g.accumulate);
-}
-
-// Grid (ceil(nx/blockDim.x), rows): threads along j, blocks over rows kr.
-template <typename T, int NC>
-__global__ void __launch_bounds__(128, 4) adj_cell_kernel(const StepArgs<T, NC> a, const Consts<T, NC> k,
-                                                       const AdjConsts<T, NC> ka, const AdjArgs<T> g,
-                                                       const int face_blocks) {
-    const int nx = a.nx, ny = a.ny;
-    const long long cplane = (long long)nx * ny;
-    const long long xplane = (long long)(nx + 1) * ny, yplane = (long long)nx * (ny + 1);
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    double djdl = 0.0;
-    if (j < nx) {
-        const Nb xm = nb_index(j - 1, nx, a.xper), xp = nb_index(j + 1, nx, a.xper);
-        const T igxm = xm.ghost ? T(0) : a.cx[xm.i + 1].ig, igxp = xp.ghost ? T(0) : a.cx[xp.i + 1].ig;
-        const FaceM<T> fxW = a.fx[j + 1], fxE = a.fx[j + 2];
-        for (int kr = blockIdx.y; kr < ny; kr += gridDim.y) {
-            const long long t = (long long)kr * nx + j;
-            const Nb ym = nb_index(kr - 1, ny, a.yper), yp = nb_index(kr + 1, ny, a.yper);
-            const T igym = ym.ghost ? T(0) : a.cy[ym.i + 1].ig, igyp = yp.ghost ? T(0) : a.cy[yp.i + 1].ig;
-            const FaceM<T> fyS = a.fy[kr + 1], fyN = a.fy[kr + 2];
-            // x-face adjoints of faces j, j+1 in rows kr, kr-1, kr+1; y-face adjoints of
-            // faces kr, kr+1 (offset nx) in columns j, j-1, j+1
-            const T* Ax0 = g.Ax + (long long)kr * (nx + 1) + j;
-            const T* Axm = g.Ax + (long long)ym.i * (nx + 1) + j;
-            const T* Axp = g.Ax + (long long)yp.i * (nx + 1) + j;
-            const T* Ay0 = g.Ay + (long long)kr * nx + j;
-            const T* Aym = g.Ay + (long long)kr * nx + xm.i;
-            const T* Ayp = g.Ay + (long long)kr * nx + xp.i;
-            T Pb[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const T ex = T(EX(i)), ey = T(EY(i));
-                const T* ax = Ax0 + i * xplane;
-                const T* ay = Ay0 + i * yplane;
-                // normal weights of this cell in its four faces
-                T v = ((T(1) - fxE.w) + ex * fxE.hcd) * ax[1] + (fxW.w - ex * fxW.hcd) * ax[0] +
-                      ((T(1) - fyN.w) + ey * fyN.hcd) * ay[nx] + (fyS.w - ey * fyS.hcd) * ay[0];
-                // tangential: this P enters G^y of the cells above and below, used by their x-faces
-                if (EY(i) != 0) {
-                    const T c = -ey * k.hc;
-                    if (!ym.ghost) v += c * igym * (fxE.tl * Axm[i * xplane + 1] + fxW.tr * Axm[i * xplane]);
-                    if (!yp.ghost) v -= c * igyp * (fxE.tl * Axp[i * xplane + 1] + fxW.tr * Axp[i * xplane]);
-                }
-                // and G^x of the cells left and right, used by their y-faces
-                if (EX(i) != 0) {
-                    const T c = -ex * k.hc;
-                    if (!xm.ghost) v += c * igxm * (fyN.tl * Aym[i * yplane + nx] + fyS.tr * Aym[i * yplane]);
-                    if (!xp.ghost) v -= c * igxp * (fyN.tl * Ayp[i * yplane + nx] + fyS.tr * Ayp[i * yplane]);
-                }
-                Pb[i] = v;
-            }
-            // forward cell quantities
-            T ft[Q], mu[Q], fe[Q], dfe[Q];
-            T phi = T(0);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                ft[i] = g.f[i * cplane + t];
-                mu[i] = g.mu[i * cplane + t];
-                phi += ft[i];
-            }
-            feq_all(k, phi, fe);
-            dfeq_all(ka, phi, dfe);
-            T phibar = T(0);
-            // P = a_bp f + b_bp feq(phi) (Eq. 2.21), Fp = a_tp f + b_tp feq(phi) (Eq. 2.13), phi = sum f
-            T s = T(0);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                phibar += (ka.b_bp * Pb[i] + ka.b_tp * mu[i]) * dfe[i];
-                s += Pb[i] * fma(ka.da_bp, ft[i], ka.db_bp * fe[i]) + mu[i] * fma(ka.da_tp, ft[i], ka.db_tp * fe[i]);
-            }
-            djdl += double(s);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) g.lam[i * cplane + t] = fma(ka.a_bp, Pb[i], fma(ka.a_tp, mu[i], phibar));
-        }
-    }
-    block_partial<T>(djdl, g.partial + face_blocks + blockIdx.y * gridDim.x + blockIdx.x, g.accumulate);
-}
-
 // Cells next to a Dirichlet wall.  The mirrored NEE ghost beyond the wall has
 // P_g = feq(2 bv - phi) + P - feq(phi) of this cell; its adjoint (the x- or
-// y-face weights of the ghost, as in adj_cell_kernel) folds back into the cell.
+// y-face weights of the ghost, as in the cell gather of adj_tile_kernel) folds back into the cell.
 // Everything the fold adds is linear in the ghost adjoints, so it is added to
-// the lam that adj_cell_kernel wrote.  Threads enumerate rows 0 and ny-1 (when
+// the lam that adj_tile_kernel wrote.  Threads enumerate rows 0 and ny-1 (when
 // y has walls), then columns 0 and nx-1 of the remaining rows (when x has walls).
 template <typename T, int NC>
 __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs<T, NC> a, const Consts<T, NC> k,
@@ -396,6 +232,250 @@ __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs<T, NC> a, 
         for (int i = 0; i < Q; ++i) g.lam[i * cplane + c] += fma(ka.a_bp, PG[i], dphibar);
     }
     block_partial<T>(djdl, g.partial + first_partial + blockIdx.x, g.accumulate);
+}
+
+// The face and cell parts of the adjoint step in one launch.  A CTA of TX x TY
+// threads owns the cells j0..j0+TX-1, k0..k0+TY-1.  It stages P (with the ghost
+// transform) for a two-cell halo and mu for a one-cell halo in shared memory,
+// computes the adjoints A of every face its cells gather from (x-faces j0..j0+TX
+// of rows k0-1..k0+TY, y-faces k0..k0+TY of columns j0-1..j0+TX), then gathers
+// the adjoint of P for each of its cells from those shared face adjoints.  A face's dJ/dlambda term is counted by the CTA that owns it (its cell
+// range, plus the last face of the domain); with walls, owned faces are also
+// written to Ax / Ay for adj_wall_kernel.
+struct TileIdx {
+    int i;      // interior index (wrapped), or the interior cell a ghost mirrors
+    int state;  // 0 interior, 1 ghost (one cell beyond a Dirichlet wall), 2 beyond any use
+};
+__device__ __forceinline__ TileIdx tile_idx(int i, int n, bool per) {
+    if (per) {
+        i %= n;
+        return TileIdx{i < 0 ? i + n : i, 0};
+    }
+    if (i >= 0 && i < n) return TileIdx{i, 0};
+    if (i == -1) return TileIdx{0, 1};
+    if (i == n) return TileIdx{n - 1, 1};
+    return TileIdx{0, 2};
+}
+
+template <typename T, int TX, int TY>
+struct AdjTile {
+    static constexpr int PW = TX + 4, PH = TY + 4;  // P: columns j0-2.., rows k0-2..
+    static constexpr int MW = TX + 2, MH = TY + 2;  // mu: columns j0-1.., rows k0-1..
+    static constexpr int XW = TX + 1, XH = TY + 2;  // x-faces j0..j0+TX, rows k0-1..k0+TY
+    static constexpr int YW = TX + 2, YH = TY + 1;  // y-faces k0..k0+TY, columns j0-1..j0+TX
+    static constexpr size_t bytes() { return size_t(Q) * (PW * PH + MW * MH + XW * XH + YW * YH) * sizeof(T); }
+};
+
+template <typename T, int NC, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) adj_tile_kernel(const StepArgs<T, NC> a, const Consts<T, NC> k,
+                                                           const AdjConsts<T, NC> ka, const AdjArgs<T> g,
+                                                           const int write_faces) {
+    using L = AdjTile<T, TX, TY>;
+    extern __shared__ __align__(16) unsigned char adj_smem[];
+    T* sP = reinterpret_cast<T*>(adj_smem);
+    T* sMu = sP + Q * L::PW * L::PH;
+    T* sAx = sMu + Q * L::MW * L::MH;
+    T* sAy = sAx + Q * L::XW * L::XH;
+    const int nx = a.nx, ny = a.ny;
+    const long long cplane = (long long)nx * ny;
+    const long long xplane = (long long)(nx + 1) * ny, yplane = (long long)nx * (ny + 1);
+    const int j0 = blockIdx.x * TX, k0 = blockIdx.y * TY;
+    const int tid = threadIdx.x, nthr = TX * TY;
+    double djdl = 0.0;
+
+    // 1. P tile (two-cell halo) and mu tile (one-cell halo)
+    for (int e = tid; e < L::PW * L::PH; e += nthr) {
+        const int pc = e % L::PW, pr = e / L::PW;
+        const TileIdx X = tile_idx(j0 - 2 + pc, nx, a.xper), Y = tile_idx(k0 - 2 + pr, ny, a.yper);
+        T P[Q];
+        if (X.state == 2 || Y.state == 2 || (X.state == 1 && Y.state == 1)) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) P[i] = T(0);  // beyond use, or a corner ghost (zero weights only)
+        } else {
+            const bool gx = X.state == 1;
+            const T bv = gx ? (j0 - 2 + pc < 0 ? k.bcv[0] : k.bcv[1]) : (k0 - 2 + pr < 0 ? k.bcv[2] : k.bcv[3]);
+            load_P(k, g, cplane, (long long)Y.i * nx + X.i, X.state == 1 || Y.state == 1, bv, P);
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) sP[(i * L::PH + pr) * L::PW + pc] = P[i];
+    }
+    for (int e = tid; e < L::MW * L::MH; e += nthr) {
+        const int mc = e % L::MW, mr = e / L::MW;
+        const TileIdx X = tile_idx(j0 - 1 + mc, nx, a.xper), Y = tile_idx(k0 - 1 + mr, ny, a.yper);
+        const bool real = X.state == 0 && Y.state == 0;
+        const long long c = (long long)Y.i * nx + X.i;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) sMu[(i * L::MH + mr) * L::MW + mc] = real ? g.mu[i * cplane + c] : T(0);
+    }
+    __syncthreads();
+
+    auto Pt = [&](int i, int r, int c) -> T { return sP[(i * L::PH + r) * L::PW + c]; };
+    auto Mt = [&](int i, int r, int c) -> T { return sMu[(i * L::MH + r) * L::MW + c]; };
+
+    // 2a. x-face adjoints: face jf = j0 + xc between cells jf-1 and jf of row k0 - 1 + xr
+    for (int e = tid; e < L::XW * L::XH; e += nthr) {
+        const int xc = e % L::XW, xr = e / L::XW;
+        const int jf = j0 + xc, row = k0 - 1 + xr;
+        const TileIdx Rw = tile_idx(row, ny, a.yper);
+        T A[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) A[i] = T(0);
+        if (jf <= nx && Rw.state == 0) {
+            const bool lghost = !a.xper && jf == 0, rghost = !a.xper && jf == nx;
+            const FaceM<T> m = a.fx[jf + 1];
+            const T ig = a.cy[Rw.i + 1].ig;
+            const int pl = xc + 1, pr = xc + 2, prow = xr + 1;  // P tile coordinates of L, R
+            T fb[Q];
+            T phib = T(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const T en = T(EX(i)), et = T(EY(i));
+                const T GL = lghost ? T(0) : (Pt(i, prow + 1, pl) - Pt(i, prow - 1, pl)) * ig;
+                const T GR = rghost ? T(0) : (Pt(i, prow + 1, pr) - Pt(i, prow - 1, pr)) * ig;
+                fb[i] = ((T(1) - m.w) + en * m.hcd) * Pt(i, prow, pl) - et * k.hc * m.tl * GL +
+                        (m.w - en * m.hcd) * Pt(i, prow, pr) - et * k.hc * m.tr * GR;
+                phib += fb[i];
+            }
+            T fe[Q], dfe[Q];
+            feq_all(k, phib, fe);
+            dfeq_all(ka, phib, dfe);
+            const TileIdx Lc = tile_idx(jf - 1, nx, a.xper), Rc = tile_idx(jf, nx, a.xper);
+            const T rL = lghost ? T(0) : a.cx[Lc.i + 1].r, rR = rghost ? T(0) : a.cx[Rc.i + 1].r;
+            T gv[Q];
+            T sg = T(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                T v = T(0);
+                if (EX(i) != 0) v = T(EX(i)) * (rR * Mt(i, xr, xc + 1) - rL * Mt(i, xr, xc));
+                gv[i] = v;
+                sg += v * dfe[i];
+            }
+            T sdl = T(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                A[i] = fma(ka.a_f, gv[i], ka.b_f * sg);
+                sdl += gv[i] * fma(ka.da_f, fb[i], ka.db_f * fe[i]);
+            }
+            const bool owned = (xr >= 1 && xr <= TY && row < ny) && (xc < TX || jf == nx);
+            if (owned && !(a.xper && jf == nx)) djdl += double(sdl);  // a periodic face is counted once
+            if (owned && write_faces) {
+                T* Ag = g.Ax + (long long)row * (nx + 1) + jf;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) Ag[i * xplane] = A[i];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) sAx[(i * L::XH + xr) * L::XW + xc] = A[i];
+    }
+    // 2b. y-face adjoints: face kf = k0 + yr between rows kf-1 and kf of column j0 - 1 + yc
+    for (int e = tid; e < L::YW * L::YH; e += nthr) {
+        const int yc = e % L::YW, yr = e / L::YW;
+        const int kf = k0 + yr, col = j0 - 1 + yc;
+        const TileIdx Cw = tile_idx(col, nx, a.xper);
+        T A[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) A[i] = T(0);
+        if (kf <= ny && Cw.state == 0) {
+            const bool lghost = !a.yper && kf == 0, rghost = !a.yper && kf == ny;
+            const FaceM<T> m = a.fy[kf + 1];
+            const T ig = a.cx[Cw.i + 1].ig;
+            const int pc = yc + 1, pl = yr + 1, pr = yr + 2;  // P tile column, rows of L (below) and R
+            T fb[Q];
+            T phib = T(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const T en = T(EY(i)), et = T(EX(i));
+                const T GL = lghost ? T(0) : (Pt(i, pl, pc + 1) - Pt(i, pl, pc - 1)) * ig;
+                const T GR = rghost ? T(0) : (Pt(i, pr, pc + 1) - Pt(i, pr, pc - 1)) * ig;
+                fb[i] = ((T(1) - m.w) + en * m.hcd) * Pt(i, pl, pc) - et * k.hc * m.tl * GL +
+                        (m.w - en * m.hcd) * Pt(i, pr, pc) - et * k.hc * m.tr * GR;
+                phib += fb[i];
+            }
+            T fe[Q], dfe[Q];
+            feq_all(k, phib, fe);
+            dfeq_all(ka, phib, dfe);
+            const TileIdx Lr = tile_idx(kf - 1, ny, a.yper), Rr = tile_idx(kf, ny, a.yper);
+            const T rL = lghost ? T(0) : a.cy[Lr.i + 1].r, rR = rghost ? T(0) : a.cy[Rr.i + 1].r;
+            T gv[Q];
+            T sg = T(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                T v = T(0);
+                if (EY(i) != 0) v = T(EY(i)) * (rR * Mt(i, yr + 1, yc) - rL * Mt(i, yr, yc));
+                gv[i] = v;
+                sg += v * dfe[i];
+            }
+            T sdl = T(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                A[i] = fma(ka.a_f, gv[i], ka.b_f * sg);
+                sdl += gv[i] * fma(ka.da_f, fb[i], ka.db_f * fe[i]);
+            }
+            const bool owned = (yc >= 1 && yc <= TX && col < nx) && (yr < TY || kf == ny);
+            if (owned && !(a.yper && kf == ny)) djdl += double(sdl);
+            if (owned && write_faces) {
+                T* Ag = g.Ay + (long long)kf * nx + col;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) Ag[i * yplane] = A[i];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) sAy[(i * L::YH + yr) * L::YW + yc] = A[i];
+    }
+    __syncthreads();
+
+    // 3. cells: gather the adjoint of P from the shared face adjoints
+    const int tx = tid % TX, ty = tid / TX;
+    const int j = j0 + tx, kr = k0 + ty;
+    if (j < nx && kr < ny) {
+        const long long t = (long long)kr * nx + j;
+        const Nb xm = nb_index(j - 1, nx, a.xper), xp = nb_index(j + 1, nx, a.xper);
+        const Nb ym = nb_index(kr - 1, ny, a.yper), yp = nb_index(kr + 1, ny, a.yper);
+        const T igxm = xm.ghost ? T(0) : a.cx[xm.i + 1].ig, igxp = xp.ghost ? T(0) : a.cx[xp.i + 1].ig;
+        const T igym = ym.ghost ? T(0) : a.cy[ym.i + 1].ig, igyp = yp.ghost ? T(0) : a.cy[yp.i + 1].ig;
+        const FaceM<T> fxW = a.fx[j + 1], fxE = a.fx[j + 2], fyS = a.fy[kr + 1], fyN = a.fy[kr + 2];
+        // x-face (face j0+xc, row k0-1+xr) and y-face (column j0-1+yc, face k0+yr) adjoints
+        auto Ax = [&](int i, int xc, int xr) -> T { return sAx[(i * L::XH + xr) * L::XW + xc]; };
+        auto Ay = [&](int i, int yc, int yr) -> T { return sAy[(i * L::YH + yr) * L::YW + yc]; };
+        T Pb[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const T ex = T(EX(i)), ey = T(EY(i));
+            T v = ((T(1) - fxE.w) + ex * fxE.hcd) * Ax(i, tx + 1, ty + 1) + (fxW.w - ex * fxW.hcd) * Ax(i, tx, ty + 1) +
+                  ((T(1) - fyN.w) + ey * fyN.hcd) * Ay(i, tx + 1, ty + 1) + (fyS.w - ey * fyS.hcd) * Ay(i, tx + 1, ty);
+            if (EY(i) != 0) {
+                const T c = -ey * k.hc;
+                if (!ym.ghost) v += c * igym * (fxE.tl * Ax(i, tx + 1, ty) + fxW.tr * Ax(i, tx, ty));
+                if (!yp.ghost) v -= c * igyp * (fxE.tl * Ax(i, tx + 1, ty + 2) + fxW.tr * Ax(i, tx, ty + 2));
+            }
+            if (EX(i) != 0) {
+                const T c = -ex * k.hc;
+                if (!xm.ghost) v += c * igxm * (fyN.tl * Ay(i, tx, ty + 1) + fyS.tr * Ay(i, tx, ty));
+                if (!xp.ghost) v -= c * igxp * (fyN.tl * Ay(i, tx + 2, ty + 1) + fyS.tr * Ay(i, tx + 2, ty));
+            }
+            Pb[i] = v;
+        }
+        T ft[Q], mu[Q], fe[Q], dfe[Q];
+        T phi = T(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            ft[i] = g.f[i * cplane + t];
+            mu[i] = Mt(i, ty + 1, tx + 1);
+            phi += ft[i];
+        }
+        feq_all(k, phi, fe);
+        dfeq_all(ka, phi, dfe);
+        T phibar = T(0), s = T(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            phibar += (ka.b_bp * Pb[i] + ka.b_tp * mu[i]) * dfe[i];
+            s += Pb[i] * fma(ka.da_bp, ft[i], ka.db_bp * fe[i]) + mu[i] * fma(ka.da_tp, ft[i], ka.db_tp * fe[i]);
+        }
+        djdl += double(s);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g.lam[i * cplane + t] = fma(ka.a_bp, Pb[i], fma(ka.a_tp, mu[i], phibar));
+    }
+    block_partial<T>(djdl, g.partial + blockIdx.y * gridDim.x + blockIdx.x, g.accumulate);
 }
 
 // *dj_dalpha += (sum of the partials) / c_s^2, in a fixed order (one block of 1024).

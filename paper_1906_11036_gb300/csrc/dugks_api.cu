@@ -458,21 +458,14 @@ AdjConsts<T, NC> make_adj_consts(const dugks_ctx* ctx) {
     return ka;
 }
 
-// adjoint grids: 128 threads along a row, one block row per grid row (rows
-// beyond 65535 are looped over); faces in two z-slices (x-faces, y-faces)
+// adjoint: tiles of kAdjTX x kAdjTY cells (adj_tile_kernel); the wall fold uses 128-thread blocks
 constexpr int kAdjThreads = 128;
-dim3 adj_face_grid(const dugks_ctx* ctx) {
-    return dim3(unsigned((ctx->nx + 1 + kAdjThreads - 1) / kAdjThreads), unsigned(std::min(ctx->ny + 1, 65535)), 2u);
+constexpr int kAdjTX = 32, kAdjTY = 8;
+dim3 adj_tile_grid(const dugks_ctx* ctx) {
+    return dim3(unsigned((ctx->nx + kAdjTX - 1) / kAdjTX), unsigned((ctx->ny + kAdjTY - 1) / kAdjTY), 1u);
 }
-dim3 adj_cell_grid(const dugks_ctx* ctx) {
-    return dim3(unsigned((ctx->nx + kAdjThreads - 1) / kAdjThreads), unsigned(std::min(ctx->ny, 65535)), 1u);
-}
-int adj_face_blocks(const dugks_ctx* ctx) {
-    const dim3 d = adj_face_grid(ctx);
-    return int(d.x * d.y * d.z);
-}
-int adj_cell_blocks(const dugks_ctx* ctx) {
-    const dim3 d = adj_cell_grid(ctx);
+int adj_tile_blocks(const dugks_ctx* ctx) {
+    const dim3 d = adj_tile_grid(ctx);
     return int(d.x * d.y);
 }
 // cells next to a Dirichlet wall (adj_wall_kernel), each counted once
@@ -485,9 +478,13 @@ long long adj_wall_cells(const dugks_ctx* ctx) {
     return nrc + ncc;
 }
 int adj_wall_blocks(const dugks_ctx* ctx) { return int((adj_wall_cells(ctx) + kAdjThreads - 1) / kAdjThreads); }
-int adj_partials(const dugks_ctx* ctx) { return adj_face_blocks(ctx) + adj_cell_blocks(ctx) + adj_wall_blocks(ctx); }
+int adj_partials(const dugks_ctx* ctx) { return adj_tile_blocks(ctx) + adj_wall_blocks(ctx); }
 
 dugks_status adj_alloc(dugks_ctx* ctx) {
+    if (adj_tile_grid(ctx).y > 65535u) {
+        ctx->last_error = "the adjoint supports ny <= 524280";
+        return DUGKS_ERR_UNSUPPORTED;
+    }
     if (ctx->adj_ax) return DUGKS_OK;
     cudaError_t e;
     const size_t nxf = size_t(ctx->nx + 1) * ctx->ny, nyf = size_t(ctx->nx) * (ctx->ny + 1);
@@ -531,13 +528,17 @@ cudaError_t launch_adjoint_step(dugks_ctx* ctx, const void* f, const void* mu, v
     g.phi = static_cast<T*>(ctx->adj_phi);
     g.partial = ctx->adj_partial;
     g.accumulate = dj_dalpha ? 0 : 1;
-    const int fb = adj_face_blocks(ctx), cb = adj_cell_blocks(ctx);
+    const int tb = adj_tile_blocks(ctx);
     const long long ncell = (long long)ctx->nx * ctx->ny;
-    adj_p_kernel<T, NC><<<int(std::min<long long>((ncell + 255) / 256, 65535)), 256, 0, ctx->stream>>>(a, k, g);
-    adj_face_kernel<T, NC><<<adj_face_grid(ctx), kAdjThreads, 0, ctx->stream>>>(a, k, ka, g);
-    adj_cell_kernel<T, NC><<<adj_cell_grid(ctx), kAdjThreads, 0, ctx->stream>>>(a, k, ka, g, fb);
+    const size_t smem = AdjTile<T, kAdjTX, kAdjTY>::bytes();
+    cudaError_t e = cudaFuncSetAttribute(adj_tile_kernel<T, NC, kAdjTX, kAdjTY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
     const int wb = adj_wall_blocks(ctx);
-    if (wb > 0) adj_wall_kernel<T, NC><<<wb, kAdjThreads, 0, ctx->stream>>>(a, k, ka, g, fb + cb);
+    adj_p_kernel<T, NC><<<int(std::min<long long>((ncell + 255) / 256, 65535)), 256, 0, ctx->stream>>>(a, k, g);
+    adj_tile_kernel<T, NC, kAdjTX, kAdjTY><<<adj_tile_grid(ctx), kAdjTX * kAdjTY, smem, ctx->stream>>>(a, k, ka, g,
+                                                                                                     wb > 0 ? 1 : 0);
+    if (wb > 0) adj_wall_kernel<T, NC><<<wb, kAdjThreads, 0, ctx->stream>>>(a, k, ka, g, tb);
     if (dj_dalpha) return launch_adj_sum(ctx, dj_dalpha);
     return cudaGetLastError();
 }
