@@ -7,8 +7,8 @@
 // step contracted with mu (alpha enters through lambda = alpha / c_s^2 in the
 // weights of Eqs. 2.13, 2.21 and 2.22).
 //
-//   adj_p_kernel : forward P = fbar^+ and phi of every cell.
-//   adj_tile_kernel, per tile of cells: (faces) recomputes the forward face
+//   adj_tile_kernel, per tile of cells: (P) recomputes the forward P = fbar^+
+//     of its cells and halo (Eq. 2.21, mirrored ghosts); (faces) the forward face
 //     value fbar (Eqs. 2.19, 2.20, 2.26), phi_b and feq(phi_b), takes the
 //     adjoint g of the face flux from the two cells that use it (Eq. 2.12) and
 //     forms the adjoint of fbar through Eq. 2.22:
@@ -40,30 +40,9 @@ struct AdjArgs {
     T* lam;            // out: dJ/d ftilde^n
     T* Ax;             // x-face adjoints [Q][ny][nx+1]
     T* Ay;             // y-face adjoints [Q][ny+1][nx]
-    T* P;              // forward fbar^+ of every cell [Q][ny][nx] (adj_p_kernel)
-    T* phi;            // forward phi of every cell [ny][nx]
     double* partial;   // per-block partial sums of dJ/dlambda (faces, cells, wall cells)
     int accumulate;    // 1: add to the partials (a reverse sweep sums them once at its end); 0: overwrite
 };
-
-// Forward P = fbar^+ (Eq. 2.21) and phi of every cell, once per adjoint step.
-template <typename T, int NC>
-__global__ void __launch_bounds__(256) adj_p_kernel(const StepArgs<T, NC> a, const Consts<T, NC> k, const AdjArgs<T> g) {
-    const long long n = (long long)a.nx * a.ny;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        T ft[Q], fe[Q];
-        T phi = T(0);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            ft[i] = g.f[i * n + c];
-            phi += ft[i];
-        }
-        feq_all(k, phi, fe);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) g.P[i * n + c] = fma(k.a_bp, ft[i], k.b_bp * fe[i]);
-        g.phi[c] = phi;
-    }
-}
 
 // Neighbour index along one direction, for i in [-1, n]: the interior cell
 // (periodic image) or, past a Dirichlet wall, the adjacent interior cell whose
@@ -76,23 +55,6 @@ __device__ __forceinline__ Nb nb_index(int i, int n, bool per) {
     if (i < 0) return per ? Nb{i + n, false} : Nb{0, true};
     if (i >= n) return per ? Nb{i - n, false} : Nb{n - 1, true};
     return Nb{i, false};
-}
-
-// P of cell c from the P buffer, or of the mirrored NEE ghost next to it:
-// P_g = feq(2 bv - phi) + P - feq(phi).
-template <typename T, int NC>
-__device__ __forceinline__ void load_P(const Consts<T, NC>& k, const AdjArgs<T>& g, long long n, long long c,
-                                       bool ghost, T bv, T (&P)[Q]) {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) P[i] = g.P[i * n + c];
-    if (ghost) {
-        const T phi = g.phi[c];
-        T fe[Q], fg[Q];
-        feq_all(k, phi, fe);
-        feq_all(k, T(2) * bv - phi, fg);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) P[i] = fg[i] + (P[i] - fe[i]);
-    }
 }
 
 template <typename T, int NC>
@@ -291,10 +253,26 @@ __global__ void __launch_bounds__(TX * TY) adj_tile_kernel(const StepArgs<T, NC>
         if (X.state == 2 || Y.state == 2 || (X.state == 1 && Y.state == 1)) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) P[i] = T(0);  // beyond use, or a corner ghost (zero weights only)
-        } else {
-            const bool gx = X.state == 1;
-            const T bv = gx ? (j0 - 2 + pc < 0 ? k.bcv[0] : k.bcv[1]) : (k0 - 2 + pr < 0 ? k.bcv[2] : k.bcv[3]);
-            load_P(k, g, cplane, (long long)Y.i * nx + X.i, X.state == 1 || Y.state == 1, bv, P);
+        } else {  // P = fbar^+ (Eq. 2.21) from ftilde, and the mirrored ghost P_g = feq(2 bv - phi) + P - feq(phi)
+            const long long c = (long long)Y.i * nx + X.i;
+            T ft[Q], fe[Q];
+            T phi = T(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                ft[i] = g.f[i * cplane + c];
+                phi += ft[i];
+            }
+            feq_all(k, phi, fe);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) P[i] = fma(k.a_bp, ft[i], k.b_bp * fe[i]);
+            if (X.state == 1 || Y.state == 1) {
+                const bool gx = X.state == 1;
+                const T bv = gx ? (j0 - 2 + pc < 0 ? k.bcv[0] : k.bcv[1]) : (k0 - 2 + pr < 0 ? k.bcv[2] : k.bcv[3]);
+                T fg[Q];
+                feq_all(k, T(2) * bv - phi, fg);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) P[i] = fg[i] + (P[i] - fe[i]);
+            }
         }
 #pragma unroll
         for (int i = 0; i < Q; ++i) sP[(i * L::PH + pr) * L::PW + pc] = P[i];

@@ -68,8 +68,6 @@ struct dugks_ctx {
     // adjoint work buffers (allocated on first use)
     void* adj_ax = nullptr;
     void* adj_ay = nullptr;
-    void* adj_p = nullptr;    // forward fbar^+ [Q][ny][nx]
-    void* adj_phi = nullptr;  // forward phi [ny][nx]
     double* adj_partial = nullptr;
     double* adj_dalpha = nullptr;
     // source terms (dugks_set_source)
@@ -419,7 +417,7 @@ void free_ctx(dugks_ctx* ctx) {
     cudaGetDevice(&prev);
     cudaSetDevice(ctx->device);
     for (void* p : {ctx->buf[0], ctx->buf[1], ctx->fxm, ctx->fym, ctx->cxm, ctx->cym, ctx->adj_ax, ctx->adj_ay,
-                    ctx->adj_p, ctx->adj_phi, ctx->src_field, ctx->hist[0], ctx->hist[1],
+                    ctx->src_field, ctx->hist[0], ctx->hist[1],
                     static_cast<void*>(ctx->adj_partial), static_cast<void*>(ctx->adj_dalpha)})
         if (p) cudaFree(p);
     for (void* p : {static_cast<void*>(ctx->dxv), static_cast<void*>(ctx->dyv), static_cast<void*>(ctx->staging),
@@ -490,8 +488,6 @@ dugks_status adj_alloc(dugks_ctx* ctx) {
     const size_t nxf = size_t(ctx->nx + 1) * ctx->ny, nyf = size_t(ctx->nx) * (ctx->ny + 1);
     if ((e = cudaMalloc(&ctx->adj_ax, Q * nxf * ctx->elem)) != cudaSuccess ||
         (e = cudaMalloc(&ctx->adj_ay, Q * nyf * ctx->elem)) != cudaSuccess ||
-        (e = cudaMalloc(&ctx->adj_p, Q * size_t(ctx->nx) * ctx->ny * ctx->elem)) != cudaSuccess ||
-        (e = cudaMalloc(&ctx->adj_phi, size_t(ctx->nx) * ctx->ny * ctx->elem)) != cudaSuccess ||
         (e = cudaMalloc(&ctx->adj_partial,
                         sizeof(double) * size_t(adj_partials(ctx)))) !=
             cudaSuccess ||
@@ -524,18 +520,14 @@ cudaError_t launch_adjoint_step(dugks_ctx* ctx, const void* f, const void* mu, v
     g.lam = static_cast<T*>(lam);
     g.Ax = static_cast<T*>(ctx->adj_ax);
     g.Ay = static_cast<T*>(ctx->adj_ay);
-    g.P = static_cast<T*>(ctx->adj_p);
-    g.phi = static_cast<T*>(ctx->adj_phi);
     g.partial = ctx->adj_partial;
     g.accumulate = dj_dalpha ? 0 : 1;
     const int tb = adj_tile_blocks(ctx);
-    const long long ncell = (long long)ctx->nx * ctx->ny;
     const size_t smem = AdjTile<T, kAdjTX, kAdjTY>::bytes();
     cudaError_t e = cudaFuncSetAttribute(adj_tile_kernel<T, NC, kAdjTX, kAdjTY>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     const int wb = adj_wall_blocks(ctx);
-    adj_p_kernel<T, NC><<<int(std::min<long long>((ncell + 255) / 256, 65535)), 256, 0, ctx->stream>>>(a, k, g);
     adj_tile_kernel<T, NC, kAdjTX, kAdjTY><<<adj_tile_grid(ctx), kAdjTX * kAdjTY, smem, ctx->stream>>>(a, k, ka, g,
                                                                                                      wb > 0 ? 1 : 0);
     if (wb > 0) adj_wall_kernel<T, NC><<<wb, kAdjThreads, 0, ctx->stream>>>(a, k, ka, g, tb);
