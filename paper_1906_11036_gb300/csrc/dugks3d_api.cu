@@ -159,7 +159,7 @@ Args3<T> args3(const dugks_3d_ctx* ctx) {
 
 template <typename T, int QQ, int NC, int NW>
 constexpr size_t smem3() {
-    return size_t(3 * NW * QQ * 32 + NW * NCROSS * 32 + 3 * NW * 4 * 32 + NW * QQ * 32) * sizeof(T);
+    return size_t(3 * NW * QQ * 32 + NW * NCROSS * 32 + 3 * NW * 4 * 32 + 3 * NW * QQ * 32) * sizeof(T);
 }
 
 template <typename T, int QQ, int NC, int NW>
@@ -174,11 +174,11 @@ cudaError_t launch3(dugks_3d_ctx* ctx) {
 template <typename F>
 auto dispatch3(const dugks_3d_ctx* ctx, F&& f) {
     if (ctx->precision == 32) {
-        if (ctx->q == 19) return ctx->nc == 4 ? f.template operator()<float, 19, 4, 16>() : f.template operator()<float, 19, NCL, 16>();
-        return ctx->nc == 4 ? f.template operator()<float, 15, 4, 16>() : f.template operator()<float, 15, NCL, 16>();
+        if (ctx->q == 19) return ctx->nc == 4 ? f.template operator()<float, 19, 4, 12>() : f.template operator()<float, 19, NCL, 12>();
+        return ctx->nc == 4 ? f.template operator()<float, 15, 4, 12>() : f.template operator()<float, 15, NCL, 12>();
     }
-    if (ctx->q == 19) return ctx->nc == 4 ? f.template operator()<double, 19, 4, 8>() : f.template operator()<double, 19, NCL, 8>();
-    return ctx->nc == 4 ? f.template operator()<double, 15, 4, 8>() : f.template operator()<double, 15, NCL, 8>();
+    if (ctx->q == 19) return ctx->nc == 4 ? f.template operator()<double, 19, 4, 6>() : f.template operator()<double, 19, NCL, 6>();
+    return ctx->nc == 4 ? f.template operator()<double, 15, 4, 6>() : f.template operator()<double, 15, NCL, 6>();
 }
 
 struct LaunchOp {

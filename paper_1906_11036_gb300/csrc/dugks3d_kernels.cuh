@@ -13,9 +13,11 @@
 // The update (Eq. 2.12) reads ftilde of the cell again (an L1/L2 hit) to form
 // ftilde^+ = P + (P - ftilde)/3 (Eq. 2.23).
 //
-// ftilde of the next plane is prefetched with cp.async into per-thread
-// shared-memory slots while the faces of the current plane are computed; a
-// thread refills its slots only after it has consumed their contents.
+// ftilde of the planes is staged with cp.async into a three-plane ring of
+// per-thread shared-memory slots beside the P ring: while plane z is
+// processed, ftilde(z) waits for the update, ftilde(z+1) feeds P and
+// ftilde(z+2) is in flight.  A thread only touches its own slots, and refills a
+// slot only after its own update has read it.
 //
 // Only the velocities that cross a face need their reconstructed fbar; the
 // interface phi_b = sum_i fbar_i follows from the moments M0 = sum_i P_i and
@@ -112,7 +114,7 @@ __global__ void __launch_bounds__(NW * 32, 1) step3d(const Args3<T> a, const Con
     T* sP = reinterpret_cast<T*>(smem_raw);  // [3][NW][QQ][32]: P of three planes
     T* sY = sP + 3 * NW * QQ * 32;           // [NW][NCROSS][32]: north y-face f of each row
     T* sM = sY + NW * NCROSS * 32;           // [3][NW][4][32]: moments M0, Mx, My, Mz of P
-    T* sF = sM + 3 * NW * 4 * 32;            // [NW][QQ][32]: ftilde of the next plane (cp.async)
+    T* sF = sM + 3 * NW * 4 * 32;            // [3][NW][QQ][32]: ftilde of three planes (cp.async)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int x0 = blockIdx.x * 30, y0 = blockIdx.y * (NW - 2), z0 = blockIdx.z * a.zseg;
     if (z0 >= a.nz) return;  // uniform over the CTA
@@ -131,12 +133,16 @@ __global__ void __launch_bounds__(NW * 32, 1) step3d(const Args3<T> a, const Con
     auto Ps = [&](int slot, int ww, int i, int l) -> T { return sP[((slot * NW + ww) * QQ + i) * 32 + l]; };
     auto Ms = [&](int slot, int ww, int m, int l) -> T { return sM[((slot * NW + ww) * 4 + m) * 32 + l]; };
 
+    // ring slot of plane zz (z0-1 <= zz <= z1+1), shared by sP, sM and sF
+    auto slot_of = [&](int zz) { return (zz - z0 + 1) % 3; };
+    auto Fs = [&](int slot, int i) -> T { return sF[((slot * NW + w) * QQ + i) * 32 + lane]; };
     // start the copy of this thread's ftilde of plane zz into its slots of sF
     auto prefetch = [&](int zz) {
         const long long c = ((long long)wrapc(zz, nz, a.per[2]) * ny + sk) * nx + sj;
+        const int sl = slot_of(zz);
 #pragma unroll
         for (int i = 0; i < QQ; ++i) {
-            const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(sF + (w * QQ + i) * 32 + lane));
+            const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(sF + ((sl * NW + w) * QQ + i) * 32 + lane));
             asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(a.fin + i * a.plane + c),
                          "n"(int(sizeof(T))));
         }
@@ -151,10 +157,10 @@ __global__ void __launch_bounds__(NW * 32, 1) step3d(const Args3<T> a, const Con
         T phi = T(0);
 #pragma unroll
         for (int i = 0; i < QQ; ++i) {
-            f[i] = sF[(w * QQ + i) * 32 + lane];
+            f[i] = Fs(slot, i);
             phi += f[i];
         }
-        // phi depends on every slot value, so the slots are free again
+        // the slot of plane next held plane next-3, whose update this thread has done
         prefetch(next);
         T P[QQ];
         T hs = T(0);
@@ -303,7 +309,7 @@ __global__ void __launch_bounds__(NW * 32, 1) step3d(const Args3<T> a, const Con
 #pragma unroll
             for (int i = 0; i < QQ; ++i) {
                 const T P = Ps(so, w, i, lane);
-                T v = fma(k.third, P - a.fin[i * a.plane + c], P);  // ftilde^+ (Eq. 2.23)
+                T v = fma(k.third, P - Fs(so, i), P);  // ftilde^+ (Eq. 2.23)
                 if (XS3<QQ>(i, 0) >= 0)
                     v = fma(-T(E3<QQ>(i, 0)) * cxj.r, fEx[XS3<QQ>(i, 0)] - fWx[XS3<QQ>(i, 0)], v);
                 if (XS3<QQ>(i, 1) >= 0)
