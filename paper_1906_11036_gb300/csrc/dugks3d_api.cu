@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -380,6 +381,8 @@ dugks_status dugks_3d_create(const dugks_3d_mesh* mesh, const dugks_3d_vset* vse
     nseg = std::min<long long>(nseg, std::max(1, ctx->nz / 8));
     nseg = std::min<long long>(nseg, 65535);
     ctx->zseg = int((ctx->nz + nseg - 1) / nseg);
+    // tuning override (planes per CTA segment), e.g. for a sweep
+    if (const char* v = getenv("DUGKS_3D_ZSEG")) ctx->zseg = std::max(1, std::min(ctx->nz, atoi(v)));
     ctx->grid[2] = (ctx->nz + ctx->zseg - 1) / ctx->zseg;
     if (ctx->grid[1] > 65535) { free3(ctx); return DUGKS_ERR_ARG; }
     *out = ctx;
