@@ -355,10 +355,14 @@ template <typename T, int NC>
 cudaError_t launch_step(dugks_ctx* ctx) {
     const StepArgs<T, NC> a = make_args<T, NC>(ctx, ctx->cur);
     const Consts<T, NC> k = make_consts<T, NC>(ctx);
-    if (ctx->nsrc > 0) {  // the scalar fused kernel with the source terms
+    if (ctx->nsrc > 0) {  // the fused kernel with the source terms: velocity pairs in FP32, else scalar
         dim3 grid(ctx->nstrips, ctx->nseg);
-        fused_step_src<T, NC><<<grid, 32, fused_smem(ctx), ctx->stream>>>(ctx->tmap[ctx->cur], a, k, ctx->seg_rows,
-                                                                         ctx->stages, make_src_args<T>(ctx));
+        if constexpr (sizeof(T) == 4 && NC != NC_LARGE)
+            fused_step_vp_src<NC><<<grid, 32, fused_smem(ctx), ctx->stream>>>(
+                ctx->tmap[ctx->cur], a, make_constsp<NC>(ctx), ctx->seg_rows, ctx->stages, make_src_args<float>(ctx));
+        else
+            fused_step_src<T, NC><<<grid, 32, fused_smem(ctx), ctx->stream>>>(ctx->tmap[ctx->cur], a, k, ctx->seg_rows,
+                                                                             ctx->stages, make_src_args<T>(ctx));
         return cudaGetLastError();
     }
     if (ctx->kernel == DUGKS_KERNEL_NAIVE) {

@@ -77,9 +77,15 @@ __device__ __forceinline__ void add_source(const SrcArgs<T>& sa, long long c, T 
                                            bool write_hist) {
     const T phio = sa.first ? phi : sa.hin[c];
     if (write_hist) sa.hout[c] = phi;
+    // every field load is issued before any is used
+    T Sv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) Sv[q] = q < sa.nterms ? sa.field[q * sa.fplane + c] : T(0);
     T Fn = T(0), Fo = T(0);
-    for (int q = 0; q < sa.nterms; ++q) {
-        const T S = sa.field[q * sa.fplane + c];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        if (q >= sa.nterms) break;
+        const T S = Sv[q];
         T xn = sa.en[q] * S, xo = sa.ep[q] * S;
         for (int m = 0; m < sa.power[q]; ++m) {
             xn *= phi;
@@ -694,10 +700,50 @@ __device__ __forceinline__ void vp_xflux(const ConstsP<NC>& k, const V9& fb, F2 
         }
 }
 
-template <int NC, bool EDGE>
+// Source terms of one cell added to the velocity pairs of P and Fp (the
+// arithmetic of add_source on the scalar path; phi = sum of the cell's ftilde)
+__device__ __forceinline__ void add_source_vp(const SrcArgs<float>& sa, long long c, float phi, V9& P, V9& Fp,
+                                              bool write_hist) {
+    const float phio = sa.first ? phi : sa.hin[c];
+    if (write_hist) sa.hout[c] = phi;
+    float Sv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) Sv[q] = q < sa.nterms ? sa.field[q * sa.fplane + c] : 0.f;
+    float Fn = 0.f, Fo = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        if (q >= sa.nterms) break;
+        float xn = sa.en[q] * Sv[q], xo = sa.ep[q] * Sv[q];
+        for (int m = 0; m < sa.power[q]; ++m) {
+            xn *= phi;
+            xo *= phio;
+        }
+        Fn += xn;
+        Fo += xo;
+    }
+    float dn = 0.f, dO = 0.f;
+    for (int m = sa.ndb - 1; m >= 0; --m) {
+        dn = fmaf(dn, phi, sa.db[m]);
+        dO = fmaf(dO, phio, sa.db[m]);
+    }
+    const float gn = dn * Fn, go = dO * Fo;
+    const float Ft = Fn + 0.25f * (Fn - Fo), gt = gn + 0.25f * (gn - go);
+    const float Fa = 1.5f * Fn - 0.5f * Fo, ga = 1.5f * gn - 0.5f * go;
+    const F2 Ft2 = f2(Ft), gt2 = f2(gt), Fa2 = f2(Fa), ga2 = f2(ga);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        P.p[q] = P.p[q] + fma2(f2(sa.kP_g[PA(q)], sa.kP_g[PB(q)]), gt2, f2(sa.kP_f[PA(q)], sa.kP_f[PB(q)]) * Ft2);
+        Fp.p[q] = Fp.p[q] + fma2(f2(sa.kU_g[PA(q)], sa.kU_g[PB(q)]), ga2, f2(sa.kU_f[PA(q)], sa.kU_f[PB(q)]) * Fa2);
+    }
+    P.z += fmaf(sa.kP_g[0], gt, sa.kP_f[0] * Ft);
+    Fp.z += fmaf(sa.kU_g[0], ga, sa.kU_f[0] * Fa);
+}
+
+template <int NC, bool EDGE, bool SRC = false>
 __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<float, NC>& a, const ConstsP<NC>& k,
                                         unsigned char* stages, uint64_t* bars, const int S, const int lane,
-                                        const int xw, const int y0, const int y1, int& ring) {
+                                        const int xw, const int y0, const int y1, int& ring,
+                                        const SrcArgs<float>* sa = nullptr) {
     // `ring` counts the rows this warp has already passed through its stage ring (a warp may
     // process several tiles); row t of the warp uses stage t % S in phase (t / S) & 1
     using L = WarpLayout<float>;
@@ -822,6 +868,11 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
     auto ghost_of = [&](int r) { return ghost_col || (!a.yper && (r < 0 || r >= ny)); };
     const float bv_s = k.s.bcv[2], bv_n = k.s.bcv[3];
     auto bv_of = [&](int r) { return ghost_col ? bvx : (r < 0 ? bv_s : bv_n); };
+    // source terms of row r's cell (a ghost takes those of the interior cell it mirrors)
+    auto cell_src = [&](int r, const V9& Fr, V9& P, V9& Fp) {
+        if (SRC && !(EDGE && role == ROLE_OUT))
+            add_source_vp(*sa, (long long)src_row(r) * nx + scol, vsum(Fr), P, Fp, updates && r >= y0 && r < y1);
+    };
 
     bool failed = false;
     V9 F, P0, Fp0, Ly;
@@ -833,6 +884,7 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
     FaceM<float> fyB = a.fy[y0], fyA = a.fy[y0 + 1];
     if (!failed) {
         vp_cell(k, F, P0, Fp0, ghost_of(y0 - 1), bv_of(y0 - 1));
+        cell_src(y0 - 1, F, P0, Fp0);
         grad_x(y0 - 1, P0, Gx);
         vp_lower(k, fyA, P0, Gx, Ly);
 #pragma unroll
@@ -843,6 +895,7 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
         fyB = fyA;
         fyA = a.fy[y0 + 2];
         vp_cell(k, F, P0, Fp0, ghost_of(y0), bv_of(y0));
+        cell_src(y0, F, P0, Fp0);
         grad_x(y0, P0, Gx);
         vp_yface(k, fyB, P0, Gx, Ly, fS);
         vp_lower(k, fyA, P0, Gx, Ly);
@@ -854,6 +907,7 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
             fyB = fyA;
             fyA = a.fy[r + 2];
             vp_cell(k, F, P, Fp, ghost_of(r), bv_of(r));
+            cell_src(r, F, P, Fp);
             grad_x(r, P, Gx);
             vp_yface(k, fyB, P, Gx, Ly, fN);
             vp_lower(k, fyA, P, Gx, Ly);
@@ -907,6 +961,33 @@ __global__ void __launch_bounds__(32, DUGKS_VP_MIN_WARPS) fused_step_vp(const __
     int ring = 0;
     if (edge) vp_rows<NC, true>(&tin, a, k, smem, bars, S, lane, xw, y0, y1, ring);
     else vp_rows<NC, false>(&tin, a, k, smem, bars, S, lane, xw, y0, y1, ring);
+}
+
+// the velocity-pair step with the source terms F and R (12 resident warps per SM
+// give the source arithmetic registers without spills)
+template <int NC>
+__global__ void __launch_bounds__(32, 12) fused_step_vp_src(const __grid_constant__ CUtensorMap tin,
+                                                            const StepArgs<float, NC> a, const ConstsP<NC> k,
+                                                            const int seg_rows, const int S,
+                                                            const __grid_constant__ SrcArgs<float> sa) {
+    using L = WarpLayout<float>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + size_t(S) * L::STAGE_BYTES);
+    const int lane = threadIdx.x;
+    const int xw = blockIdx.x * L::WI;
+    const int y0 = blockIdx.y * seg_rows;
+    const int y1 = min(y0 + seg_rows, a.ny);
+    if (y0 >= a.ny || xw >= a.nx) return;
+    if (lane == 0) {
+        for (int q = 0; q < S; ++q) mbar_init(&bars[q], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const bool edge = xw - 1 < 0 || xw + L::WI >= a.nx;
+    int ring = 0;
+    if (edge) vp_rows<NC, true, true>(&tin, a, k, smem, bars, S, lane, xw, y0, y1, ring, &sa);
+    else vp_rows<NC, false, true>(&tin, a, k, smem, bars, S, lane, xw, y0, y1, ring, &sa);
 }
 
 // ---------------------------------------------------------------------------
