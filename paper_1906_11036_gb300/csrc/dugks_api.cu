@@ -80,6 +80,11 @@ struct dugks_ctx {
     int src_power[8];
     void* src_field = nullptr;            // S_k [nsrc][ny][nx], precision's type
     void* hist[2] = {nullptr, nullptr};   // phi^{n-1} (read) / phi^n (written), alternating with cur
+    // FP32 velocity-pair path: fields and history as nsrc + 1 pitched planes, alternating with cur,
+    // staged by TMA into the same ring stage as ftilde
+    void* aux[2] = {nullptr, nullptr};
+    CUtensorMap taux[2];
+    int aux_box = 0, src_stage = 0;  // bytes of one aux box; bytes of one ring stage
     bool src_first = true;
     double t = 0, t0 = 0;   // time of the state; source start time
     double tbase = 0;       // t = tbase + tsteps * dt (tbase set by set_source, init_phi, load_state)
@@ -247,11 +252,16 @@ void* fused_fn(const dugks_ctx* ctx) {
     }
 }
 
+// the FP32 velocity-pair kernel takes the source fields from the TMA-staged aux planes
+bool src_uses_aux(const dugks_ctx* ctx) { return ctx->precision == 32 && ctx->nc != NC_LARGE; }
+
+size_t src_vp_smem(const dugks_ctx* ctx) { return size_t(ctx->stages) * (ctx->src_stage + 8) + 128; }
+
 size_t fused_smem(const dugks_ctx* ctx) {
     return ctx->precision == 32 ? WarpLayout<float>::bytes(ctx->stages) : WarpLayout<double>::bytes(ctx->stages);
 }
 
-dugks_status make_tensor_maps(dugks_ctx* ctx) {
+EncodeTiledFn tiled_encoder(dugks_ctx* ctx) {
     static EncodeTiledFn encode = nullptr;
     if (!encode) {
         void* fn = nullptr;
@@ -259,10 +269,16 @@ dugks_status make_tensor_maps(dugks_ctx* ctx) {
         cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
         if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
             ctx->last_error = "cuTensorMapEncodeTiled is not available from the driver";
-            return DUGKS_ERR_CUDA;
+            return nullptr;
         }
         encode = reinterpret_cast<EncodeTiledFn>(fn);
     }
+    return encode;
+}
+
+dugks_status make_tensor_maps(dugks_ctx* ctx) {
+    EncodeTiledFn encode = tiled_encoder(ctx);
+    if (!encode) return DUGKS_ERR_CUDA;
     const int align = 16 / int(ctx->elem);
     const cuuint64_t dims[3] = {cuuint64_t(ctx->nx), cuuint64_t(ctx->ny), cuuint64_t(Q)};
     const cuuint64_t strides[2] = {cuuint64_t(ctx->pitch) * ctx->elem, cuuint64_t(ctx->plane) * ctx->elem};
@@ -329,6 +345,7 @@ SrcArgs<T> make_src_args(const dugks_ctx* ctx) {
     sa.first = ctx->src_first ? 1 : 0;
     for (int q = 0; q < ctx->nsrc; ++q) {
         sa.power[q] = ctx->src_power[q];
+        sa.dpow[q] = ctx->src_power[q] - (q ? ctx->src_power[q - 1] : 0);
         sa.en[q] = T(std::exp(ctx->src_rate[q] * ctx->t));
         sa.ep[q] = ctx->src_first ? sa.en[q] : T(std::exp(ctx->src_rate[q] * (ctx->t - ctx->dt)));
     }
@@ -348,6 +365,11 @@ SrcArgs<T> make_src_args(const dugks_ctx* ctx) {
     sa.fplane = (long long)ctx->nx * ctx->ny;
     sa.hin = static_cast<const T*>(ctx->hist[ctx->cur]);
     sa.hout = static_cast<T*>(ctx->hist[ctx->cur ^ 1]);
+    sa.aux_in = static_cast<const T*>(ctx->aux[ctx->cur]);
+    sa.aux_out = static_cast<T*>(ctx->aux[ctx->cur ^ 1]);
+    sa.aux_plane = ctx->plane;
+    sa.aux_box = ctx->aux_box;
+    sa.stage_bytes = ctx->src_stage;
     return sa;
 }
 
@@ -358,8 +380,9 @@ cudaError_t launch_step(dugks_ctx* ctx) {
     if (ctx->nsrc > 0) {  // the fused kernel with the source terms: velocity pairs in FP32, else scalar
         dim3 grid(ctx->nstrips, ctx->nseg);
         if constexpr (sizeof(T) == 4 && NC != NC_LARGE)
-            fused_step_vp_src<NC><<<grid, 32, fused_smem(ctx), ctx->stream>>>(
-                ctx->tmap[ctx->cur], a, make_constsp<NC>(ctx), ctx->seg_rows, ctx->stages, make_src_args<float>(ctx));
+            fused_step_vp_src<NC><<<grid, 32, src_vp_smem(ctx), ctx->stream>>>(
+                ctx->tmap[ctx->cur], a, make_constsp<NC>(ctx), ctx->seg_rows, ctx->stages, make_src_args<float>(ctx),
+                ctx->taux[ctx->cur]);
         else
             fused_step_src<T, NC><<<grid, 32, fused_smem(ctx), ctx->stream>>>(ctx->tmap[ctx->cur], a, k, ctx->seg_rows,
                                                                              ctx->stages, make_src_args<T>(ctx));
@@ -421,7 +444,7 @@ void free_ctx(dugks_ctx* ctx) {
     cudaGetDevice(&prev);
     cudaSetDevice(ctx->device);
     for (void* p : {ctx->buf[0], ctx->buf[1], ctx->fxm, ctx->fym, ctx->cxm, ctx->cym, ctx->adj_ax, ctx->adj_ay,
-                    ctx->src_field, ctx->hist[0], ctx->hist[1],
+                    ctx->src_field, ctx->hist[0], ctx->hist[1], ctx->aux[0], ctx->aux[1],
                     static_cast<void*>(ctx->adj_partial), static_cast<void*>(ctx->adj_dalpha)})
         if (p) cudaFree(p);
     for (void* p : {static_cast<void*>(ctx->dxv), static_cast<void*>(ctx->dyv), static_cast<void*>(ctx->staging),
@@ -1053,7 +1076,43 @@ dugks_status dugks_set_source(dugks_ctx* ctx, int nterms, const double* rate, co
     }
     DeviceGuard guard(ctx->device);
     const size_t cells = size_t(ctx->nx) * ctx->ny;
-    if (nterms > 0) {
+    // the terms are held in ascending order of power (the sum F does not depend on the order)
+    int order[8];
+    for (int q = 0; q < nterms; ++q) order[q] = q;
+    std::stable_sort(order, order + nterms, [&](int x, int y) { return power[x] < power[y]; });
+    const char* fields = static_cast<const char*>(fields_dev);
+    if (nterms > 0 && src_uses_aux(ctx)) {
+        CK(cudaStreamSynchronize(ctx->stream));  // the old fields may still be read by queued steps
+        EncodeTiledFn encode = tiled_encoder(ctx);
+        if (!encode) return DUGKS_ERR_CUDA;
+        using L = WarpLayout<float>;
+        const size_t planes = size_t(nterms) + 1;
+        for (int b = 0; b < 2; ++b) {
+            if (ctx->aux[b]) { cudaFree(ctx->aux[b]); ctx->aux[b] = nullptr; }
+            cudaError_t e = cudaMalloc(&ctx->aux[b], planes * size_t(ctx->plane) * sizeof(float));
+            if (e != cudaSuccess) { ctx->aux[b] = nullptr; return cuda_fail(ctx, e, "cudaMalloc(source planes)"); }
+            // the nterms field planes, pitched like ftilde; the last plane holds the phi history
+            for (int q = 0; q < nterms; ++q)
+                CK(cudaMemcpy2DAsync(static_cast<float*>(ctx->aux[b]) + size_t(q) * ctx->plane,
+                                     size_t(ctx->pitch) * sizeof(float), fields + size_t(order[q]) * cells * sizeof(float),
+                                     size_t(ctx->nx) * sizeof(float), size_t(ctx->nx) * sizeof(float), size_t(ctx->ny),
+                                     cudaMemcpyDeviceToDevice, ctx->stream));
+            const cuuint64_t dims[3] = {cuuint64_t(ctx->nx), cuuint64_t(ctx->ny), cuuint64_t(planes)};
+            const cuuint64_t strides[2] = {cuuint64_t(ctx->pitch) * sizeof(float),
+                                           cuuint64_t(ctx->plane) * sizeof(float)};
+            const cuuint32_t box[3] = {cuuint32_t(L::BOXW), 1u, cuuint32_t(planes)};
+            const cuuint32_t estr[3] = {1u, 1u, 1u};
+            CUresult r = encode(&ctx->taux[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, ctx->aux[b], dims, strides, box,
+                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) {
+                ctx->last_error = "cuTensorMapEncodeTiled failed for the source planes (" + std::to_string(int(r)) + ")";
+                return DUGKS_ERR_CUDA;
+            }
+        }
+        ctx->aux_box = int(planes) * L::BOXW * int(sizeof(float));
+        ctx->src_stage = L::STAGE_BYTES + (ctx->aux_box + 127) / 128 * 128;
+    } else if (nterms > 0) {
         CK(cudaStreamSynchronize(ctx->stream));  // the old fields may still be read by queued steps
         if (ctx->src_field) { cudaFree(ctx->src_field); ctx->src_field = nullptr; }
         cudaError_t e = cudaMalloc(&ctx->src_field, size_t(nterms) * cells * ctx->elem);
@@ -1063,12 +1122,14 @@ dugks_status dugks_set_source(dugks_ctx* ctx, int nterms, const double* rate, co
                 e = cudaMalloc(&ctx->hist[b], cells * ctx->elem);
                 if (e != cudaSuccess) { ctx->hist[b] = nullptr; return cuda_fail(ctx, e, "cudaMalloc(source history)"); }
             }
-        CK(cudaMemcpyAsync(ctx->src_field, fields_dev, size_t(nterms) * cells * ctx->elem, cudaMemcpyDeviceToDevice,
-                           ctx->stream));
-        for (int q = 0; q < nterms; ++q) {
-            ctx->src_rate[q] = rate[q];
-            ctx->src_power[q] = power[q];
-        }
+        for (int q = 0; q < nterms; ++q)
+            CK(cudaMemcpyAsync(static_cast<char*>(ctx->src_field) + size_t(q) * cells * ctx->elem,
+                               fields + size_t(order[q]) * cells * ctx->elem, cells * ctx->elem,
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    for (int q = 0; q < nterms; ++q) {
+        ctx->src_rate[q] = rate[order[q]];
+        ctx->src_power[q] = power[order[q]];
     }
     ctx->nsrc = nterms;
     ctx->t0 = ctx->t = ctx->tbase = t0;

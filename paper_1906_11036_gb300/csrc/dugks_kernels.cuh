@@ -50,7 +50,8 @@ template <typename T>
 struct SrcArgs {
     int nterms;
     int first;            // 1: no history yet (S^{n-1} = S^n)
-    int power[8];
+    int power[8];         // terms in ascending order of power
+    int dpow[8];          // power[k] - power[k-1] (power[-1] = 0)
     T en[8], ep[8];       // exp(rate_k t_n), exp(rate_k t_{n-1})
     T db[8];              // b'(phi) coefficients, lowest order first
     int ndb;
@@ -60,6 +61,12 @@ struct SrcArgs {
     long long fplane;     // nx * ny
     const T* hin;         // phi^{n-1} [ny][nx]
     T* hout;              // phi^n [ny][nx]
+    // velocity-pair path: fields and history in pitched planes staged by TMA with ftilde
+    const T* aux_in;      // [nterms + 1][ny][pitch]: S_k, then phi^{n-1}
+    T* aux_out;           // same layout; its last plane receives phi^n
+    long long aux_plane;  // elements per plane (pitch * ny)
+    int aux_box;          // bytes of one aux TMA box (nterms + 1 planes of one row)
+    int stage_bytes;      // bytes of one ring stage: ftilde box + aux box (128-byte multiples)
 };
 
 // L1 prefetch of the source fields and the history of cell c (a few rows ahead of use)
@@ -701,49 +708,50 @@ __device__ __forceinline__ void vp_xflux(const ConstsP<NC>& k, const V9& fb, F2 
 }
 
 // Source terms of one cell added to the velocity pairs of P and Fp (the
-// arithmetic of add_source on the scalar path; phi = sum of the cell's ftilde)
-__device__ __forceinline__ void add_source_vp(const SrcArgs<float>& sa, long long c, float phi, V9& P, V9& Fp,
-                                              bool write_hist) {
-    const float phio = sa.first ? phi : sa.hin[c];
-    if (write_hist) sa.hout[c] = phi;
-    float Sv[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) Sv[q] = q < sa.nterms ? sa.field[q * sa.fplane + c] : 0.f;
-    float Fn = 0.f, Fo = 0.f;
+// arithmetic of add_source on the scalar path, with phi^n and phi^{n-1} carried
+// as one pair).  Av[0..nterms-1] are the cell's field values S_k, in ascending
+// order of power, and Av[8] its phi^{n-1}, staged with its ftilde.  Each pair
+// holds two opposite velocities, so their c_i.u terms differ only in sign and
+// their weights agree.
+__device__ __forceinline__ void add_source_vp(const SrcArgs<float>& sa, const float (&Av)[9], float phi, V9& P,
+                                              V9& Fp) {
+    const F2 X = f2(phi, sa.first ? phi : Av[8]);  // (phi^n, phi^{n-1})
+    F2 pw = f2(1.f), Fs = f2(0.f);                 // X^power[k]; (F^n, F^{n-1})
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        if (q >= sa.nterms) break;
-        float xn = sa.en[q] * Sv[q], xo = sa.ep[q] * Sv[q];
-        for (int m = 0; m < sa.power[q]; ++m) {
-            xn *= phi;
-            xo *= phio;
+        if (q < sa.nterms) {
+            for (int m = 0; m < sa.dpow[q]; ++m) pw = pw * X;
+            Fs = fma2(f2(sa.en[q], sa.ep[q]) * f2(Av[q]), pw, Fs);
         }
-        Fn += xn;
-        Fo += xo;
     }
-    float dn = 0.f, dO = 0.f;
-    for (int m = sa.ndb - 1; m >= 0; --m) {
-        dn = fmaf(dn, phi, sa.db[m]);
-        dO = fmaf(dO, phio, sa.db[m]);
-    }
-    const float gn = dn * Fn, go = dO * Fo;
-    const float Ft = Fn + 0.25f * (Fn - Fo), gt = gn + 0.25f * (gn - go);
-    const float Fa = 1.5f * Fn - 0.5f * Fo, ga = 1.5f * gn - 0.5f * go;
-    const F2 Ft2 = f2(Ft), gt2 = f2(gt), Fa2 = f2(Fa), ga2 = f2(ga);
+    F2 d = f2(0.f);  // (b'(phi^n), b'(phi^{n-1}))
+    for (int m = sa.ndb - 1; m >= 0; --m) d = fma2(d, X, f2(sa.db[m]));
+    const F2 G = d * Fs;  // (g^n, g^{n-1}) = b' F
+    // F and g at the interface (backward difference over dt/2) and at the update
+    const float Ft = fmaf(0.25f, Fs.v.x - Fs.v.y, Fs.v.x), gt = fmaf(0.25f, G.v.x - G.v.y, G.v.x);
+    const float Fa = fmaf(0.5f, Fs.v.x - Fs.v.y, Fs.v.x), ga = fmaf(0.5f, G.v.x - G.v.y, G.v.x);
+    const F2 gt2 = f2(gt), ga2 = f2(ga);
+    const F2 aP1 = f2(sa.kP_f[1] * Ft), aP2 = f2(sa.kP_f[5] * Ft);  // weight 1/9 and 1/36 pairs
+    const F2 aU1 = f2(sa.kU_f[1] * Fa), aU2 = f2(sa.kU_f[5] * Fa);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        P.p[q] = P.p[q] + fma2(f2(sa.kP_g[PA(q)], sa.kP_g[PB(q)]), gt2, f2(sa.kP_f[PA(q)], sa.kP_f[PB(q)]) * Ft2);
-        Fp.p[q] = Fp.p[q] + fma2(f2(sa.kU_g[PA(q)], sa.kU_g[PB(q)]), ga2, f2(sa.kU_f[PA(q)], sa.kU_f[PB(q)]) * Fa2);
+        P.p[q] = P.p[q] + fma2(f2(sa.kP_g[PA(q)], sa.kP_g[PB(q)]), gt2, q < 2 ? aP1 : aP2);
+        Fp.p[q] = Fp.p[q] + fma2(f2(sa.kU_g[PA(q)], sa.kU_g[PB(q)]), ga2, q < 2 ? aU1 : aU2);
     }
-    P.z += fmaf(sa.kP_g[0], gt, sa.kP_f[0] * Ft);
-    Fp.z += fmaf(sa.kU_g[0], ga, sa.kU_f[0] * Fa);
+    P.z = fmaf(sa.kP_f[0], Ft, P.z);  // the rest velocity has c_0 = 0
+    Fp.z = fmaf(sa.kU_f[0], Fa, Fp.z);
 }
+
+#ifndef DUGKS_VP_SRC_UNROLL
+#define DUGKS_VP_SRC_UNROLL 1
+#endif
+constexpr int kVpSrcUnroll = DUGKS_VP_SRC_UNROLL;  // rows per iteration of the source variant's row loop
 
 template <int NC, bool EDGE, bool SRC = false>
 __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<float, NC>& a, const ConstsP<NC>& k,
                                         unsigned char* stages, uint64_t* bars, const int S, const int lane,
                                         const int xw, const int y0, const int y1, int& ring,
-                                        const SrcArgs<float>* sa = nullptr) {
+                                        const SrcArgs<float>* sa = nullptr, const CUtensorMap* taux = nullptr) {
     // `ring` counts the rows this warp has already passed through its stage ring (a warp may
     // process several tiles); row t of the warp uses stage t % S in phase (t / S) & 1
     using L = WarpLayout<float>;
@@ -782,13 +790,19 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
         if (r >= ny) return a.yper ? r - ny : ny - 1;
         return r;
     };
+    const int stride = SRC ? sa->stage_bytes : L::STAGE_BYTES;  // bytes per ring stage
+    const uint32_t txb = uint32_t(SRC ? L::BOX_BYTES + sa->aux_box : L::BOX_BYTES);
+    auto issue = [&](int st, int row) {
+        mbar_arrive_expect_tx(&bars[st], txb);
+        tma_load_3d(stages + size_t(st) * stride, tin, &bars[st], xs, row, 0);
+        if (SRC) tma_load_3d(stages + size_t(st) * stride + L::STAGE_BYTES, taux, &bars[st], xs, row, 0);
+    };
     if (lane == 0) {
-        for (int q = 0; q < min(S, R); ++q) {
-            const int st = (ring + q) % S;
-            mbar_arrive_expect_tx(&bars[st], uint32_t(L::BOX_BYTES));
-            tma_load_3d(stages + size_t(st) * L::STAGE_BYTES, tin, &bars[st], xs, src_row(y0 - 1 + q), 0);
-        }
+        for (int q = 0; q < min(S, R); ++q) issue((ring + q) % S, src_row(y0 - 1 + q));
     }
+    float Av[9];  // source path: this lane's S_k (0..7) and phi^{n-1} (8) of the row just loaded
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Av[q] = 0.f;
     int s = ring % S, issued = min(S, R), consumed = 0;
     uint32_t ph = uint32_t((ring / S) & 1);
 
@@ -797,13 +811,26 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
         if (__any_sync(0xffffffffu, !ok)) return false;
         float ft[Q];
         if (from_smem) {
-            const float* st = reinterpret_cast<const float*>(stages + size_t(s) * L::STAGE_BYTES) + soff;
+            const float* st = reinterpret_cast<const float*>(stages + size_t(s) * stride) + soff;
 #pragma unroll
             for (int i = 0; i < Q; ++i) ft[i] = st[i * L::BOXW];
+            if (SRC) {
+                const float* ax = reinterpret_cast<const float*>(stages + size_t(s) * stride + L::STAGE_BYTES) + soff;
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (q < sa->nterms) Av[q] = ax[q * L::BOXW];
+                Av[8] = ax[sa->nterms * L::BOXW];
+            }
         } else if (role != ROLE_OUT) {
             const long long base = (long long)src_row(r) * a.pitch + scol;
 #pragma unroll
             for (int i = 0; i < Q; ++i) ft[i] = a.fin[i * a.plane + base];
+            if (SRC) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (q < sa->nterms) Av[q] = sa->aux_in[q * sa->aux_plane + base];
+                Av[8] = sa->aux_in[sa->nterms * sa->aux_plane + base];
+            }
         } else {
 #pragma unroll
             for (int i = 0; i < Q; ++i) ft[i] = 0.f;
@@ -815,8 +842,7 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
         if (issued < R) {
             if (lane == 0) {
                 fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&bars[s], uint32_t(L::BOX_BYTES));
-                tma_load_3d(stages + size_t(s) * L::STAGE_BYTES, tin, &bars[s], xs, src_row(r + S), 0);
+                issue(s, src_row(r + S));
             }
             ++issued;
         }
@@ -870,8 +896,11 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
     auto bv_of = [&](int r) { return ghost_col ? bvx : (r < 0 ? bv_s : bv_n); };
     // source terms of row r's cell (a ghost takes those of the interior cell it mirrors)
     auto cell_src = [&](int r, const V9& Fr, V9& P, V9& Fp) {
-        if (SRC && !(EDGE && role == ROLE_OUT))
-            add_source_vp(*sa, (long long)src_row(r) * nx + scol, vsum(Fr), P, Fp, updates && r >= y0 && r < y1);
+        if (SRC && !(EDGE && role == ROLE_OUT)) {
+            const float phi = vsum(Fr);
+            if (updates && r >= y0 && r < y1) sa->aux_out[sa->nterms * sa->aux_plane + (long long)r * a.pitch + j] = phi;
+            add_source_vp(*sa, Av, phi, P, Fp);
+        }
     };
 
     bool failed = false;
@@ -899,7 +928,7 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
         grad_x(y0, P0, Gx);
         vp_yface(k, fyB, P0, Gx, Ly, fS);
         vp_lower(k, fyA, P0, Gx, Ly);
-#pragma unroll 2
+#pragma unroll(SRC ? kVpSrcUnroll : 2)
         for (int r = y0 + 1; r <= y1; ++r) {
             V9 P, Fp;
             F2 fN[4];
@@ -969,11 +998,12 @@ template <int NC>
 __global__ void __launch_bounds__(32, 12) fused_step_vp_src(const __grid_constant__ CUtensorMap tin,
                                                             const StepArgs<float, NC> a, const ConstsP<NC> k,
                                                             const int seg_rows, const int S,
-                                                            const __grid_constant__ SrcArgs<float> sa) {
+                                                            const __grid_constant__ SrcArgs<float> sa,
+                                                            const __grid_constant__ CUtensorMap taux) {
     using L = WarpLayout<float>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + size_t(S) * L::STAGE_BYTES);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + size_t(S) * sa.stage_bytes);
     const int lane = threadIdx.x;
     const int xw = blockIdx.x * L::WI;
     const int y0 = blockIdx.y * seg_rows;
@@ -986,8 +1016,8 @@ __global__ void __launch_bounds__(32, 12) fused_step_vp_src(const __grid_constan
     __syncwarp();
     const bool edge = xw - 1 < 0 || xw + L::WI >= a.nx;
     int ring = 0;
-    if (edge) vp_rows<NC, true, true>(&tin, a, k, smem, bars, S, lane, xw, y0, y1, ring, &sa);
-    else vp_rows<NC, false, true>(&tin, a, k, smem, bars, S, lane, xw, y0, y1, ring, &sa);
+    if (edge) vp_rows<NC, true, true>(&tin, a, k, smem, bars, S, lane, xw, y0, y1, ring, &sa, &taux);
+    else vp_rows<NC, false, true>(&tin, a, k, smem, bars, S, lane, xw, y0, y1, ring, &sa, &taux);
 }
 
 // ---------------------------------------------------------------------------
