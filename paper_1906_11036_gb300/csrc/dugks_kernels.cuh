@@ -742,10 +742,17 @@ __device__ __forceinline__ void add_source_vp(const SrcArgs<float>& sa, const fl
     Fp.z = fmaf(sa.kU_f[0], Fa, Fp.z);
 }
 
+#ifndef DUGKS_VP_UNROLL
+#define DUGKS_VP_UNROLL 2
+#endif
 #ifndef DUGKS_VP_SRC_UNROLL
 #define DUGKS_VP_SRC_UNROLL 1
 #endif
-constexpr int kVpSrcUnroll = DUGKS_VP_SRC_UNROLL;  // rows per iteration of the source variant's row loop
+#ifndef DUGKS_VP_SRC_MIN_WARPS
+#define DUGKS_VP_SRC_MIN_WARPS 16
+#endif
+// rows per iteration of the row loop, without and with the source terms (instruction-cache footprint)
+constexpr int kVpUnroll = DUGKS_VP_UNROLL, kVpSrcUnroll = DUGKS_VP_SRC_UNROLL;
 
 template <int NC, bool EDGE, bool SRC = false>
 __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<float, NC>& a, const ConstsP<NC>& k,
@@ -928,7 +935,7 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
         grad_x(y0, P0, Gx);
         vp_yface(k, fyB, P0, Gx, Ly, fS);
         vp_lower(k, fyA, P0, Gx, Ly);
-#pragma unroll(SRC ? kVpSrcUnroll : 2)
+#pragma unroll(SRC ? kVpSrcUnroll : kVpUnroll)
         for (int r = y0 + 1; r <= y1; ++r) {
             V9 P, Fp;
             F2 fN[4];
@@ -992,10 +999,10 @@ __global__ void __launch_bounds__(32, DUGKS_VP_MIN_WARPS) fused_step_vp(const __
     else vp_rows<NC, false>(&tin, a, k, smem, bars, S, lane, xw, y0, y1, ring);
 }
 
-// the velocity-pair step with the source terms F and R (12 resident warps per SM
-// give the source arithmetic registers without spills)
+// the velocity-pair step with the source terms F and R (16 resident warps per SM,
+// as the plain step; the source arithmetic fits in 128 registers without spills)
 template <int NC>
-__global__ void __launch_bounds__(32, 12) fused_step_vp_src(const __grid_constant__ CUtensorMap tin,
+__global__ void __launch_bounds__(32, DUGKS_VP_SRC_MIN_WARPS) fused_step_vp_src(const __grid_constant__ CUtensorMap tin,
                                                             const StepArgs<float, NC> a, const ConstsP<NC> k,
                                                             const int seg_rows, const int S,
                                                             const __grid_constant__ SrcArgs<float> sa,
