@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/dugks3d.h"
@@ -140,6 +141,29 @@ Consts3<T, QQ, NC> consts3(const dugks_3d_ctx* ctx) {
     return k;
 }
 
+// the pair constants of step3d_vp (FP32)
+template <int QQ, int NC>
+Consts3P<QQ, NC> consts3p(const dugks_3d_ctx* ctx) {
+    const Consts3<float, QQ, NC> s = consts3<float, QQ, NC>(ctx);
+    Consts3P<QQ, NC> k;
+    for (int q = 0; q < Consts3P<QQ, NC>::NP; ++q)
+        for (int m = 0; m < NC; ++m) {
+            k.hbp[q][m] = make_float2(s.hbp[PA3<QQ>(q)][m], s.hbp[PB3<QQ>(q)][m]);
+            k.hf[q][m] = make_float2(s.hf[PA3<QQ>(q)][m], s.hf[PB3<QQ>(q)][m]);
+        }
+    for (int i = 0; i < QQ; ++i)
+        for (int m = 0; m < NC; ++m) k.feq[i][m] = s.feq[i][m];
+    k.a_bp = s.a_bp;
+    k.b_bp = s.b_bp;
+    k.third = s.third;
+    k.hc = s.hc;
+    k.a_bp2 = make_float2(s.a_bp, s.a_bp);
+    k.a_f2 = make_float2(s.a_f, s.a_f);
+    k.third2 = make_float2(s.third, s.third);
+    for (int w = 0; w < 6; ++w) k.bcv[w] = s.bcv[w];
+    return k;
+}
+
 template <typename T>
 Args3<T> args3(const dugks_3d_ctx* ctx) {
     Args3<T> a;
@@ -163,11 +187,16 @@ constexpr size_t smem3() {
     return size_t(3 * NW * QQ * 32 + NW * NCROSS * 32 + 3 * NW * 4 * 32 + 3 * NW * QQ * 32) * sizeof(T);
 }
 
+// FP32 runs the velocity-pair kernel, FP64 the scalar one
 template <typename T, int QQ, int NC, int NW>
 cudaError_t launch3(dugks_3d_ctx* ctx) {
     const dim3 grid(ctx->grid[0], ctx->grid[1], ctx->grid[2]);
-    step3d<T, QQ, NC, NW><<<grid, NW * 32, smem3<T, QQ, NC, NW>(), ctx->stream>>>(args3<T>(ctx),
-                                                                                  consts3<T, QQ, NC>(ctx));
+    if constexpr (std::is_same<T, float>::value)
+        step3d_vp<QQ, NC, NW><<<grid, NW * 32, smem3_vp<QQ, NW>(), ctx->stream>>>(args3<float>(ctx),
+                                                                               consts3p<QQ, NC>(ctx));
+    else
+        step3d<T, QQ, NC, NW><<<grid, NW * 32, smem3<T, QQ, NC, NW>(), ctx->stream>>>(args3<T>(ctx),
+                                                                                      consts3<T, QQ, NC>(ctx));
     return cudaGetLastError();
 }
 
@@ -190,8 +219,12 @@ struct LaunchOp {
 struct AttrOp {
     template <typename T, int QQ, int NC, int NW>
     cudaError_t operator()() const {
-        return cudaFuncSetAttribute(step3d<T, QQ, NC, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    int(smem3<T, QQ, NC, NW>()));
+        if constexpr (std::is_same<T, float>::value)
+            return cudaFuncSetAttribute(step3d_vp<QQ, NC, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        int(smem3_vp<QQ, NW>()));
+        else
+            return cudaFuncSetAttribute(step3d<T, QQ, NC, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        int(smem3<T, QQ, NC, NW>()));
     }
 };
 struct NwOp {

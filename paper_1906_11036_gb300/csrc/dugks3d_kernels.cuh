@@ -325,6 +325,324 @@ __global__ void __launch_bounds__(NW * 32, 1) step3d(const Args3<T> a, const Con
     asm volatile("cp.async.wait_group 0;" ::: "memory");  // the last prefetch lands before exit
 }
 
+// ---------------------------------------------------------------------------
+// step3d_vp: the same dataflow in single precision on velocity pairs
+// ---------------------------------------------------------------------------
+//
+// Every moving velocity is paired with its opposite (D3Q19: 9 pairs, D3Q15: 7)
+// and a pair is one float2: the rings hold P and ftilde of a cell as pairs (one
+// 64-bit shared-memory access per pair) and the per-velocity arithmetic runs on
+// the packed FP32 instructions.  The second velocity of a pair is the opposite
+// of the first, so each per-pair weight has the form (a + s b, a - s b) with s
+// the direction sign of the first.  The rest velocity never crosses a face: its
+// P stays in a register until the update.
+
+using dugks::F2;
+using dugks::f2;
+using dugks::fma2;
+using dugks::sgn2;
+using dugks::shfl_up2;
+
+// the opposite of velocity i
+template <int QQ>
+__host__ __device__ constexpr int OPP3(int i) {
+    for (int j = 0; j < QQ; ++j)
+        if (E3<QQ>(j, 0) == -E3<QQ>(i, 0) && E3<QQ>(j, 1) == -E3<QQ>(i, 1) && E3<QQ>(j, 2) == -E3<QQ>(i, 2)) return j;
+    return -1;
+}
+// pair q = (PA3(q), PB3(q)): the pairs in order of their first velocity, the second its
+// opposite (tables spelled out so that they fold to constants after unrolling)
+template <int QQ>
+__host__ __device__ constexpr int PA3(int q) { return QQ == 19 ? 2 * q + 1 : "\1\3\5\7\10\11\12"[q]; }
+template <int QQ>
+__host__ __device__ constexpr int PB3(int q) { return QQ == 19 ? 2 * q + 2 : "\2\4\6\13\14\15\16"[q]; }
+template <int QQ>
+__host__ __device__ constexpr bool pairs_ok() {
+    for (int q = 0; q < (QQ - 1) / 2; ++q)
+        if (PB3<QQ>(q) != OPP3<QQ>(PA3<QQ>(q)) || (q > 0 && PA3<QQ>(q) <= PA3<QQ>(q - 1))) return false;
+    return true;
+}
+template <int QQ>
+__host__ __device__ constexpr int QE3(int q, int a) { return E3<QQ>(PA3<QQ>(q), a); }
+// position of pair q among the pairs crossing a face normal to axis a (-1: parallel)
+template <int QQ>
+__host__ __device__ constexpr int XP3(int q, int a) {
+    if (QE3<QQ>(q, a) == 0) return -1;
+    int s = 0;
+    for (int m = 0; m < q; ++m) s += QE3<QQ>(m, a) != 0 ? 1 : 0;
+    return s;
+}
+constexpr int NCP = NCROSS / 2;  // crossing pairs per face of either lattice
+
+static_assert(pairs_ok<19>() && pairs_ok<15>() && PB3<15>(3) == 11, "velocity pairs");
+static_assert(XP3<19>(8, 1) == NCP - 1 && XP3<15>(6, 2) == NCP - 1 && XP3<19>(0, 1) == -1, "crossing pairs");
+
+template <int QQ, int NC>
+struct Consts3P {
+    static constexpr int NP = (QQ - 1) / 2;
+    float2 hbp[NP][NC];  // per pair: b_bp (feq_A, feq_B) coefficients in powers of phi
+    float2 hf[NP][NC];   // per pair: b_f (feq_A, feq_B)
+    float feq[QQ][NC];   // feq_i (ghosts)
+    float2 a_bp2, a_f2, third2;
+    float a_bp, b_bp, third, hc;
+    float bcv[6];
+};
+
+template <int QQ, int NC>
+__device__ __forceinline__ F2 hbp3(const Consts3P<QQ, NC>& k, int q, F2 x) {
+    F2 s{k.hbp[q][NC - 1]};
+#pragma unroll
+    for (int m = NC - 2; m >= 0; --m) s = fma2(s, x, F2{k.hbp[q][m]});
+    return s;
+}
+template <int QQ, int NC>
+__device__ __forceinline__ F2 hf3(const Consts3P<QQ, NC>& k, int q, F2 x) {
+    F2 s{k.hf[q][NC - 1]};
+#pragma unroll
+    for (int m = NC - 2; m >= 0; --m) s = fma2(s, x, F2{k.hf[q][m]});
+    return s;
+}
+
+template <int QQ, int NW>
+__host__ __device__ constexpr size_t smem3_vp() {
+    constexpr int NP = (QQ - 1) / 2;
+    return size_t(2 * (3 * NW * NP * 32) + NW * NCP * 32) * sizeof(float2) + size_t(3 * NW * 4 * 32 + 3 * NW * 32) * sizeof(float);
+}
+
+template <int QQ, int NC, int NW>
+__global__ void __launch_bounds__(NW * 32, 1) step3d_vp(const Args3<float> a, const Consts3P<QQ, NC> k) {
+    constexpr int NP = (QQ - 1) / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    F2* sP = reinterpret_cast<F2*>(smem_raw);  // [3][NW][NP][32]: P pairs of three planes
+    F2* sF = sP + 3 * NW * NP * 32;            // [3][NW][NP][32]: ftilde pairs of three planes (cp.async)
+    F2* sY = sF + 3 * NW * NP * 32;            // [NW][NCP][32]: north y-face f of each row
+    float* sM = reinterpret_cast<float*>(sY + NW * NCP * 32);  // [3][NW][4][32]: moments M0, Mx, My, Mz
+    float* sF0 = sM + 3 * NW * 4 * 32;                         // [3][NW][32]: ftilde of the rest velocity
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x0 = blockIdx.x * 30, y0 = blockIdx.y * (NW - 2), z0 = blockIdx.z * a.zseg;
+    if (z0 >= a.nz) return;  // uniform over the CTA
+    const int z1 = min(z0 + a.zseg, a.nz);
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int j = x0 - 1 + lane, kk = y0 - 1 + w;
+    const int sj = wrapc(j, nx, a.per[0]), sk = wrapc(kk, ny, a.per[1]);
+    const bool gx = !a.per[0] && (j < 0 || j >= nx), gy = !a.per[1] && (kk < 0 || kk >= ny);
+    const int jm = min(max(j, -1), nx), km = min(max(kk, -1), ny);
+    const FaceM<float> fE = a.fm[0][jm + 2], fN = a.fm[1][km + 2];
+    const CellM<float> cxj = a.cm[0][jm + 1], cyk = a.cm[1][km + 1];
+    const bool interior_row = w >= 1 && w <= NW - 2;
+    const bool interior_col = lane >= 1 && lane <= 30;
+    const bool updates = interior_row && interior_col && j < nx && kk < ny;
+    const int l1 = max(lane - 1, 0), l2 = min(lane + 1, 31);
+    const int w1 = max(w - 1, 0), w2 = min(w + 1, NW - 1);
+
+    auto Ps = [&](int slot, int ww, int q, int l) -> F2 { return sP[((slot * NW + ww) * NP + q) * 32 + l]; };
+    auto Ms = [&](int slot, int ww, int m, int l) -> float { return sM[((slot * NW + ww) * 4 + m) * 32 + l]; };
+    auto slot_of = [&](int zz) { return (zz - z0 + 1) % 3; };
+    // start the copy of this thread's ftilde of plane zz into its slots of sF and sF0
+    auto prefetch = [&](int zz) {
+        const long long c = ((long long)wrapc(zz, nz, a.per[2]) * ny + sk) * nx + sj;
+        const int sl = slot_of(zz);
+        auto cp4 = [&](const void* dst, int i) {
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                             static_cast<unsigned>(__cvta_generic_to_shared(dst))),
+                         "l"(a.fin + i * a.plane + c));
+        };
+        cp4(sF0 + (sl * NW + w) * 32 + lane, 0);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            F2* d = sF + ((sl * NW + w) * NP + q) * 32 + lane;
+            cp4(&d->v.x, PA3<QQ>(q));
+            cp4(&d->v.y, PB3<QQ>(q));
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+
+    // P of plane zz (already prefetched) into ring slot `slot`, its rest component returned;
+    // then prefetch plane `next`
+    auto compute_P = [&](int zz, int slot, int next) -> float {
+        const bool gz = !a.per[2] && (zz < 0 || zz >= nz);
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        F2 F[NP];
+        const float F0 = sF0[(slot * NW + w) * 32 + lane];
+        F2 fs = f2(0.f);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            F[q] = sF[((slot * NW + w) * NP + q) * 32 + lane];
+            fs = fs + F[q];
+        }
+        const float phi = F0 + (fs.v.x + fs.v.y);
+        // the slots of plane next held plane next-3, whose update this thread has done
+        prefetch(next);
+        const F2 phi2 = f2(phi);
+        F2 P[NP];
+        F2 hs = f2(0.f);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            const F2 h = hbp3(k, q, phi2);
+            P[q] = fma2(F2{k.a_bp2}, F[q], h);
+            hs = hs + h;
+        }
+        float P0 = fmaf(k.a_bp, F0, fmaf(k.b_bp, phi, -(hs.v.x + hs.v.y)));  // rest velocity via the zeroth moment
+        if (gx || gy || gz) {  // mirrored ghost: P_g = feq(2 bv - phi) + P - feq(phi)
+            const float bv = gx ? (j < 0 ? k.bcv[0] : k.bcv[1])
+                                : (gy ? (kk < 0 ? k.bcv[2] : k.bcv[3]) : (zz < 0 ? k.bcv[4] : k.bcv[5]));
+            const float pg = 2.f * bv - phi;
+            auto dfe = [&](int i) { return horner3(k.feq, i, pg) - horner3(k.feq, i, phi); };
+#pragma unroll
+            for (int q = 0; q < NP; ++q) P[q] = P[q] + f2(dfe(PA3<QQ>(q)), dfe(PB3<QQ>(q)));
+            P0 += dfe(0);
+        }
+        F2 s2 = f2(0.f);
+        float mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            sP[((slot * NW + w) * NP + q) * 32 + lane] = P[q];
+            s2 = s2 + P[q];
+            const float d = P[q].v.x - P[q].v.y;  // e_a P of the pair = e_a(A) (P_A - P_B)
+            if (QE3<QQ>(q, 0) != 0) mx += QE3<QQ>(q, 0) > 0 ? d : -d;
+            if (QE3<QQ>(q, 1) != 0) my += QE3<QQ>(q, 1) > 0 ? d : -d;
+            if (QE3<QQ>(q, 2) != 0) mz += QE3<QQ>(q, 2) > 0 ? d : -d;
+        }
+        float* M = sM + (slot * NW + w) * 4 * 32 + lane;
+        M[0] = P0 + (s2.v.x + s2.v.y);
+        M[32] = mx;
+        M[64] = my;
+        M[96] = mz;
+        return P0;
+    };
+
+    // tangential part of a face reconstruction: tl times the central difference of the
+    // lower/left cell plus tr times that of the other cell, for one tangential axis
+    auto tang = [&](const F2& lm, const F2& lp, const F2& rm, const F2& rp, float tl, float tr) {
+        return fma2(f2(tl), lp - lm, f2(tr) * (rp - rm));
+    };
+    // f of the pairs crossing the z-face between ring slots lo (below) and hi (above)
+    auto z_face = [&](int lo, int hi, const FaceM<float>& fz, F2 (&out)[NCP]) {
+        const float phib = (1.f - fz.w) * Ms(lo, w, 0, lane) + fz.w * Ms(hi, w, 0, lane) +
+                           fz.hcd * (Ms(lo, w, 3, lane) - Ms(hi, w, 3, lane)) -
+                           k.hc * (fz.tl * ((Ms(lo, w, 1, l2) - Ms(lo, w, 1, l1)) * cxj.ig +
+                                            (Ms(lo, w2, 2, lane) - Ms(lo, w1, 2, lane)) * cyk.ig) +
+                                   fz.tr * ((Ms(hi, w, 1, l2) - Ms(hi, w, 1, l1)) * cxj.ig +
+                                            (Ms(hi, w2, 2, lane) - Ms(hi, w1, 2, lane)) * cyk.ig));
+        const F2 phib2 = f2(phib);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            if (XP3<QQ>(q, 2) < 0) continue;
+            const int en = QE3<QQ>(q, 2), ex = QE3<QQ>(q, 0), ey = QE3<QQ>(q, 1);
+            F2 v = fma2(sgn2(1.f - fz.w, fz.hcd, en), Ps(lo, w, q, lane), sgn2(fz.w, -fz.hcd, en) * Ps(hi, w, q, lane));
+            if (ex != 0)
+                v = fma2(sgn2(0.f, -k.hc * cxj.ig, ex),
+                         tang(Ps(lo, w, q, l1), Ps(lo, w, q, l2), Ps(hi, w, q, l1), Ps(hi, w, q, l2), fz.tl, fz.tr), v);
+            if (ey != 0)
+                v = fma2(sgn2(0.f, -k.hc * cyk.ig, ey),
+                         tang(Ps(lo, w1, q, lane), Ps(lo, w2, q, lane), Ps(hi, w1, q, lane), Ps(hi, w2, q, lane), fz.tl,
+                              fz.tr), v);
+            out[XP3<QQ>(q, 2)] = fma2(F2{k.a_f2}, v, hf3(k, q, phib2));
+        }
+    };
+
+    // pipeline fill: planes z0-1 and z0, and the bottom face of plane z0
+    prefetch(z0 - 1);
+    compute_P(z0 - 1, 0, z0);
+    float P0n = compute_P(z0, 1, z0 + 1);  // rest component of P of the plane being updated
+    __syncthreads();
+    F2 fB[NCP];
+    if (interior_row) z_face(0, 1, a.fm[2][z0 + 1], fB);
+
+    for (int z = z0; z < z1; ++z) {
+        const int sm = (z - z0) % 3, so = (z - z0 + 1) % 3, sp = (z - z0 + 2) % 3;
+        const float P0 = P0n;
+        P0n = compute_P(z + 1, sp, z + 2);
+        __syncthreads();
+        const CellM<float> czl = a.cm[2][z + 1];
+        F2 fEx[NCP], fNy[NCP], fTz[NCP];
+#pragma unroll
+        for (int s = 0; s < NCP; ++s) fEx[s] = fNy[s] = fTz[s] = f2(0.f);
+        // east x-face (lanes 0..30 of the interior rows)
+        if (interior_row && lane <= 30) {
+            const int lr = lane + 1;
+            const float phib = (1.f - fE.w) * Ms(so, w, 0, lane) + fE.w * Ms(so, w, 0, lr) +
+                               fE.hcd * (Ms(so, w, 1, lane) - Ms(so, w, 1, lr)) -
+                               k.hc * (fE.tl * ((Ms(so, w2, 2, lane) - Ms(so, w1, 2, lane)) * cyk.ig +
+                                                (Ms(sp, w, 3, lane) - Ms(sm, w, 3, lane)) * czl.ig) +
+                                       fE.tr * ((Ms(so, w2, 2, lr) - Ms(so, w1, 2, lr)) * cyk.ig +
+                                                (Ms(sp, w, 3, lr) - Ms(sm, w, 3, lr)) * czl.ig));
+            const F2 phib2 = f2(phib);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                if (XP3<QQ>(q, 0) < 0) continue;
+                const int en = QE3<QQ>(q, 0), ey = QE3<QQ>(q, 1), ez = QE3<QQ>(q, 2);
+                F2 v = fma2(sgn2(1.f - fE.w, fE.hcd, en), Ps(so, w, q, lane), sgn2(fE.w, -fE.hcd, en) * Ps(so, w, q, lr));
+                if (ey != 0)
+                    v = fma2(sgn2(0.f, -k.hc * cyk.ig, ey),
+                             tang(Ps(so, w1, q, lane), Ps(so, w2, q, lane), Ps(so, w1, q, lr), Ps(so, w2, q, lr), fE.tl,
+                                  fE.tr), v);
+                if (ez != 0)
+                    v = fma2(sgn2(0.f, -k.hc * czl.ig, ez),
+                             tang(Ps(sm, w, q, lane), Ps(sp, w, q, lane), Ps(sm, w, q, lr), Ps(sp, w, q, lr), fE.tl,
+                                  fE.tr), v);
+                fEx[XP3<QQ>(q, 0)] = fma2(F2{k.a_f2}, v, hf3(k, q, phib2));
+            }
+        }
+        // north y-face (rows 0..NW-2, lanes 1..30): shared with the row above as its south face
+        if (w <= NW - 2 && interior_col) {
+            const int wu = w + 1;
+            const float phib = (1.f - fN.w) * Ms(so, w, 0, lane) + fN.w * Ms(so, wu, 0, lane) +
+                               fN.hcd * (Ms(so, w, 2, lane) - Ms(so, wu, 2, lane)) -
+                               k.hc * (fN.tl * ((Ms(so, w, 1, l2) - Ms(so, w, 1, l1)) * cxj.ig +
+                                                (Ms(sp, w, 3, lane) - Ms(sm, w, 3, lane)) * czl.ig) +
+                                       fN.tr * ((Ms(so, wu, 1, l2) - Ms(so, wu, 1, l1)) * cxj.ig +
+                                                (Ms(sp, wu, 3, lane) - Ms(sm, wu, 3, lane)) * czl.ig));
+            const F2 phib2 = f2(phib);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                if (XP3<QQ>(q, 1) < 0) continue;
+                const int en = QE3<QQ>(q, 1), ex = QE3<QQ>(q, 0), ez = QE3<QQ>(q, 2);
+                F2 v = fma2(sgn2(1.f - fN.w, fN.hcd, en), Ps(so, w, q, lane), sgn2(fN.w, -fN.hcd, en) * Ps(so, wu, q, lane));
+                if (ex != 0)
+                    v = fma2(sgn2(0.f, -k.hc * cxj.ig, ex),
+                             tang(Ps(so, w, q, l1), Ps(so, w, q, l2), Ps(so, wu, q, l1), Ps(so, wu, q, l2), fN.tl,
+                                  fN.tr), v);
+                if (ez != 0)
+                    v = fma2(sgn2(0.f, -k.hc * czl.ig, ez),
+                             tang(Ps(sm, w, q, lane), Ps(sp, w, q, lane), Ps(sm, wu, q, lane), Ps(sp, wu, q, lane), fN.tl,
+                                  fN.tr), v);
+                const F2 f = fma2(F2{k.a_f2}, v, hf3(k, q, phib2));
+                fNy[XP3<QQ>(q, 1)] = f;
+                sY[(w * NCP + XP3<QQ>(q, 1)) * 32 + lane] = f;
+            }
+        }
+        // top z-face (interior rows)
+        if (interior_row) z_face(so, sp, a.fm[2][z + 2], fTz);
+        // west x-face: the east face of the lane to the left
+        F2 fWx[NCP];
+#pragma unroll
+        for (int s = 0; s < NCP; ++s) fWx[s] = shfl_up2(fEx[s]);
+        __syncthreads();  // south faces in sY; every read of slot sm is done
+        if (updates) {
+            const long long c = ((long long)z * ny + kk) * nx + j;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const F2 P = Ps(so, w, q, lane);
+                F2 v = fma2(F2{k.third2}, P - sF[((so * NW + w) * NP + q) * 32 + lane], P);  // ftilde^+ (Eq. 2.23)
+                if (XP3<QQ>(q, 0) >= 0)
+                    v = fma2(sgn2(0.f, -cxj.r, QE3<QQ>(q, 0)), fEx[XP3<QQ>(q, 0)] - fWx[XP3<QQ>(q, 0)], v);
+                if (XP3<QQ>(q, 1) >= 0)
+                    v = fma2(sgn2(0.f, -cyk.r, QE3<QQ>(q, 1)),
+                             fNy[XP3<QQ>(q, 1)] - sY[((w - 1) * NCP + XP3<QQ>(q, 1)) * 32 + lane], v);
+                if (XP3<QQ>(q, 2) >= 0)
+                    v = fma2(sgn2(0.f, -czl.r, QE3<QQ>(q, 2)), fTz[XP3<QQ>(q, 2)] - fB[XP3<QQ>(q, 2)], v);
+                a.fout[PA3<QQ>(q) * a.plane + c] = v.v.x;
+                a.fout[PB3<QQ>(q) * a.plane + c] = v.v.y;
+            }
+            a.fout[c] = fmaf(k.third, P0 - sF0[(so * NW + w) * 32 + lane], P0);
+        }
+#pragma unroll
+        for (int s = 0; s < NCP; ++s) fB[s] = fTz[s];
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");  // the last prefetch lands before exit
+}
+
 // phi = sum_i ftilde_i (optional output) and per-block partial sums of |V| phi in double
 template <typename T, int QQ>
 __global__ void __launch_bounds__(256) phi_mass3(const T* __restrict__ f, T* __restrict__ phi, int nx, int ny, int nz,

@@ -113,9 +113,7 @@ namespace {
 
 dugks_status cuda_fail(dugks_ctx* ctx, cudaError_t e, const char* what) {
     if (ctx) {
-        char buf[256];
-        snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
-        ctx->last_error = buf;
+        ctx->last_error = std::string(what) + ": " + cudaGetErrorString(e);
     }
     return e == cudaErrorMemoryAllocation ? DUGKS_ERR_NOMEM : DUGKS_ERR_CUDA;
 }

@@ -158,4 +158,26 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, uint64_
         : "memory");
 }
 
+// a pair of FP32 values on the packed instructions of sm_100+ (__fadd2_rn,
+// __fmul2_rn, __ffma2_rn): two opposite velocities of a velocity set
+struct F2 {
+    float2 v;
+};
+__device__ __forceinline__ F2 f2(float a, float b) { return F2{make_float2(a, b)}; }
+__device__ __forceinline__ F2 f2(float a) { return F2{make_float2(a, a)}; }
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2{__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2{__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) { return F2{__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2{__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)}; }
+__device__ __forceinline__ F2 shfl_dn2(F2 x) {
+    return f2(__shfl_down_sync(0xffffffffu, x.v.x, 1), __shfl_down_sync(0xffffffffu, x.v.y, 1));
+}
+__device__ __forceinline__ F2 shfl_up2(F2 x) {
+    return f2(__shfl_up_sync(0xffffffffu, x.v.x, 1), __shfl_up_sync(0xffffffffu, x.v.y, 1));
+}
+// (a + s b, a - s b) for the direction sign s of a pair's first velocity
+__device__ __forceinline__ F2 sgn2(float a, float b, int s) {
+    return s > 0 ? f2(a + b, a - b) : (s < 0 ? f2(a - b, a + b) : f2(a));
+}
+
 }  // namespace dugks
