@@ -227,6 +227,18 @@ struct AttrOp {
                                         int(smem3<T, QQ, NC, NW>()));
     }
 };
+struct OccOp {
+    int* occ;
+    template <typename T, int QQ, int NC, int NW>
+    cudaError_t operator()() const {
+        if constexpr (std::is_same<T, float>::value)
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, step3d_vp<QQ, NC, NW>, NW * 32,
+                                                                 smem3_vp<QQ, NW>());
+        else
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, step3d<T, QQ, NC, NW>, NW * 32,
+                                                                 smem3<T, QQ, NC, NW>());
+    }
+};
 struct NwOp {
     template <typename T, int QQ, int NC, int NW>
     int operator()() const { return NW; }
@@ -402,18 +414,32 @@ dugks_status dugks_3d_create(const dugks_3d_mesh* mesh, const dugks_3d_vset* vse
         return st;
     }
     if ((e = dispatch3(ctx, AttrOp{})) != cudaSuccess) { st = fail3(ctx, e, "cudaFuncSetAttribute"); free3(ctx); return st; }
-    // grid: 30-column strips x (NW-2)-row blocks x z segments of at least 8 planes,
-    // about four CTAs (one per SM at a time) per SM over the launch
+    // grid: 30-column strips x (NW-2)-row blocks x z segments.  The segment length
+    // minimises (waves of resident CTAs) x (planes per CTA + about one plane of
+    // pipeline fill), with segments of at least 8 planes where nz allows.
     ctx->nw = dispatch3(ctx, NwOp{});
-    int sms = 0;
+    int sms = 0, occ = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if ((e = dispatch3(ctx, OccOp{&occ})) != cudaSuccess || occ < 1) {
+        st = e != cudaSuccess ? fail3(ctx, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor") : DUGKS_ERR_UNSUPPORTED;
+        if (occ < 1 && e == cudaSuccess) ctx->last_error = "the 3-D step kernel does not fit on an SM";
+        free3(ctx);
+        return st;
+    }
     ctx->grid[0] = (ctx->nx + 29) / 30;
     ctx->grid[1] = (ctx->ny + ctx->nw - 3) / (ctx->nw - 2);
     const long long tiles = (long long)ctx->grid[0] * ctx->grid[1];
-    long long nseg = std::max<long long>(1, (4LL * std::max(sms, 1) + tiles - 1) / tiles);
-    nseg = std::min<long long>(nseg, std::max(1, ctx->nz / 8));
-    nseg = std::min<long long>(nseg, 65535);
-    ctx->zseg = int((ctx->nz + nseg - 1) / nseg);
+    const long long slots = (long long)std::max(sms, 1) * occ;
+    double best = INFINITY;
+    for (int zs = ctx->nz; zs >= std::min(8, ctx->nz); --zs) {
+        const long long nseg = (ctx->nz + zs - 1) / zs;
+        if (nseg > 65535) break;
+        const double cost = double((tiles * nseg + slots - 1) / slots) * (zs + 1.0);
+        if (cost < best * (1.0 - 1e-9)) {
+            best = cost;
+            ctx->zseg = zs;
+        }
+    }
     // tuning override (planes per CTA segment), e.g. for a sweep
     if (const char* v = getenv("DUGKS_3D_ZSEG")) ctx->zseg = std::max(1, std::min(ctx->nz, atoi(v)));
     ctx->grid[2] = (ctx->nz + ctx->zseg - 1) / ctx->zseg;

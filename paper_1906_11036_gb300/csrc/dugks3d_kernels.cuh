@@ -549,12 +549,18 @@ __global__ void __launch_bounds__(NW * 32, 1) step3d_vp(const Args3<float> a, co
     F2 fB[NCP];
     if (interior_row) z_face(0, 1, a.fm[2][z0 + 1], fB);
 
+    // z metrics of the plane being updated and of its top face, loaded a plane ahead
+    CellM<float> czn = a.cm[2][z0 + 1];
+    FaceM<float> fzn = a.fm[2][z0 + 2];
     for (int z = z0; z < z1; ++z) {
         const int sm = (z - z0) % 3, so = (z - z0 + 1) % 3, sp = (z - z0 + 2) % 3;
         const float P0 = P0n;
+        const CellM<float> czl = czn;
+        const FaceM<float> fzt = fzn;
+        czn = a.cm[2][min(z + 2, nz)];
+        fzn = a.fm[2][min(z + 3, nz + 1)];
         P0n = compute_P(z + 1, sp, z + 2);
         __syncthreads();
-        const CellM<float> czl = a.cm[2][z + 1];
         F2 fEx[NCP], fNy[NCP], fTz[NCP];
 #pragma unroll
         for (int s = 0; s < NCP; ++s) fEx[s] = fNy[s] = fTz[s] = f2(0.f);
@@ -613,7 +619,7 @@ __global__ void __launch_bounds__(NW * 32, 1) step3d_vp(const Args3<float> a, co
             }
         }
         // top z-face (interior rows)
-        if (interior_row) z_face(so, sp, a.fm[2][z + 2], fTz);
+        if (interior_row) z_face(so, sp, fzt, fTz);
         // west x-face: the east face of the lane to the left
         F2 fWx[NCP];
 #pragma unroll
