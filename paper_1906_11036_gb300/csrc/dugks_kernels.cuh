@@ -725,14 +725,11 @@ __device__ __forceinline__ void add_source_vp(const SrcArgs<float>& sa, const fl
 #ifndef DUGKS_VP_UNROLL
 #define DUGKS_VP_UNROLL 2
 #endif
-#ifndef DUGKS_VP_SRC_UNROLL
-#define DUGKS_VP_SRC_UNROLL 1
-#endif
 #ifndef DUGKS_VP_SRC_MIN_WARPS
 #define DUGKS_VP_SRC_MIN_WARPS 16
 #endif
-// rows per iteration of the row loop, without and with the source terms (instruction-cache footprint)
-constexpr int kVpUnroll = DUGKS_VP_UNROLL, kVpSrcUnroll = DUGKS_VP_SRC_UNROLL;
+// rows per iteration of the row loop without the source terms
+constexpr int kVpUnroll = DUGKS_VP_UNROLL;
 
 template <int NC, bool EDGE, bool SRC = false>
 __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<float, NC>& a, const ConstsP<NC>& k,
@@ -895,6 +892,38 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
     F2 Pm[4], fS[4], Gx[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) { Pm[q] = fS[q] = Gx[q] = f2(0.f); }
+    if constexpr (SRC) {
+        // one loop over rows y0-1 .. y1 whose first two passes skip the parts that need the
+        // rows below: the source arithmetic is inlined once (instruction-cache footprint)
+        P0 = Fp0 = Ly = V9{};
+#pragma unroll 1
+        for (int r = y0 - 1; r <= y1; ++r) {
+            V9 P, Fp;
+            F2 fN[4];
+            if (!load_row(r, F)) { failed = true; break; }
+            const FaceM<float> fyB = a.fy[r + 1], fyA = a.fy[r + 2];  // faces below / above row r
+            vp_cell(k, F, P, Fp, ghost_of(r), bv_of(r));
+            cell_src(r, F, P, Fp);
+            grad_x(r, P, Gx);
+            if (r >= y0) vp_yface(k, fyB, P, Gx, Ly, fN);
+            vp_lower(k, fyA, P, Gx, Ly);
+            if (r > y0) {
+                const CellM<float> cyk = a.cy[r];  // row r - 1
+                V9 fb;
+                F2 dW[4];
+                x_fbar(cyk, P0, P, Pm, fb);
+                vp_xflux(k, fb, dW);
+                x_store(r - 1, cyk, Fp0, dW, fN, fS);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                Pm[q] = P0.p[q];
+                if (r >= y0) fS[q] = fN[q];
+            }
+            P0 = P;
+            Fp0 = Fp;
+        }
+    } else {
     if (!load_row(y0 - 1, F)) failed = true;
     // face metrics: fyB = face below the current row, fyA = face above it (index f+1 for face f)
     FaceM<float> fyB = a.fy[y0], fyA = a.fy[y0 + 1];
@@ -915,7 +944,7 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
         grad_x(y0, P0, Gx);
         vp_yface(k, fyB, P0, Gx, Ly, fS);
         vp_lower(k, fyA, P0, Gx, Ly);
-#pragma unroll(SRC ? kVpSrcUnroll : kVpUnroll)
+#pragma unroll(kVpUnroll)
         for (int r = y0 + 1; r <= y1; ++r) {
             V9 P, Fp;
             F2 fN[4];
@@ -943,6 +972,7 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
             P0 = P;
             Fp0 = Fp;
         }
+    }
     }
     if (failed && lane == 0) {
         atomicOr(a.err, 1);
