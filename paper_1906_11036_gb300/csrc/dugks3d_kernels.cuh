@@ -624,7 +624,13 @@ __global__ void __launch_bounds__(NW * 32, 1) step3d_vp(const Args3<float> a, co
         F2 fWx[NCP];
 #pragma unroll
         for (int s = 0; s < NCP; ++s) fWx[s] = shfl_up2(fEx[s]);
-        __syncthreads();  // south faces in sY; every read of slot sm is done
+        // Row w's update needs the south face of row w - 1 (sY), and the next compute_P of
+        // row w overwrites, in slot sm, data that row w - 1 has read for its faces: so each
+        // row waits for the row below only (named barrier w: row w - 1 arrives, row w waits)
+        // instead of for the whole CTA.  Every barrier id 1 .. NW-1 has exactly one arriving
+        // and one waiting warp per plane.
+        if (w <= NW - 2) asm volatile("bar.arrive %0, 64;" ::"r"(w + 1) : "memory");
+        if (w >= 1) asm volatile("bar.sync %0, 64;" ::"r"(w) : "memory");
         if (updates) {
             const long long c = ((long long)z * ny + kk) * nx + j;
 #pragma unroll
