@@ -71,6 +71,15 @@ __device__ __forceinline__ void dfeq_all(const AdjConsts<T, NC>& ka, T phi, T (&
     out[0] = T(1) - s;
 }
 
+// d feq_i / d phi of one moving velocity (i > 0), as dfeq_all computes it
+template <typename T, int NC>
+__device__ __forceinline__ T dfeq_i(const AdjConsts<T, NC>& ka, int i, T phi) {
+    T v = ka.dfeq[i][NC - 1];
+#pragma unroll
+    for (int m = NC - 2; m >= 0; --m) v = fma(v, phi, ka.dfeq[i][m]);
+    return v;
+}
+
 template <typename T>
 __device__ __forceinline__ void block_partial(double v, double* out, int accumulate) {
 #pragma unroll
@@ -314,9 +323,14 @@ __global__ void __launch_bounds__(TX * TY) adj_tile_kernel(const StepArgs<T, NC>
                         (m.w - en * m.hcd) * Pt(i, prow, pr) - et * k.hc * m.tr * GR;
                 phib += fb[i];
             }
+            // feq and its derivative at phi_b: only the velocities crossing the face carry a flux adjoint
             T fe[Q], dfe[Q];
-            feq_all(k, phib, fe);
-            dfeq_all(ka, phib, dfe);
+#pragma unroll
+            for (int i = 1; i < Q; ++i)
+                if (EX(i) != 0) {
+                    fe[i] = feq_i(k, i, phib);
+                    dfe[i] = dfeq_i(ka, i, phib);
+                }
             const TileIdx Lc = tile_idx(jf - 1, nx, a.xper), Rc = tile_idx(jf, nx, a.xper);
             const T rL = lghost ? T(0) : a.cx[Lc.i + 1].r, rR = rghost ? T(0) : a.cx[Rc.i + 1].r;
             T gv[Q];
@@ -326,13 +340,13 @@ __global__ void __launch_bounds__(TX * TY) adj_tile_kernel(const StepArgs<T, NC>
                 T v = T(0);
                 if (EX(i) != 0) v = T(EX(i)) * (rR * Mt(i, xr, xc + 1) - rL * Mt(i, xr, xc));
                 gv[i] = v;
-                sg += v * dfe[i];
+                if (EX(i) != 0) sg += v * dfe[i];
             }
             T sdl = T(0);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 A[i] = fma(ka.a_f, gv[i], ka.b_f * sg);
-                sdl += gv[i] * fma(ka.da_f, fb[i], ka.db_f * fe[i]);
+                if (EX(i) != 0) sdl += gv[i] * fma(ka.da_f, fb[i], ka.db_f * fe[i]);
             }
             const bool owned = (xr >= 1 && xr <= TY && row < ny) && (xc < TX || jf == nx);
             if (owned && !(a.xper && jf == nx)) djdl += double(sdl);  // a periodic face is counted once
@@ -369,9 +383,14 @@ __global__ void __launch_bounds__(TX * TY) adj_tile_kernel(const StepArgs<T, NC>
                         (m.w - en * m.hcd) * Pt(i, pr, pc) - et * k.hc * m.tr * GR;
                 phib += fb[i];
             }
+            // feq and its derivative at phi_b: only the velocities crossing the face carry a flux adjoint
             T fe[Q], dfe[Q];
-            feq_all(k, phib, fe);
-            dfeq_all(ka, phib, dfe);
+#pragma unroll
+            for (int i = 1; i < Q; ++i)
+                if (EY(i) != 0) {
+                    fe[i] = feq_i(k, i, phib);
+                    dfe[i] = dfeq_i(ka, i, phib);
+                }
             const TileIdx Lr = tile_idx(kf - 1, ny, a.yper), Rr = tile_idx(kf, ny, a.yper);
             const T rL = lghost ? T(0) : a.cy[Lr.i + 1].r, rR = rghost ? T(0) : a.cy[Rr.i + 1].r;
             T gv[Q];
@@ -381,13 +400,13 @@ __global__ void __launch_bounds__(TX * TY) adj_tile_kernel(const StepArgs<T, NC>
                 T v = T(0);
                 if (EY(i) != 0) v = T(EY(i)) * (rR * Mt(i, yr + 1, yc) - rL * Mt(i, yr, yc));
                 gv[i] = v;
-                sg += v * dfe[i];
+                if (EY(i) != 0) sg += v * dfe[i];
             }
             T sdl = T(0);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 A[i] = fma(ka.a_f, gv[i], ka.b_f * sg);
-                sdl += gv[i] * fma(ka.da_f, fb[i], ka.db_f * fe[i]);
+                if (EY(i) != 0) sdl += gv[i] * fma(ka.da_f, fb[i], ka.db_f * fe[i]);
             }
             const bool owned = (yc >= 1 && yc <= TX && col < nx) && (yr < TY || kf == ny);
             if (owned && !(a.yper && kf == ny)) djdl += double(sdl);
