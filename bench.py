@@ -249,9 +249,37 @@ def adjoint_ratio(args):
     s.gradient(phi0_t, p.steps, phiN, checkpoint_every=20)
     t_grad = time.perf_counter() - t0
     s.close()
-    return {"workload": "burgers_512x512, 400 FP32 steps, checkpoint every 20",
-            "forward_ms_per_step": t_fwd, "adjoint_ms_per_step": t_adj, "adjoint_step_ratio": t_adj / t_fwd,
-            "forward_run_s": t_run, "gradient_s": t_grad, "gradient_to_forward_ratio": t_grad / t_run}
+    out = {"workload": "burgers_512x512, 400 FP32 steps, checkpoint every 20",
+           "forward_ms_per_step": t_fwd, "adjoint_ms_per_step": t_adj, "adjoint_step_ratio": t_adj / t_fwd,
+           "forward_run_s": t_run, "gradient_s": t_grad, "gradient_to_forward_ratio": t_grad / t_run}
+    # the same step on 2048^2 (state, mu and lambda larger than L2): roofline of the adjoint step,
+    # algorithmic bytes = read ftilde^n and mu, write lambda = 3 x 36 B per cell in FP32
+    p, phi0 = I.burgers(2048, steps=20)
+    s = Solver(p, precision=32)
+    s.init_phi(torch.tensor(phi0, dtype=torch.float32, device="cuda"))
+    s.step(5)
+    f = s.save_state().clone()
+    mu = torch.randn_like(f)
+    lam, da = s.adjoint_step(f, mu)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(s.stream)
+    s.step(20)
+    ev[1].record(s.stream)
+    ev[2].record(s.stream)
+    for _ in range(10):
+        lam, da = s.adjoint_step(f, mu, da)
+    ev[3].record(s.stream)
+    ev[3].synchronize()
+    t_fwd2, t_adj2 = ev[0].elapsed_time(ev[1]) / 20, ev[2].elapsed_time(ev[3]) / 10
+    s.close()
+    peak, peak_kind = measured_peak()
+    alg = 2048 * 2048 * 3 * Q * 4
+    out["large"] = {"workload": "burgers_2048x2048, FP32", "forward_ms_per_step": t_fwd2,
+                    "adjoint_ms_per_step": t_adj2, "adjoint_step_ratio": t_adj2 / t_fwd2,
+                    "algorithmic_bytes_per_adjoint_step": alg,
+                    "roofline_frac": alg / (t_adj2 * 1e-3) / 1e9 / peak, "peak_kind": peak_kind}
+    return out
 
 
 def batched_vs_single(steps: int = 100):
