@@ -21,6 +21,7 @@
 
 #include "../../include/dugks.h"
 #include "dugks_adjoint.cuh"
+#include "dugks_adjoint_rows.cuh"
 #include "dugks_batch.cuh"
 #include "dugks_kernels.cuh"
 
@@ -528,6 +529,60 @@ cudaError_t launch_adj_sum(dugks_ctx* ctx, double* dj_dalpha) {
     return cudaGetLastError();
 }
 
+// The row-marching FP32 adjoint (adj_rows_kernel): grids periodic on both axes, equilibrium
+// degree <= 3, f and mu rows that TMA can copy (nx a multiple of 4, 16-byte aligned buffers).
+constexpr int kAdjRowStages = 6;
+// It is used from about 3 M cells up (2048^2: 351 us against 465 us for the tiled kernel; on
+// 1024^2 and below, with too few warps in flight, the tiled kernel is faster).
+// DUGKS_ADJ_ROWS=1 / 0 forces it on (where it applies) / off.
+bool adj_rows_ok(const dugks_ctx* ctx, const void* f, const void* mu) {
+    const bool applies = ctx->precision == 32 && ctx->nc != NC_LARGE && ctx->xper && ctx->yper && ctx->nx % 4 == 0 &&
+                         ctx->nx >= 8 && ctx->ny >= 4 && (reinterpret_cast<uintptr_t>(f) % 16) == 0 &&
+                         (reinterpret_cast<uintptr_t>(mu) % 16) == 0;
+    if (!applies) return false;
+    if (const char* v = getenv("DUGKS_ADJ_ROWS")) return atoi(v) != 0;
+    return (long long)ctx->nx * ctx->ny >= 3LL * 1024 * 1024;
+}
+
+template <int NC>
+cudaError_t launch_adjoint_rows(dugks_ctx* ctx, const StepArgs<float, NC>& a, const Consts<float, NC>& k,
+                                const AdjConsts<float, NC>& ka, const AdjArgs<float>& g, const void* f,
+                                const void* mu) {
+    EncodeTiledFn encode = tiled_encoder(ctx);
+    if (!encode) return cudaErrorNotSupported;
+    using L = AdjRowLayout;
+    CUtensorMap tm[2];
+    const cuuint64_t dims[3] = {cuuint64_t(ctx->nx), cuuint64_t(ctx->ny), cuuint64_t(Q)};
+    const cuuint64_t strides[2] = {cuuint64_t(ctx->nx) * 4, cuuint64_t(ctx->nx) * ctx->ny * 4};
+    const cuuint32_t box[3] = {cuuint32_t(L::BOXW), 1u, cuuint32_t(Q)};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    const void* base[2] = {f, mu};
+    for (int b = 0; b < 2; ++b)
+        if (encode(&tm[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base[b]), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e != cudaSuccess) return e;
+    // about three waves of 12 warps per SM, segments of at least 16 rows, one partial per warp
+    const int strips = (ctx->nx + L::WI - 1) / L::WI;
+    const long long cap = adj_partials(ctx);
+    long long nseg = std::max<long long>(1, 36LL * sms / strips);
+    nseg = std::min<long long>(nseg, std::max(1, ctx->ny / 16));
+    nseg = std::max<long long>(1, std::min<long long>(nseg, cap / strips));
+    const int seg = int((ctx->ny + nseg - 1) / nseg);
+    nseg = (ctx->ny + seg - 1) / seg;
+    if ((long long)strips * nseg > cap) return cudaErrorInvalidConfiguration;
+    if (!g.accumulate && (long long)strips * nseg < cap)  // slots this launch leaves alone are summed too
+        if ((e = cudaMemsetAsync(g.partial + strips * nseg, 0, sizeof(double) * size_t(cap - strips * nseg),
+                                 ctx->stream)) != cudaSuccess)
+            return e;
+    adj_rows_kernel<NC><<<dim3(strips, unsigned(nseg)), 32, L::bytes(kAdjRowStages), ctx->stream>>>(
+        tm[0], tm[1], a, k, ka, g, seg, kAdjRowStages);
+    return cudaGetLastError();
+}
+
 // One adjoint step.  dj_dalpha != nullptr: the step's partials overwrite the
 // partial buffer and are summed into *dj_dalpha; nullptr: they are added to the
 // partial buffer (a reverse sweep zeroes it first and sums it at the end).
@@ -547,6 +602,14 @@ cudaError_t launch_adjoint_step(dugks_ctx* ctx, const void* f, const void* mu, v
     g.Ay = static_cast<T*>(ctx->adj_ay);
     g.partial = ctx->adj_partial;
     g.accumulate = dj_dalpha ? 0 : 1;
+    if constexpr (sizeof(T) == 4 && NC != NC_LARGE) {
+        if (adj_rows_ok(ctx, f, mu)) {
+            cudaError_t e = launch_adjoint_rows<NC>(ctx, a, k, ka, g, f, mu);
+            if (e != cudaSuccess) return e;
+            if (dj_dalpha) return launch_adj_sum(ctx, dj_dalpha);
+            return cudaGetLastError();
+        }
+    }
     const int tb = adj_tile_blocks(ctx);
     const size_t smem = AdjTile<T, kAdjTX, kAdjTY>::bytes();
     cudaError_t e = cudaFuncSetAttribute(adj_tile_kernel<T, NC, kAdjTX, kAdjTY>,

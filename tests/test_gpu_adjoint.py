@@ -50,6 +50,11 @@ CASES = {
     "poly_20x13": lambda: I.burgers(20, 13)[0].with_(b=(0.05, 0.3, 0.2, 0.1), d=(0.1, 0.6, 0.2, 0.05)),
     "tiny_3x2": lambda: I.burgers(3, 2)[0],
     "tiny_walls_2x3": lambda: I.nonuniform(2, 3)[0],
+    # periodic grids with nx a multiple of 4: FP32 runs the row-marching adjoint
+    "periodic_rows_64x37": lambda: I.burgers(64, 37)[0],
+    "periodic_rows_124x50": lambda: I.burgers(124, 50)[0],
+    "periodic_mixed_40x33": lambda: _mixed(False, False, 40, 33),
+    "periodic_rows_8x5": lambda: I.burgers(8, 5)[0],
 }
 
 
@@ -59,7 +64,9 @@ def _rel(a, b):
 
 @pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("name", list(CASES))
-def test_adjoint_step_matches_oracle(name, prec):
+def test_adjoint_step_matches_oracle(name, prec, monkeypatch):
+    if name.startswith("periodic_"):
+        monkeypatch.setenv("DUGKS_ADJ_ROWS", "1")  # the row-marching FP32 adjoint, whatever the size
     p = CASES[name]()
     rng = np.random.default_rng(len(name))
     o = Oracle(p)
@@ -77,8 +84,32 @@ def test_adjoint_step_matches_oracle(name, prec):
     assert abs(da - da_ref) <= tol * 10 * max(abs(da_ref), 1e-12)
 
 
-@pytest.mark.parametrize("prec", [64, 32])
-def test_checkpointed_gradient_matches_oracle(prec):
+def test_row_marching_and_tiled_fp32_adjoints_agree(monkeypatch):
+    """On a periodic grid the FP32 adjoint step runs as a row march; the tiled
+    kernel (DUGKS_ADJ_ROWS=0) computes the same quantities: they agree to FP32
+    rounding, and both match the FP64 oracle."""
+    p = I.burgers(256, 200)[0]
+    rng = np.random.default_rng(3)
+    o = Oracle(p)
+    f = o.init(1.0 + 0.2 * rng.standard_normal((p.ny, p.nx))) + 0.01 * rng.standard_normal((9, p.ny, p.nx))
+    mu = rng.standard_normal(f.shape)
+    lam_ref, da_ref = o.adjoint_step(f, mu)
+    out = []
+    for rows in ("1", "0"):
+        monkeypatch.setenv("DUGKS_ADJ_ROWS", rows)
+        s = _solver(p, 32)
+        lam, da = s.adjoint_step(torch.tensor(f, dtype=torch.float32, device="cuda"),
+                                 torch.tensor(mu, dtype=torch.float32, device="cuda"))
+        out.append((lam.double().cpu().numpy(), float(da.item())))
+        s.close()
+    (lr, dr), (lt, dtl) = out
+    assert _rel(lr, lt) <= 1e-5 and abs(dr - dtl) <= 1e-4 * abs(dtl)
+    assert _rel(lr, lam_ref) <= 2e-5 and abs(dr - da_ref) <= 2e-4 * abs(da_ref)
+
+
+@pytest.mark.parametrize("prec,rows", [(64, "0"), (32, "0"), (32, "1")])
+def test_checkpointed_gradient_matches_oracle(prec, rows, monkeypatch):
+    monkeypatch.setenv("DUGKS_ADJ_ROWS", rows)  # FP32: the tiled and the row-marching adjoint
     p, phi0 = I.burgers(48, 40, steps=60)
     xc, yc = p.centres()
     area = np.outer(np.diff(p.yf), np.diff(p.xf))
