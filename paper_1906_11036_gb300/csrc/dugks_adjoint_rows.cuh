@@ -20,7 +20,7 @@
 namespace dugks {
 
 #ifndef DUGKS_ADJ_ROWS_MIN_WARPS
-#define DUGKS_ADJ_ROWS_MIN_WARPS 12
+#define DUGKS_ADJ_ROWS_MIN_WARPS 16  // 126 registers, no spills; 4 stages keep 16 warps in shared memory
 #endif
 
 struct AdjRowLayout {

@@ -531,8 +531,11 @@ cudaError_t launch_adj_sum(dugks_ctx* ctx, double* dj_dalpha) {
 
 // The row-marching FP32 adjoint (adj_rows_kernel): grids periodic on both axes, equilibrium
 // degree <= 3, f and mu rows that TMA can copy (nx a multiple of 4, 16-byte aligned buffers).
-constexpr int kAdjRowStages = 6;
-// It is used from about 3 M cells up (2048^2: 351 us against 465 us for the tiled kernel; on
+#ifndef DUGKS_ADJ_ROW_STAGES
+#define DUGKS_ADJ_ROW_STAGES 4
+#endif
+constexpr int kAdjRowStages = DUGKS_ADJ_ROW_STAGES;  // row stages in flight per warp (>= 3)
+// It is used from about 3 M cells up (2048^2: 344 us against 465 us for the tiled kernel; on
 // 1024^2 and below, with too few warps in flight, the tiled kernel is faster).
 // DUGKS_ADJ_ROWS=1 / 0 forces it on (where it applies) / off.
 bool adj_rows_ok(const dugks_ctx* ctx, const void* f, const void* mu) {
