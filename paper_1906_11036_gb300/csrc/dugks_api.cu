@@ -568,7 +568,7 @@ cudaError_t launch_adjoint_rows(dugks_ctx* ctx, const StepArgs<float, NC>& a, co
     int sms = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e != cudaSuccess) return e;
-    // about three waves of 12 warps per SM, segments of at least 16 rows, one partial per warp
+    // about 36 warps per SM over the launch, segments of at least 16 rows, one partial per warp
     const int strips = (ctx->nx + L::WI - 1) / L::WI;
     const long long cap = adj_partials(ctx);
     long long nseg = std::max<long long>(1, 36LL * sms / strips);
