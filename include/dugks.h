@@ -41,7 +41,7 @@ typedef enum {
     DUGKS_ERR_CONFIG = 2,      /* physically invalid setup (CFL >= 1, alpha <= 0, faces not increasing) */
     DUGKS_ERR_CUDA = 3,        /* a CUDA runtime or driver call failed */
     DUGKS_ERR_NONFINITE = 4,   /* NaN or Inf detected in phi */
-    DUGKS_ERR_UNSUPPORTED = 5, /* valid request that this build does not implement */
+    DUGKS_ERR_UNSUPPORTED = 5, /* valid request that the library does not implement */
     DUGKS_ERR_NOMEM = 6,       /* device or host allocation failed */
     DUGKS_ERR_TIMEOUT = 7      /* a bounded device-side wait expired; the step result is invalid */
 } dugks_status;
