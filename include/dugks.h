@@ -180,6 +180,14 @@ dugks_status dugks_set_stream(dugks_ctx *ctx, void *stream);
  * (DUGKS_ERR_TIMEOUT) or a CUDA error. */
 dugks_status dugks_sync(dugks_ctx *ctx);
 
+/* Failure-path check without a fault: launches one warp that waits at most
+ * limit_us microseconds (1 ... 1000000) on an mbarrier that nothing completes,
+ * the same bounded wait the step kernels use.  The wait expires and sets the
+ * context's device error word, so the next dugks_sync returns
+ * DUGKS_ERR_TIMEOUT (and keeps doing so: the context stays in the error state).
+ * DUGKS_ERR_ARG for a null ctx or a limit outside the range. */
+dugks_status dugks_wait_timeout_check(dugks_ctx *ctx, int limit_us);
+
 /* Sizes and launch shape of a context. */
 dugks_status dugks_info(const dugks_ctx *ctx, dugks_info_t *out);
 

@@ -1104,6 +1104,14 @@ dugks_status dugks_sync(dugks_ctx* ctx) {
     return DUGKS_OK;
 }
 
+dugks_status dugks_wait_timeout_check(dugks_ctx* ctx, int limit_us) {
+    if (!ctx || limit_us < 1 || limit_us > 1000000) return DUGKS_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    wait_timeout_kernel<<<1, 32, 0, ctx->stream>>>(ctx->err_dev, 1000ull * (unsigned long long)limit_us);
+    CK(cudaGetLastError());
+    return DUGKS_OK;
+}
+
 dugks_status dugks_info(const dugks_ctx* ctx, dugks_info_t* out) {
     if (!ctx || !out) return DUGKS_ERR_ARG;
     out->nx = ctx->nx;

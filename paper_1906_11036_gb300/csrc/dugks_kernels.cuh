@@ -1009,6 +1009,19 @@ __global__ void __launch_bounds__(32, DUGKS_VP_MIN_WARPS) fused_step_vp(const __
     else vp_rows<NC, false>(&tin, a, k, smem, bars, S, lane, xw, y0, y1, ring);
 }
 
+// One warp waits, bounded, on an mbarrier that nothing completes: the wait expires and the
+// error word is set, as after a stalled copy in a step kernel.
+__global__ void __launch_bounds__(32) wait_timeout_kernel(int* err, unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const bool ok = mbar_wait_bounded(&bar, 0u, limit_ns);
+    if (__any_sync(0xffffffffu, !ok) && threadIdx.x == 0) atomicOr(err, 1);
+}
+
 // the velocity-pair step with the source terms F and R (16 resident warps per SM,
 // as the plain step; the source arithmetic fits in 128 registers without spills)
 template <int NC>

@@ -102,6 +102,7 @@ def library():
         L.dugks_load_state.argtypes = [vp, vp]
         L.dugks_set_stream.argtypes = [vp, vp]
         L.dugks_sync.argtypes = [vp]
+        L.dugks_wait_timeout_check.argtypes = [vp, ctypes.c_int]
         L.dugks_info.argtypes = [vp, P(Info)]
         L.dugks_adjoint_step.argtypes = [vp, vp, vp, vp, vp]
         L.dugks_set_source.argtypes = [vp, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int), vp, ctypes.c_double]
@@ -141,7 +142,8 @@ def library():
         L.dugks_last_error.restype = ctypes.c_char_p
         for name in ("dugks_check_config", "dugks_create", "dugks_destroy", "dugks_init_phi", "dugks_init_phi_host",
                      "dugks_step", "dugks_get_phi", "dugks_get_phi_host", "dugks_save_state", "dugks_load_state",
-                     "dugks_set_stream", "dugks_sync", "dugks_info", "dugks_adjoint_step", "dugks_adjoint",
+                     "dugks_set_stream", "dugks_sync", "dugks_wait_timeout_check", "dugks_info",
+                     "dugks_adjoint_step", "dugks_adjoint",
                      "dugks_set_source",
                      "dugks_phi_mass_noalloc", "dugks_batch_create", "dugks_batch_destroy", "dugks_batch_init_phi",
                      "dugks_batch_step", "dugks_batch_get_phi", "dugks_batch_save_state", "dugks_batch_sync",
@@ -324,6 +326,10 @@ class Solver:
 
     def sync(self):
         self._check(self.L.dugks_sync(self.h), "dugks_sync")
+
+    def wait_timeout_check(self, limit_us: int = 2000):
+        """Let one bounded device wait expire on purpose (no fault): the next sync raises DUGKS_ERR_TIMEOUT."""
+        self._check(self.L.dugks_wait_timeout_check(self.h, int(limit_us)), "dugks_wait_timeout_check")
 
     def adjoint_step(self, f, mu, dj_dalpha=None):
         """lam = (d f^{n+1}/d f^n)^T mu at state f (CUDA tensors [9, ny, nx]); the

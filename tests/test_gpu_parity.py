@@ -246,3 +246,26 @@ def test_full_size_fp32_vs_stored_oracle(name):
     print(f"{name}: FP32 rel-L2 vs FP64 oracle over {len(got)} samples after {p.steps} steps: {err:.3e}")
     assert err <= 2e-5
     assert abs(m - float(g["mass"])) <= 2e-5 * abs(float(g["mass"]))
+
+
+def test_expired_bounded_wait_is_reported_without_a_fault():
+    """Failure detection without a GPU fault: a bounded device wait that nothing
+    completes expires after ~2 ms, sets the error word, and dugks_sync reports
+    DUGKS_ERR_TIMEOUT; the context and the device stay usable."""
+    from paper_1906_11036_gb300.dugks import DugksError, Solver
+
+    p, phi0 = I.burgers(40, 30, steps=5)
+    s = Solver(p, precision=32)
+    s.init_phi(torch.tensor(phi0, device="cuda"))
+    s.step(2)
+    s.sync()
+    s.wait_timeout_check(2000)
+    with pytest.raises(DugksError) as ei:
+        s.sync()
+    assert ei.value.status == 7  # DUGKS_ERR_TIMEOUT
+    s.close()
+    t = Solver(p, precision=32)  # a fresh context runs normally afterwards
+    t.init_phi(torch.tensor(phi0, device="cuda"))
+    t.step(3)
+    t.sync()
+    t.close()
