@@ -227,6 +227,15 @@ dugks_status dugks_set_source(dugks_ctx *ctx, int nterms, const double *rate, co
 dugks_status dugks_adjoint_step(dugks_ctx *ctx, const void *f_dev, const void *mu_dev, void *lam_dev,
                                 double *dj_dalpha_dev);
 
+/* Which kernel runs an FP32 adjoint step (a cross-check hook; results agree to
+ * FP32 rounding).  DUGKS_ADJ_AUTO (the default): the row-marching kernel on
+ * grids periodic in both directions with nx a multiple of 4 from about 3 M
+ * cells, else the tiled kernel; DUGKS_ADJ_TILED: always the tiled kernel;
+ * DUGKS_ADJ_ROWS: the row-marching kernel wherever it applies, whatever the
+ * size.  DUGKS_ERR_ARG for a null ctx or an unknown value. */
+enum { DUGKS_ADJ_AUTO = 0, DUGKS_ADJ_TILED = 1, DUGKS_ADJ_ROWS = 2 };
+dugks_status dugks_set_adjoint_kernel(dugks_ctx *ctx, int kernel);
+
 /* Gradient of J through nsteps steps from phi0: given grad_phiN = dJ/dphi^N
  * (device, [ny][nx]), writes dJ/dphi^0 into grad_phi0_dev (device [ny][nx])
  * and dJ/dalpha into *grad_alpha_out (host; may be NULL).  Runs the forward

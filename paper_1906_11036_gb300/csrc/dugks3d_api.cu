@@ -440,8 +440,6 @@ dugks_status dugks_3d_create(const dugks_3d_mesh* mesh, const dugks_3d_vset* vse
             ctx->zseg = zs;
         }
     }
-    // tuning override (planes per CTA segment), e.g. for a sweep
-    if (const char* v = getenv("DUGKS_3D_ZSEG")) ctx->zseg = std::max(1, std::min(ctx->nz, atoi(v)));
     ctx->grid[2] = (ctx->nz + ctx->zseg - 1) / ctx->zseg;
     if (ctx->grid[1] > 65535) { free3(ctx); return DUGKS_ERR_ARG; }
     *out = ctx;

@@ -24,6 +24,7 @@
 #include "dugks_adjoint_rows.cuh"
 #include "dugks_batch.cuh"
 #include "dugks_kernels.cuh"
+#include "dugks_step_vp.cuh"
 
 using namespace dugks;
 
@@ -56,6 +57,7 @@ struct dugks_ctx {
     void* fym = nullptr;  // FaceM<T>[ny+3]
     void* cxm = nullptr;  // CellM<T>[nx+2]
     void* cym = nullptr;  // CellM<T>[ny+2]
+    RowY* rowy = nullptr; // FP32: per-row y metrics of step_vp, rows -1 .. ny
     double* dxv = nullptr;  // cell widths (double) for the mass
     double* dyv = nullptr;
     double* staging = nullptr;  // nx*ny doubles for host transfers
@@ -65,6 +67,8 @@ struct dugks_ctx {
     int red_blocks = 0;
     CUtensorMap tmap[2];
     int nt = 32, stages = 8, seg_rows = 0, nstrips = 0, nseg = 0, occupancy = 0;
+    int seg_rows_src = 0, nseg_src = 0;  // row segments of the source-term kernel
+    SegPlan sp{1, 0, 1};  // step_vp: long segments first, then short ones
     long long steps_done = 0;
     // adjoint work buffers (allocated on first use)
     void* adj_ax = nullptr;
@@ -90,6 +94,7 @@ struct dugks_ctx {
     double t = 0, t0 = 0;   // time of the state; source start time
     double tbase = 0;       // t = tbase + tsteps * dt (tbase set by set_source, init_phi, load_state)
     long long tsteps = 0;
+    int adj_kernel = DUGKS_ADJ_AUTO;  // dugks_set_adjoint_kernel
     std::string last_error;
 };
 
@@ -239,8 +244,8 @@ StepArgs<T, NC> make_args(const dugks_ctx* ctx, int from) {
 void* fused_fn(const dugks_ctx* ctx) {
     if (ctx->precision == 32) {
         switch (ctx->nc) {
-            case 3: return reinterpret_cast<void*>(&fused_step_vp<3>);
-            case 4: return reinterpret_cast<void*>(&fused_step_vp<4>);
+            case 3: return reinterpret_cast<void*>(&step_vp<3>);
+            case 4: return reinterpret_cast<void*>(&step_vp<4>);
             default: return reinterpret_cast<void*>(&fused_step<float, NC_LARGE>);  // high degree: scalar path
         }
     }
@@ -300,16 +305,36 @@ dugks_status make_tensor_maps(dugks_ctx* ctx) {
     return DUGKS_OK;
 }
 
-// Strip and segment counts of the fused kernel for this grid: one warp per
-// (30-column strip, row segment), enough segments to fill every SM.
+// step_vp's segments: every strip gets K = slots / nstrips long segments that together
+// cover about a fraction `first` of its rows (one wave of warps), then short segments of
+// seg_short rows.  Blocks start in launch order, so the short segments fill in behind
+// the long ones as warps finish, and each warp pays the pipeline fill (two extra rows
+// and the latency of its first loads) over a long segment.  Grids without enough rows
+// for that keep the uniform plan.
+void plan_long_short(dugks_ctx* ctx, long long slots, double first, int seg_short) {
+    const long long K = std::max<long long>(1, slots / ctx->nstrips);
+    const int L = int(first * ctx->ny / double(K));
+    if (L < 2 * seg_short || L < 24) return;
+    const int rest = ctx->ny - int(K) * L;
+    if (rest <= 0) return;
+    const int nshort = (rest + seg_short - 1) / seg_short;
+    ctx->sp = SegPlan{L, int(K), seg_short};
+    ctx->nseg = int(K) + nshort;
+    ctx->seg_rows = L;
+}
+
+// Strip and segment counts of the fused kernels for this grid: one warp per
+// (30-column strip, row segment), at least 16 rows per segment so that the two
+// pipeline-fill rows stay cheap; about three waves of segments, which the block
+// scheduler balances.  The FP32 step (step_vp) then takes the long-then-short
+// plan where the grid has the rows for it (2048^2: 35 segments of 46 rows per
+// strip, then 8-row segments; 66.5 us against 70.0 us for uniform 20-row ones).
 dugks_status plan_fused(dugks_ctx* ctx) {
     int sms = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaDeviceGetAttribute");
     ctx->nt = 32;
-    ctx->stages = 3;  // rows in flight per warp: 3 measured 0.8 % faster than 4, deeper rings slower
-    // tuning overrides (pipeline depth and rows per warp), e.g. for a sweep
-    if (const char* v = getenv("DUGKS_STAGES")) ctx->stages = std::max(2, std::min(16, atoi(v)));
+    ctx->stages = 3;  // rows in flight per warp
     void* fn = fused_fn(ctx);
     const size_t smem = fused_smem(ctx);
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -325,15 +350,41 @@ dugks_status plan_fused(dugks_ctx* ctx) {
     const int wi = WarpLayout<float>::WI;
     ctx->nstrips = (ctx->nx + wi - 1) / wi;
     const long long slots = (long long)sms * occ;
-    // about three waves of warps: short segments even out the end of each wave
-    // (measured on 2048^2: 20 rows per segment 75.8 us, 60 rows in one wave 78 us)
-    long long nseg = std::max<long long>(1, 3 * slots / ctx->nstrips);
-    // at least 16 rows per segment so the two pipeline-fill rows stay cheap
-    nseg = std::min<long long>(nseg, std::max(1, ctx->ny / 16));
-    ctx->seg_rows = int((ctx->ny + nseg - 1) / nseg);
-    if (const char* v = getenv("DUGKS_SEG_ROWS")) ctx->seg_rows = std::max(1, std::min(ctx->ny, atoi(v)));
-    ctx->nseg = (ctx->ny + ctx->seg_rows - 1) / ctx->seg_rows;
+    const long long max_seg = std::max(1, ctx->ny / 16);
+    auto cut = [&](long long nseg, int& seg_rows, int& nseg_out) {
+        nseg = std::max<long long>(1, std::min<long long>(nseg, max_seg));
+        seg_rows = int((ctx->ny + nseg - 1) / nseg);
+        nseg_out = (ctx->ny + seg_rows - 1) / seg_rows;
+    };
+    cut(3 * slots / ctx->nstrips, ctx->seg_rows, ctx->nseg);
+    cut(3 * slots / ctx->nstrips, ctx->seg_rows_src, ctx->nseg_src);
+    ctx->sp = SegPlan{ctx->seg_rows, ctx->nseg, ctx->seg_rows};
+    if (ctx->precision == 32 && ctx->nc != NC_LARGE) plan_long_short(ctx, slots, 0.8, 8);
     return DUGKS_OK;
+}
+
+// Per-row y metrics of step_vp (rows -1 .. ny at index k + 1) from the y-face and
+// y-cell metrics: the reconstruction weights of the faces below and above each row
+// (Eqs. 2.19, 2.20), its central-difference factor and its flux factor (Eq. 2.12).
+std::vector<RowY> make_rowy(const std::vector<FaceM<float>>& fy, const std::vector<CellM<float>>& cy, int ny,
+                            float hc) {
+    std::vector<RowY> rw(size_t(ny) + 2);
+    for (int k = -1; k <= ny; ++k) {
+        const FaceM<float> b = fy[size_t(k) + 1], t = fy[size_t(k) + 2];
+        RowY r;
+        r.up = make_float2(b.w - b.hcd, b.w + b.hcd);
+        r.u0 = b.w;
+        r.gu = hc * b.tr;
+        r.lp = make_float2((1.f - t.w) + t.hcd, (1.f - t.w) - t.hcd);
+        r.l0 = 1.f - t.w;
+        r.gl = hc * t.tl;
+        r.igy = cy[size_t(k) + 1].ig;
+        r.ry = cy[size_t(k) + 1].r;
+        r.hup = b.hcd;
+        r.hlo = t.hcd;
+        rw[size_t(k) + 1] = r;
+    }
+    return rw;
 }
 
 // Launch arguments of the source terms for the step from ctx->t (Eqs. 2.3, 2.12, 2.18).
@@ -377,14 +428,15 @@ cudaError_t launch_step(dugks_ctx* ctx) {
     const StepArgs<T, NC> a = make_args<T, NC>(ctx, ctx->cur);
     const Consts<T, NC> k = make_consts<T, NC>(ctx);
     if (ctx->nsrc > 0) {  // the fused kernel with the source terms: velocity pairs in FP32, else scalar
-        dim3 grid(ctx->nstrips, ctx->nseg);
+        dim3 grid(ctx->nstrips, ctx->nseg_src);
         if constexpr (sizeof(T) == 4 && NC != NC_LARGE)
             fused_step_vp_src<NC><<<grid, 32, src_vp_smem(ctx), ctx->stream>>>(
-                ctx->tmap[ctx->cur], a, make_constsp<NC>(ctx), ctx->seg_rows, ctx->stages, make_src_args<float>(ctx),
-                ctx->taux[ctx->cur]);
+                ctx->tmap[ctx->cur], a, make_constsp<NC>(ctx), ctx->seg_rows_src, ctx->stages,
+                make_src_args<float>(ctx), ctx->taux[ctx->cur]);
         else
-            fused_step_src<T, NC><<<grid, 32, fused_smem(ctx), ctx->stream>>>(ctx->tmap[ctx->cur], a, k, ctx->seg_rows,
-                                                                             ctx->stages, make_src_args<T>(ctx));
+            fused_step_src<T, NC><<<grid, 32, fused_smem(ctx), ctx->stream>>>(ctx->tmap[ctx->cur], a, k,
+                                                                             ctx->seg_rows_src, ctx->stages,
+                                                                             make_src_args<T>(ctx));
         return cudaGetLastError();
     }
     if (ctx->kernel == DUGKS_KERNEL_NAIVE) {
@@ -393,8 +445,8 @@ cudaError_t launch_step(dugks_ctx* ctx) {
     } else {
         dim3 grid(ctx->nstrips, ctx->nseg);
         if constexpr (sizeof(T) == 4 && NC != NC_LARGE)
-            fused_step_vp<NC><<<grid, 32, fused_smem(ctx), ctx->stream>>>(ctx->tmap[ctx->cur], a, make_constsp<NC>(ctx),
-                                                                         ctx->seg_rows, ctx->stages);
+            step_vp<NC><<<grid, 32, fused_smem(ctx), ctx->stream>>>(ctx->tmap[ctx->cur], a, make_constsp<NC>(ctx),
+                                                                   ctx->rowy, ctx->sp, ctx->stages);
         else
             fused_step<T, NC><<<grid, 32, fused_smem(ctx), ctx->stream>>>(ctx->tmap[ctx->cur], a, k, ctx->seg_rows,
                                                                          ctx->stages);
@@ -442,7 +494,8 @@ void free_ctx(dugks_ctx* ctx) {
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(ctx->device);
-    for (void* p : {ctx->buf[0], ctx->buf[1], ctx->fxm, ctx->fym, ctx->cxm, ctx->cym, ctx->adj_ax, ctx->adj_ay,
+    for (void* p : {ctx->buf[0], ctx->buf[1], ctx->fxm, ctx->fym, ctx->cxm, ctx->cym, static_cast<void*>(ctx->rowy),
+                    ctx->adj_ax, ctx->adj_ay,
                     ctx->src_field, ctx->hist[0], ctx->hist[1], ctx->aux[0], ctx->aux[1],
                     static_cast<void*>(ctx->adj_partial), static_cast<void*>(ctx->adj_dalpha)})
         if (p) cudaFree(p);
@@ -536,14 +589,14 @@ cudaError_t launch_adj_sum(dugks_ctx* ctx, double* dj_dalpha) {
 #endif
 constexpr int kAdjRowStages = DUGKS_ADJ_ROW_STAGES;  // row stages in flight per warp (>= 3)
 // It is used from about 3 M cells up (2048^2: 344 us against 465 us for the tiled kernel; on
-// 1024^2 and below, with too few warps in flight, the tiled kernel is faster).
-// DUGKS_ADJ_ROWS=1 / 0 forces it on (where it applies) / off.
+// 1024^2 and below, with too few warps in flight, the tiled kernel is faster), or wherever it
+// applies when dugks_set_adjoint_kernel asked for it.
 bool adj_rows_ok(const dugks_ctx* ctx, const void* f, const void* mu) {
     const bool applies = ctx->precision == 32 && ctx->nc != NC_LARGE && ctx->xper && ctx->yper && ctx->nx % 4 == 0 &&
                          ctx->nx >= 8 && ctx->ny >= 4 && (reinterpret_cast<uintptr_t>(f) % 16) == 0 &&
                          (reinterpret_cast<uintptr_t>(mu) % 16) == 0;
-    if (!applies) return false;
-    if (const char* v = getenv("DUGKS_ADJ_ROWS")) return atoi(v) != 0;
+    if (!applies || ctx->adj_kernel == DUGKS_ADJ_TILED) return false;
+    if (ctx->adj_kernel == DUGKS_ADJ_ROWS) return true;
     return (long long)ctx->nx * ctx->ny >= 3LL * 1024 * 1024;
 }
 
@@ -678,6 +731,7 @@ dugks_status batch_build_tables(dugks_batch* b) {
         I.args[1] = make_args<float, NC>(c, 1);
         I.args[0].err = I.args[1].err = b->d_err;
         I.k = make_constsp<NC>(c);
+        I.rw = c->rowy;
         I.nstrips = (c->nx + WarpLayout<float>::WI - 1) / WarpLayout<float>::WI;
         I.seg_rows = std::max(1, std::min(b->seg_target, c->ny));
         I.nseg = (c->ny + I.seg_rows - 1) / I.seg_rows;
@@ -943,6 +997,13 @@ dugks_status dugks_create(const dugks_mesh* mesh, const dugks_vset* vset, const 
             (e = upload(&ctx->cxm, cx.data(), cx.size() * sizeof(cx[0]))) != cudaSuccess ||
             (e = upload(&ctx->cym, cy.data(), cy.size() * sizeof(cy[0]))) != cudaSuccess)
             return fail(cuda_fail(ctx, e, "metrics upload"));
+        const std::vector<RowY> rw = make_rowy(fy, cy, ctx->ny, float(ctx->hc));
+        void* prw = nullptr;
+        if ((e = upload(&prw, rw.data(), rw.size() * sizeof(rw[0]))) != cudaSuccess) {
+            ctx->rowy = static_cast<RowY*>(prw);
+            return fail(cuda_fail(ctx, e, "row metrics upload"));
+        }
+        ctx->rowy = static_cast<RowY*>(prw);
     } else {
         std::vector<FaceM<double>> fx, fy;
         std::vector<CellM<double>> cx, cy;
@@ -1101,6 +1162,13 @@ dugks_status dugks_sync(dugks_ctx* ctx) {
         ctx->last_error = "a bounded TMA wait in the step kernel expired";
         return DUGKS_ERR_TIMEOUT;
     }
+    return DUGKS_OK;
+}
+
+dugks_status dugks_set_adjoint_kernel(dugks_ctx* ctx, int kernel) {
+    if (!ctx || (kernel != DUGKS_ADJ_AUTO && kernel != DUGKS_ADJ_TILED && kernel != DUGKS_ADJ_ROWS))
+        return DUGKS_ERR_ARG;
+    ctx->adj_kernel = kernel;
     return DUGKS_OK;
 }
 

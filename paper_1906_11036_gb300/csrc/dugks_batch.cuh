@@ -4,12 +4,13 @@
 // Every instance is cut into tiles (30-column strip x row segment), the same
 // unit the single-instance fused step gives one warp.  A launch holds as many
 // one-warp CTAs as fit on the GPU; each warp takes tiles from a global
-// counter (largest instances first) and runs the single-precision
-// velocity-pair row routine on them, carrying its TMA stage ring from one
-// tile to the next.  Instances step in lockstep, so one parity selects the
+// counter (largest instances first) and runs the single-precision row
+// routine of the single-instance step (sv_rows) on them, carrying its TMA
+// stage ring from one tile to the next, so every instance's result is the
+// single-instance step's bit for bit.  Instances step in lockstep, so one parity selects the
 // source buffer of every instance.
 #pragma once
-#include "dugks_kernels.cuh"
+#include "dugks_step_vp.cuh"
 
 namespace dugks {
 
@@ -18,6 +19,7 @@ struct BatchInst {
     CUtensorMap tmap[2];          // 3-D descriptors of the instance's two ftilde buffers
     StepArgs<float, NC> args[2];  // args[p] reads buffer p and writes buffer 1 - p
     ConstsP<NC> k;
+    const RowY* rw;  // per-row y metrics of the instance
     int seg_rows, nstrips, nseg, tile_begin;
 };
 
@@ -55,8 +57,8 @@ __global__ void __launch_bounds__(32, DUGKS_BATCH_MIN_WARPS)
         const int y0 = seg * I.seg_rows;
         const int y1 = min(y0 + I.seg_rows, a.ny);
         const bool edge = xw - 1 < 0 || xw + L::WI >= a.nx;
-        if (edge) vp_rows<NC, true>(&I.tmap[parity], a, I.k, smem, bars, S, lane, xw, y0, y1, ring);
-        else vp_rows<NC, false>(&I.tmap[parity], a, I.k, smem, bars, S, lane, xw, y0, y1, ring);
+        const bool yg = !a.yper && (y0 == 0 || y1 == a.ny);
+        sv_rows<NC>(&I.tmap[parity], a, I.k, I.rw, smem, bars, S, lane, xw, y0, y1, edge, yg, ring);
     }
 }
 

@@ -103,6 +103,7 @@ def library():
         L.dugks_set_stream.argtypes = [vp, vp]
         L.dugks_sync.argtypes = [vp]
         L.dugks_wait_timeout_check.argtypes = [vp, ctypes.c_int]
+        L.dugks_set_adjoint_kernel.argtypes = [vp, ctypes.c_int]
         L.dugks_info.argtypes = [vp, P(Info)]
         L.dugks_adjoint_step.argtypes = [vp, vp, vp, vp, vp]
         L.dugks_set_source.argtypes = [vp, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int), vp, ctypes.c_double]
@@ -330,6 +331,12 @@ class Solver:
     def wait_timeout_check(self, limit_us: int = 2000):
         """Let one bounded device wait expire on purpose (no fault): the next sync raises DUGKS_ERR_TIMEOUT."""
         self._check(self.L.dugks_wait_timeout_check(self.h, int(limit_us)), "dugks_wait_timeout_check")
+
+    ADJ_KERNELS = {"auto": 0, "tiled": 1, "rows": 2}
+
+    def set_adjoint_kernel(self, kind: str):
+        """Which kernel runs an FP32 adjoint step: "auto", "tiled" or "rows" (cross-check hook)."""
+        self._check(self.L.dugks_set_adjoint_kernel(self.h, self.ADJ_KERNELS[kind]), "dugks_set_adjoint_kernel")
 
     def adjoint_step(self, f, mu, dj_dalpha=None):
         """lam = (d f^{n+1}/d f^n)^T mu at state f (CUDA tensors [9, ny, nx]); the

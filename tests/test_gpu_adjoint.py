@@ -27,10 +27,12 @@ def _gpu():
     torch.cuda.set_device(0)
 
 
-def _solver(p, prec):
+def _solver(p, prec, adj="auto"):
     from paper_1906_11036_gb300.dugks import Solver
 
-    return Solver(p, precision=prec)
+    s = Solver(p, precision=prec)
+    s.set_adjoint_kernel(adj)
+    return s
 
 
 def _mixed(xwall, ywall, nx, ny):
@@ -64,16 +66,16 @@ def _rel(a, b):
 
 @pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("name", list(CASES))
-def test_adjoint_step_matches_oracle(name, prec, monkeypatch):
-    if name.startswith("periodic_"):
-        monkeypatch.setenv("DUGKS_ADJ_ROWS", "1")  # the row-marching FP32 adjoint, whatever the size
+def test_adjoint_step_matches_oracle(name, prec):
+    # periodic cases: the row-marching FP32 adjoint, whatever the size
+    adj = "rows" if name.startswith("periodic_") else "auto"
     p = CASES[name]()
     rng = np.random.default_rng(len(name))
     o = Oracle(p)
     f = o.init(1.0 + 0.2 * rng.standard_normal((p.ny, p.nx))) + 0.01 * rng.standard_normal((9, p.ny, p.nx))
     mu = rng.standard_normal(f.shape)
     lam_ref, da_ref = o.adjoint_step(f, mu)
-    s = _solver(p, prec)
+    s = _solver(p, prec, adj)
     dt = s.dtype
     lam, da = s.adjoint_step(torch.tensor(f, dtype=dt, device="cuda"), torch.tensor(mu, dtype=dt, device="cuda"))
     lam = lam.double().cpu().numpy()
@@ -84,10 +86,10 @@ def test_adjoint_step_matches_oracle(name, prec, monkeypatch):
     assert abs(da - da_ref) <= tol * 10 * max(abs(da_ref), 1e-12)
 
 
-def test_row_marching_and_tiled_fp32_adjoints_agree(monkeypatch):
+def test_row_marching_and_tiled_fp32_adjoints_agree():
     """On a periodic grid the FP32 adjoint step runs as a row march; the tiled
-    kernel (DUGKS_ADJ_ROWS=0) computes the same quantities: they agree to FP32
-    rounding, and both match the FP64 oracle."""
+    kernel computes the same quantities: they agree to FP32 rounding, and both
+    match the FP64 oracle."""
     p = I.burgers(256, 200)[0]
     rng = np.random.default_rng(3)
     o = Oracle(p)
@@ -95,9 +97,8 @@ def test_row_marching_and_tiled_fp32_adjoints_agree(monkeypatch):
     mu = rng.standard_normal(f.shape)
     lam_ref, da_ref = o.adjoint_step(f, mu)
     out = []
-    for rows in ("1", "0"):
-        monkeypatch.setenv("DUGKS_ADJ_ROWS", rows)
-        s = _solver(p, 32)
+    for kind in ("rows", "tiled"):
+        s = _solver(p, 32, kind)
         lam, da = s.adjoint_step(torch.tensor(f, dtype=torch.float32, device="cuda"),
                                  torch.tensor(mu, dtype=torch.float32, device="cuda"))
         out.append((lam.double().cpu().numpy(), float(da.item())))
@@ -107,16 +108,16 @@ def test_row_marching_and_tiled_fp32_adjoints_agree(monkeypatch):
     assert _rel(lr, lam_ref) <= 2e-5 and abs(dr - da_ref) <= 2e-4 * abs(da_ref)
 
 
-@pytest.mark.parametrize("prec,rows", [(64, "0"), (32, "0"), (32, "1")])
-def test_checkpointed_gradient_matches_oracle(prec, rows, monkeypatch):
-    monkeypatch.setenv("DUGKS_ADJ_ROWS", rows)  # FP32: the tiled and the row-marching adjoint
+@pytest.mark.parametrize("prec,kind", [(64, "tiled"), (32, "tiled"), (32, "rows")])
+def test_checkpointed_gradient_matches_oracle(prec, kind):
+    # FP32: the tiled and the row-marching adjoint
     p, phi0 = I.burgers(48, 40, steps=60)
     xc, yc = p.centres()
     area = np.outer(np.diff(p.yf), np.diff(p.xf))
     target = I.burgers_phi0(xc, yc, seed=5)
     gref, daref, phiN_ref = Oracle(p).gradient(phi0, p.steps, lambda phiN: area * (phiN - target), threads=8,
                                                checkpoint_every=20)
-    s = _solver(p, prec)
+    s = _solver(p, prec, kind)
     dt = s.dtype
     s.init_phi(torch.tensor(phi0, dtype=dt, device="cuda"))
     s.step(p.steps)
