@@ -38,7 +38,8 @@ typedef struct dugks_ctx dugks_ctx; /* opaque, library-owned */
 typedef enum {
     DUGKS_OK = 0,
     DUGKS_ERR_ARG = 1,         /* null pointer, bad size, bad enum value */
-    DUGKS_ERR_CONFIG = 2,      /* physically invalid setup (CFL >= 1, alpha <= 0, faces not increasing) */
+    DUGKS_ERR_CONFIG = 2,      /* physically invalid setup (CFL >= 1, alpha <= 0, faces not increasing,
+                                  negative initial equilibrium) */
     DUGKS_ERR_CUDA = 3,        /* a CUDA runtime or driver call failed */
     DUGKS_ERR_NONFINITE = 4,   /* NaN or Inf detected in phi */
     DUGKS_ERR_UNSUPPORTED = 5, /* valid request that the library does not implement */
@@ -62,7 +63,11 @@ enum {
  * midpoints.  bc[] per wall W, E, S, N: DUGKS_BC_PERIODIC (must be set on both
  * walls of a direction) or DUGKS_BC_DIRICHLET with phi = bc_value[] on the
  * wall, imposed by a mirrored ghost cell with non-equilibrium extrapolation
- * (Section 4 opening; reading recorded in the design notes). */
+ * (Section 4 opening names the scheme without defining it): the ghost sits at
+ * the mirror image x_g = 2 x_w - x_1 of the first interior centre x_1, takes
+ * phi_g = 2 phi_w - phi_1 and carries the interior cell's non-equilibrium part,
+ * fbar+_g = feq(phi_g) + (fbar+_1 - feq(phi_1)); at the wall face the tangential
+ * slope is the interior cell's alone, so corner ghosts are never used. */
 typedef struct {
     int nx, ny;
     const double *xf;
@@ -127,6 +132,20 @@ typedef struct {
 dugks_status dugks_check_config(const dugks_mesh *mesh, const dugks_vset *vset,
                                 const dugks_coef *coef, double dt);
 
+/* Positivity of the equilibrium (Eq. 2.3) for phi in [phi_min, phi_max] (host
+ * only, no CUDA call; 4097 samples of phi refined by golden-section search).
+ * The equilibrium of Eq. 2.3 turns negative for large |B|/c (e.g. B =
+ * (phi^2/2)(1, 1) with c = 1 and phi near 1: min f^eq = -0.24) and the scheme
+ * is then not usable.  Rule: DUGKS_ERR_CONFIG if at some phi the smallest of
+ * the nine f^eq_i(phi) is negative by more than 1e-3 of the largest |f^eq_i(phi)|
+ * at the same phi (a marginal negativity is accepted: with D = phi^2 the
+ * diagonal equilibria vanish at phi = 1/2 up to the small advective term).
+ * *feq_min_out (nullable) receives the smallest f^eq_i(phi) itself.  Also
+ * DUGKS_ERR_CONFIG for a non-finite coefficient, DUGKS_ERR_ARG for null
+ * pointers, bad counts or phi_min > phi_max. */
+dugks_status dugks_check_feq(const dugks_vset *vset, const dugks_coef *coef, double phi_min, double phi_max,
+                             double *feq_min_out);
+
 /* Create a context (Section 2, one time step of size dt per dugks_step).
  * Copies mesh and coefficients, precomputes per-row and per-column metrics
  * and the equilibrium polynomials, and allocates two ftilde buffers on the
@@ -177,7 +196,8 @@ dugks_status dugks_load_state(dugks_ctx *ctx, const void *f_dev_in);
 dugks_status dugks_set_stream(dugks_ctx *ctx, void *stream);
 
 /* Synchronise the stream and report a pending device-side error flag
- * (DUGKS_ERR_TIMEOUT) or a CUDA error. */
+ * (DUGKS_ERR_TIMEOUT: a bounded wait expired; DUGKS_ERR_CONFIG: dugks_init_phi
+ * met a negative equilibrium) or a CUDA error. */
 dugks_status dugks_sync(dugks_ctx *ctx);
 
 /* Failure-path check without a fault: launches one warp that waits at most
@@ -216,16 +236,29 @@ dugks_status dugks_set_source(dugks_ctx *ctx, int nterms, const double *rate, co
 /* ---- adjoint (gradients) -------------------------------------------------
  * Discrete adjoint of the step of Section 2 (reverse mode of Eqs. 2.9,
  * 2.12, 2.13, 2.19-2.22, 2.26 and of the mirrored NEE ghosts), for
- * gradients of a misfit J(phi^N) with respect to phi^0 and alpha (alpha
- * enters through lambda = alpha / c_s^2, Section 3).
+ * gradients of a misfit J(phi^N) with respect to phi^0, alpha (alpha
+ * enters through lambda = alpha / c_s^2, Section 3) and the velocity u of
+ * the convection coefficients B = u b(phi), C = u u int b'^2 dphi (Remark 3),
+ * which enter every f^eq of Eq. 2.3: cells, faces, ghosts and f^0.
  *
  * dugks_adjoint_step: lam = (d ftilde^{n+1} / d ftilde^n)^T mu at the forward
- * state f = ftilde^n, and *dj_dalpha_dev += mu . d ftilde^{n+1} / d alpha.
- * f_dev, mu_dev, lam_dev: device, [9][ny][nx] contiguous, precision's type
- * (lam_dev must not alias f_dev or mu_dev); dj_dalpha_dev: device double,
- * accumulated in a fixed order (deterministic).  Asynchronous. */
+ * state f = ftilde^n, *dj_dalpha_dev += mu . d ftilde^{n+1} / d alpha and,
+ * when dj_du_dev is not NULL, dj_du_dev[a] += mu . d ftilde^{n+1} / d u_a
+ * (a = x, y).  f_dev, mu_dev, lam_dev: device, [9][ny][nx] contiguous,
+ * precision's type (lam_dev must not alias f_dev or mu_dev); dj_dalpha_dev:
+ * device double; dj_du_dev: device, 2 doubles, or NULL; both accumulated in
+ * a fixed order (deterministic).  Asynchronous. */
 dugks_status dugks_adjoint_step(dugks_ctx *ctx, const void *f_dev, const void *mu_dev, void *lam_dev,
-                                double *dj_dalpha_dev);
+                                double *dj_dalpha_dev, double *dj_du_dev);
+
+/* on = 1: every later initialisation tests the equilibrium of its phi0 by the
+ * rule of dugks_check_feq.  dugks_init_phi_host applies it over the range of
+ * its host phi0 and returns DUGKS_ERR_CONFIG before touching the state;
+ * dugks_init_phi (device phi0) applies it per cell on the device, and the next
+ * dugks_sync returns DUGKS_ERR_CONFIG if a cell failed.  Off by default: the
+ * paper's own Example 4.1 takes phi (and with it f^eq) negative, which the
+ * linear problem allows.  DUGKS_ERR_ARG for a null ctx or on outside 0..1. */
+dugks_status dugks_set_feq_check(dugks_ctx *ctx, int on);
 
 /* Which kernel runs an FP32 adjoint step (a cross-check hook; results agree to
  * FP32 rounding).  DUGKS_ADJ_AUTO (the default): the row-marching kernel on
@@ -237,15 +270,18 @@ enum { DUGKS_ADJ_AUTO = 0, DUGKS_ADJ_TILED = 1, DUGKS_ADJ_ROWS = 2 };
 dugks_status dugks_set_adjoint_kernel(dugks_ctx *ctx, int kernel);
 
 /* Gradient of J through nsteps steps from phi0: given grad_phiN = dJ/dphi^N
- * (device, [ny][nx]), writes dJ/dphi^0 into grad_phi0_dev (device [ny][nx])
- * and dJ/dalpha into *grad_alpha_out (host; may be NULL).  Runs the forward
+ * (device, [ny][nx]), writes dJ/dphi^0 into grad_phi0_dev (device [ny][nx]),
+ * dJ/dalpha into *grad_alpha_out (host; may be NULL) and dJ/du into
+ * grad_u_out[0..1] (host; may be NULL: the u-derivative is then not formed,
+ * and the sweep reads less).  Runs the forward
  * sweep keeping one state every checkpoint_every steps, then for each segment
  * from the last recomputes its states and steps the adjoint back through it
  * (memory: ceil(nsteps/K) + K + 2 states of 9 nx ny elements, allocated for
  * the call and freed).  Synchronises the stream.  The context's own state is
  * left at an intermediate step: initialise it again before stepping. */
 dugks_status dugks_adjoint(dugks_ctx *ctx, const void *phi0_dev, long long nsteps, int checkpoint_every,
-                           const void *grad_phiN_dev, void *grad_phi0_dev, double *grad_alpha_out);
+                           const void *grad_phiN_dev, void *grad_phi0_dev, double *grad_alpha_out,
+                           double *grad_u_out);
 
 /* ---- batched instances ---------------------------------------------------
  * Many independent instances of the step of Section 2 (each with its own
@@ -300,13 +336,17 @@ const char *dugks_batch_last_error(const dugks_batch *b);
  *
  * Asynchronous on `stream`.  Returns DUGKS_ERR_ARG for null pointers, a bad
  * precision or nx, ny < 1, and DUGKS_ERR_UNSUPPORTED when nx*ny exceeds
- * DUGKS_NOALLOC_MAX_CELLS (one partial sum per 256 cells).  The first call on
- * a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  All
- * calls share the one array: calls that overlap on the GPU (concurrent
- * streams, or several host threads) race and must be serialised by the
- * caller.  Every partial sum is overwritten before it is read, so nothing
- * from an earlier call leaks into a later one. */
+ * DUGKS_NOALLOC_MAX_CELLS (one partial sum per 256 cells), DUGKS_ERR_CUDA if
+ * a launch of this call fails (an error left pending by earlier work of the
+ * caller is neither cleared nor reported).  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current and keeps it for the process; make that first call before any
+ * stream capture, and do not call the entry point again on a device after
+ * cudaDeviceReset there (the kept address would belong to the destroyed
+ * context).  All calls share the one array: calls that overlap on the GPU
+ * (concurrent streams, or several host threads) race and must be serialised
+ * by the caller.  Every partial sum is overwritten before it is read, so
+ * nothing from an earlier call leaks into a later one. */
 #define DUGKS_NOALLOC_MAX_BLOCKS 65536
 #define DUGKS_NOALLOC_MAX_CELLS (256LL * DUGKS_NOALLOC_MAX_BLOCKS)
 dugks_status dugks_phi_mass_noalloc(const void *f_dev, int precision, int nx, int ny, const double *dx_dev,

@@ -98,7 +98,8 @@ def lib():
         L.oracle_run.argtypes = [P, dp, ctypes.c_long, ctypes.c_int]
         L.oracle_max_threads.restype = ctypes.c_int
         L.oracle_equilibrium_deriv.argtypes = [P, ctypes.c_double, dp]
-        L.oracle_adjoint_step.argtypes = [P, dp, dp, dp, dp]
+        L.oracle_adjoint_step.argtypes = [P, dp, dp, dp, dp, dp]
+        L.oracle_equilibrium_du.argtypes = [P, ctypes.c_double, dp, dp]
         L.oracle_step_src.argtypes = [P, dp, dp, ctypes.c_double, dp, dp, dp, dp, ctypes.c_int]
         P3 = ctypes.POINTER(_Problem3)
         L.oracle3_equilibrium.argtypes = [P3, ctypes.c_double, dp]
@@ -185,6 +186,12 @@ class Oracle:
         self.L.oracle_equilibrium_deriv(ctypes.byref(self.s), float(phi), _ptr(out))
         return out
 
+    def equilibrium_du(self, phi: float) -> np.ndarray:
+        """d feq_i / d u_a as a [2, 9] array (B = u b(phi), C = u u int b'^2)."""
+        dx, dy = np.zeros(Q), np.zeros(Q)
+        self.L.oracle_equilibrium_du(ctypes.byref(self.s), float(phi), _ptr(dx), _ptr(dy))
+        return np.stack([dx, dy])
+
     def cell_transforms(self, ft, feq):
         ft = np.ascontiguousarray(ft, dtype=np.float64)
         feq = np.ascontiguousarray(feq, dtype=np.float64)
@@ -251,21 +258,30 @@ class Oracle:
 
     def adjoint_step(self, f: np.ndarray, mu: np.ndarray):
         """(lam, dJ/dalpha) for one step at state f given mu = dJ/d f^{n+1}."""
+        lam, da, _ = self.adjoint_step_full(f, mu)
+        return lam, da
+
+    def adjoint_step_full(self, f: np.ndarray, mu: np.ndarray):
+        """(lam, dJ/dalpha, dJ/du) for one step at state f given mu = dJ/d f^{n+1};
+        dJ/du is the explicit dependence of the step on u of B = u b(phi)."""
         f = np.ascontiguousarray(f, dtype=np.float64)
         mu = np.ascontiguousarray(mu, dtype=np.float64)
         lam = np.empty_like(f)
         da = ctypes.c_double(0.0)
+        du = np.zeros(2)
         rc = self.L.oracle_adjoint_step(ctypes.byref(self.s), _ptr(f), _ptr(mu), _ptr(lam),
-                                        ctypes.cast(ctypes.pointer(da), ctypes.POINTER(ctypes.c_double)))
+                                        ctypes.cast(ctypes.pointer(da), ctypes.POINTER(ctypes.c_double)), _ptr(du))
         if rc != 0:
             raise RuntimeError(f"oracle_adjoint_step failed ({rc})")
-        return lam, da.value
+        return lam, da.value, du
 
-    def gradient(self, phi0: np.ndarray, nsteps: int, dj_dphiN, threads: int = 0, checkpoint_every: int = 0):
+    def gradient(self, phi0: np.ndarray, nsteps: int, dj_dphiN, threads: int = 0, checkpoint_every: int = 0,
+                 with_u: bool = False):
         """Reverse-mode gradient of J(phi^N) with respect to phi0 and alpha.
         dj_dphiN(phi^N) returns dJ/dphi^N.  With checkpoint_every = K > 0 only
         every K-th state is kept and each segment is recomputed.  Returns
-        (dJ/dphi0, dJ/dalpha, phi^N)."""
+        (dJ/dphi0, dJ/dalpha, phi^N), or with with_u (dJ/dphi0, dJ/dalpha,
+        dJ/du, phi^N) where u is the velocity of B = u b(phi)."""
         K = nsteps if checkpoint_every <= 0 else checkpoint_every
         K = max(1, min(K, max(nsteps, 1)))
         ckpt = [self.init(phi0)]
@@ -277,19 +293,25 @@ class Oracle:
         g = np.asarray(dj_dphiN(phiN), dtype=np.float64)
         lam = np.broadcast_to(g, (Q,) + g.shape).copy()   # phi = sum_i f_i
         dalpha = 0.0
+        du = np.zeros(2)
         for si in range(len(ckpt) - 2, -1, -1):
             ns = min(K, nsteps - si * K)
             states = [ckpt[si]]
             for _ in range(ns - 1):
                 states.append(self.step(states[-1], threads))
             for n in range(ns - 1, -1, -1):
-                lam, da = self.adjoint_step(states[n], lam)
+                lam, da, d = self.adjoint_step_full(states[n], lam)
                 dalpha += da
-        # f^0 = feq(phi0): dJ/dphi0 = sum_i feq_i'(phi0) lam_i
+                du += d
+        # f^0 = feq(phi0): dJ/dphi0 = sum_i feq_i'(phi0) lam_i, and f^0 depends on u too
         gphi = np.zeros(phi0.shape, dtype=np.float64)
         for k in range(self.ny):
             for j in range(self.nx):
                 gphi[k, j] = float(self.equilibrium_deriv(phi0[k, j]) @ lam[:, k, j])
+                if with_u:
+                    du += self.equilibrium_du(phi0[k, j]) @ lam[:, k, j]
+        if with_u:
+            return gphi, dalpha, du, phiN
         return gphi, dalpha, phiN
 
     def phi(self, f: np.ndarray) -> np.ndarray:

@@ -203,6 +203,21 @@ void oracle_equilibrium_deriv(const oracle_problem *p, double phi, double *dfeq)
     }
 }
 
+/* d feq_i / d u_a, a = x, y, for B = u b(phi) and C = u u int_0^phi b'^2 (Eq. 2.3, Remark 3):
+ * c_i.B / c_s^2 gives w_i c_ia b / c_s^2 and C:(c_i c_i - c_s^2 I) / (2 c_s^4) gives
+ * w_i Cint (c_ia (c_i.u) - c_s^2 u_a) / c_s^4 (the derivative of u u is symmetric). */
+void oracle_equilibrium_du(const oracle_problem *p, double phi, double *dfx, double *dfy) {
+    const double cs2 = p->c * p->c / 3.0;
+    const double bv = poly(p->nb, p->b, phi);
+    const double cv = p->c_zero ? 0.0 : aux_moment_scalar(p, phi);
+    for (int i = 0; i < Q; i++) {
+        const double ci[2] = {CX[i] * p->c, CY[i] * p->c};
+        const double cu = ci[0] * p->u[0] + ci[1] * p->u[1];
+        dfx[i] = WT[i] * (ci[0] * bv / cs2 + cv * (ci[0] * cu - cs2 * p->u[0]) / (cs2 * cs2));
+        dfy[i] = WT[i] * (ci[1] * bv / cs2 + cv * (ci[1] * cu - cs2 * p->u[1]) / (cs2 * cs2));
+    }
+}
+
 static double relax_time(const oracle_problem *p) { return p->alpha / (p->c * p->c / 3.0); }
 
 /* Eqs. 2.21 and 2.13 for one cell: fbar^+ and ftilde^+ from ftilde and feq. */
@@ -657,13 +672,15 @@ int oracle_max_threads(void) {
  * Given f = ftilde^n and mu = dJ/d ftilde^{n+1}, returns lam = dJ/d ftilde^n
  * = (d step / d f)^T mu, and adds to *dj_dalpha the explicit dependence of
  * the step on alpha (through lambda = alpha / c_s^2 in the weights of Eqs.
- * 2.13, 2.21 and 2.22) contracted with mu.  The forward quantities are
+ * 2.13, 2.21 and 2.22) contracted with mu, and to dj_du[0..1] (nullable) the
+ * explicit dependence on u of B = u b(phi) (through every equilibrium the step
+ * evaluates: cells, faces and ghosts, oracle_equilibrium_du).  The forward quantities are
  * recomputed exactly as in oracle_step; every stage is then transposed in
  * reverse order: cell update, face flux and Eq. 2.22, reconstruction
  * (Eqs. 2.19, 2.20, 2.26), ghost cells, Eqs. 2.21 / 2.13, phi = sum f.
  */
 int oracle_adjoint_step(const oracle_problem *p, const double *f_in, const double *mu, double *lam,
-                        double *dj_dalpha) {
+                        double *dj_dalpha, double *dj_du) {
     if (!valid(p) || p->nsrc > 0) return -2; /* the adjoint covers the step without sources */
     workspace ws, *w = &ws;
     if (ws_alloc(w, p) != 0) { ws_free(w); return -1; }
@@ -679,7 +696,8 @@ int oracle_adjoint_step(const oracle_problem *p, const double *f_in, const doubl
     const double da_tp = 4.0 * dt / (den1 * den1), db_tp = -4.0 * dt / (den1 * den1);
     const double da_f = 2.0 * h / (den2 * den2), db_f = -2.0 * h / (den2 * den2);
     const int xper = p->bc[WALL_W] == BC_PERIODIC, yper = p->bc[WALL_S] == BC_PERIODIC;
-    double djdl = 0.0;
+    double djdl = 0.0, djdu[2] = {0.0, 0.0};
+    double dux[Q], duy[Q];
 
     /* forward recomputation: phi, feq, fbar^+ with halo */
     for (int k = 0; k < ny; k++)
@@ -734,6 +752,11 @@ int oracle_adjoint_step(const oracle_problem *p, const double *f_in, const doubl
                 djdl += g * (da_f * fbar[i] + db_f * feqb[i]);
                 s += g * b_f * dfeqb[i];
             }
+            oracle_equilibrium_du(p, phib, dux, duy);
+            for (int i = 0; i < Q; i++) {
+                djdu[0] += fbarf[i] * b_f * dux[i];
+                djdu[1] += fbarf[i] * b_f * duy[i];
+            }
             for (int i = 0; i < Q; i++) {
                 const double fbb = a_f * fbarf[i] + s;  /* dJ/d fbar_i (Eq. 2.22 and phi_b = sum fbar) */
                 const double cl = 1.0 - (xb - w->xc[jl]) / dxc + h * CX[i] * p->c / dxc;
@@ -785,6 +808,11 @@ int oracle_adjoint_step(const oracle_problem *p, const double *f_in, const doubl
                 djdl += g * (da_f * fbar[i] + db_f * feqb[i]);
                 s += g * b_f * dfeqb[i];
             }
+            oracle_equilibrium_du(p, phib, dux, duy);
+            for (int i = 0; i < Q; i++) {
+                djdu[0] += fbarf[i] * b_f * dux[i];
+                djdu[1] += fbarf[i] * b_f * duy[i];
+            }
             for (int i = 0; i < Q; i++) {
                 const double fbb = a_f * fbarf[i] + s;
                 const double cl = 1.0 - (yb - w->yc[kl]) / dyc + h * CY[i] * p->c / dyc;
@@ -826,13 +854,17 @@ int oracle_adjoint_step(const oracle_problem *p, const double *f_in, const doubl
     do {                                                                                         \
         const size_t c1 = (size_t)((ki) - 1) * nx + (size_t)((ji) - 1);                          \
         const double phi1 = w->phi[c1], phig = 2.0 * (bv) - phi1;                                \
-        double d1[Q], dg[Q], acc = 0.0;                                                          \
+        double d1[Q], dg[Q], u1x[Q], u1y[Q], ugx[Q], ugy[Q], acc = 0.0;                          \
         oracle_equilibrium_deriv(p, phi1, d1);                                                   \
         oracle_equilibrium_deriv(p, phig, dg);                                                   \
+        oracle_equilibrium_du(p, phi1, u1x, u1y);                                                \
+        oracle_equilibrium_du(p, phig, ugx, ugy);                                                \
         for (int i = 0; i < Q; i++) {                                                            \
             const double g = PB(i, (kg), (jg));                                                  \
             PB(i, (ki), (ji)) += g;                                                              \
             acc -= g * (dg[i] + d1[i]);                                                          \
+            djdu[0] += g * (ugx[i] - u1x[i]);                                                    \
+            djdu[1] += g * (ugy[i] - u1y[i]);                                                    \
             PB(i, (kg), (jg)) = 0.0;                                                             \
         }                                                                                        \
         phib_extra[c1] += acc;                                                                   \
@@ -854,9 +886,12 @@ int oracle_adjoint_step(const oracle_problem *p, const double *f_in, const doubl
             const size_t c = (size_t)k * nx + j;
             double dfe[Q], acc = phib_extra[c];
             oracle_equilibrium_deriv(p, w->phi[c], dfe);
+            oracle_equilibrium_du(p, w->phi[c], dux, duy);
             for (int i = 0; i < Q; i++) {
                 const double pb = PB(i, k + 1, j + 1), tb = mu[i * n + c];
                 acc += (b_bp * pb + b_tp * tb) * dfe[i];
+                djdu[0] += (b_bp * pb + b_tp * tb) * dux[i];
+                djdu[1] += (b_bp * pb + b_tp * tb) * duy[i];
                 djdl += pb * (da_bp * f_in[i * n + c] + db_bp * w->feq[i * n + c]) +
                         tb * (da_tp * f_in[i * n + c] + db_tp * w->feq[i * n + c]);
             }
@@ -864,6 +899,10 @@ int oracle_adjoint_step(const oracle_problem *p, const double *f_in, const doubl
         }
 #undef PB
     if (dj_dalpha) *dj_dalpha += djdl / (p->c * p->c / 3.0);
+    if (dj_du) {
+        dj_du[0] += djdu[0];
+        dj_du[1] += djdu[1];
+    }
     free(phib_extra);
     free(Pb);
     ws_free(w);

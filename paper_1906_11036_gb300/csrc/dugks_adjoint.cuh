@@ -1,11 +1,15 @@
 // dugks_adjoint.cuh -- discrete adjoint of one DUGKS step (reverse mode of
 // the step of Section 2 of arXiv:1906.11036), for gradients of a misfit of
-// phi^N with respect to phi^0 and the diffusion coefficient alpha.
+// phi^N with respect to phi^0, the diffusion coefficient alpha and the
+// velocity u of B = u b(phi).
 //
-// Given the forward state f = ftilde^n and mu = dJ/d ftilde^{n+1}, the two
-// kernels return lam = dJ/d ftilde^n and the explicit alpha-derivative of the
-// step contracted with mu (alpha enters through lambda = alpha / c_s^2 in the
-// weights of Eqs. 2.13, 2.21 and 2.22).
+// Given the forward state f = ftilde^n and mu = dJ/d ftilde^{n+1}, the
+// kernels return lam = dJ/d ftilde^n and the explicit alpha- and
+// u-derivatives of the step contracted with mu (alpha enters through
+// lambda = alpha / c_s^2 in the weights of Eqs. 2.13, 2.21 and 2.22; u through
+// every equilibrium the step evaluates, Eq. 2.3 with C = u u int b'^2:
+// d feq_i / d u_a = A_ia b(phi) + B_ia Cint(phi), A_ia = 3 w_i e_ia / c,
+// B_ia = w_i (9 e_ia (e_i.u) - 3 u_a) / c^2, e_i the unit direction).
 //
 //   adj_tile_kernel, per tile of cells: (P) recomputes the forward P = fbar^+
 //     of its cells and halo (Eq. 2.21, mirrored ghosts); (faces) the forward face
@@ -31,6 +35,8 @@ struct AdjConsts {
     T dfeq[Q][NC];  // d feq_i / d phi (i > 0); the rest velocity follows the zeroth moment
     T a_bp, b_bp, a_tp, b_tp, a_f, b_f;
     T da_bp, db_bp, da_tp, db_tp, da_f, db_f;  // derivatives of the weights with respect to lambda
+    T bpoly[NC], cpoly[NC];                   // b(phi) and Cint(phi) = int_0^phi b'^2 (0 with C = 0)
+    T Au[2][Q], Bu[2][Q];                     // d feq_i / d u_a = Au[a][i] b(phi) + Bu[a][i] Cint(phi)
 };
 
 template <typename T>
@@ -40,8 +46,11 @@ struct AdjArgs {
     T* lam;            // out: dJ/d ftilde^n
     T* Ax;             // x-face adjoints [Q][ny][nx+1]
     T* Ay;             // y-face adjoints [Q][ny+1][nx]
-    double* partial;   // per-block partial sums of dJ/dlambda (faces, cells, wall cells)
+    double* partial;   // per-block partial sums: dJ/dlambda at [slot], dJ/du_x at [pstride + slot],
+                       // dJ/du_y at [2 pstride + slot] (faces, cells, wall cells)
+    long long pstride;
     int accumulate;    // 1: add to the partials (a reverse sweep sums them once at its end); 0: overwrite
+    int want_u;        // 0: the u-derivative is not requested (its partials receive zeros)
 };
 
 // Neighbour index along one direction, for i in [-1, n]: the interior cell
@@ -80,17 +89,55 @@ __device__ __forceinline__ T dfeq_i(const AdjConsts<T, NC>& ka, int i, T phi) {
     return v;
 }
 
-template <typename T>
-__device__ __forceinline__ void block_partial(double v, double* out, int accumulate) {
+// polynomial sum_m c[m] x^m by Horner's rule
+template <typename T, int NC>
+__device__ __forceinline__ T poly_nc(const T (&c)[NC], T x) {
+    T s = c[NC - 1];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __shared__ double ws[32];
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    for (int m = NC - 2; m >= 0; --m) s = fma(s, x, c[m]);
+    return s;
+}
+
+// sum_i w_i d feq_i / d u_a at phi for a = x, y, over the velocities in `mask`
+// (bit i: velocity i), added to du[0], du[1] in double
+template <typename T, int NC>
+__device__ __forceinline__ void add_du(const AdjConsts<T, NC>& ka, T phi, const T (&w)[Q], unsigned mask,
+                                       double (&du)[2]) {
+    const T bv = poly_nc<T, NC>(ka.bpoly, phi), cv = poly_nc<T, NC>(ka.cpoly, phi);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        T sa = T(0), sb = T(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            if (mask & (1u << i)) {
+                sa = fma(w[i], ka.Au[a][i], sa);
+                sb = fma(w[i], ka.Bu[a][i], sb);
+            }
+        du[a] += double(fma(bv, sa, cv * sb));
+    }
+}
+__host__ __device__ constexpr unsigned xmask() { return (1u << 1) | (1u << 3) | (1u << 5) | (1u << 6) | (1u << 7) | (1u << 8); }
+__host__ __device__ constexpr unsigned ymask() { return (1u << 2) | (1u << 4) | (1u << 5) | (1u << 6) | (1u << 7) | (1u << 8); }
+constexpr unsigned kAllQ = (1u << Q) - 1u;
+
+// The block's sums of v[0..2] (dJ/dlambda, dJ/du_x, dJ/du_y) into out[0], out[stride],
+// out[2 stride] (one slot per block: no race), added to the slots or overwriting them.
+__device__ __forceinline__ void block_partial3(const double (&v)[3], double* out, long long stride, int accumulate) {
+    __shared__ double ws[3][32];
+    double x[3] = {v[0], v[1], v[2]};
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x[q] += __shfl_xor_sync(0xffffffffu, x[q], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) ws[q][threadIdx.x >> 5] = x[q];
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 3) {
         double s = 0.0;
-        for (int w = 0; w < int(blockDim.x >> 5); ++w) s += ws[w];
-        *out = accumulate ? *out + s : s;  // each block owns its slot: no race
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) s += ws[threadIdx.x][w];
+        double* o = out + threadIdx.x * stride;
+        *o = accumulate ? *o + s : s;
     }
 }
 
@@ -112,7 +159,7 @@ __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs<T, NC> a, 
     const int nr = max(0, r1 - r0);
     const int ncc = a.xper ? 0 : (nx > 1 ? 2 : 1) * nr;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    double djdl = 0.0;
+    double djdl = 0.0, du[2] = {0.0, 0.0};
     if (t < nrc + ncc) {
         int j, kr;
         if (t < nrc) {
@@ -146,6 +193,7 @@ __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs<T, NC> a, 
                 PG[i] += Pg[i];
                 dphibar -= Pg[i] * (dg[i] + dfe[i]);
             }
+            if (g.want_u) add_du(ka, T(2) * bv - phi, Pg, kAllQ, du);  // feq(phi_g) of the ghost
         };
         if (!a.xper && j == 0) {  // west ghost: left cell of x-face 0; its P enters G^x(0, kr)
             T Pg[Q];
@@ -199,10 +247,17 @@ __global__ void __launch_bounds__(128) adj_wall_kernel(const StepArgs<T, NC> a, 
             s += PG[i] * fma(ka.da_bp, ft[i], ka.db_bp * fe[i]);
         }
         djdl = double(s);
+        if (g.want_u) {  // - feq(phi) of every ghost and b_bp feq(phi) of Eq. 2.21 through P of the cell
+            T w[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) w[i] = (ka.b_bp - T(1)) * PG[i];
+            add_du(ka, phi, w, kAllQ, du);
+        }
 #pragma unroll
         for (int i = 0; i < Q; ++i) g.lam[i * cplane + c] += fma(ka.a_bp, PG[i], dphibar);
     }
-    block_partial<T>(djdl, g.partial + first_partial + blockIdx.x, g.accumulate);
+    const double v[3] = {djdl, du[0], du[1]};
+    block_partial3(v, g.partial + first_partial + blockIdx.x, g.pstride, g.accumulate);
 }
 
 // The face and cell parts of the adjoint step in one launch.  A CTA of TX x TY
@@ -252,7 +307,7 @@ __global__ void __launch_bounds__(TX * TY) adj_tile_kernel(const StepArgs<T, NC>
     const long long xplane = (long long)(nx + 1) * ny, yplane = (long long)nx * (ny + 1);
     const int j0 = blockIdx.x * TX, k0 = blockIdx.y * TY;
     const int tid = threadIdx.x, nthr = TX * TY;
-    double djdl = 0.0;
+    double djdl = 0.0, du[2] = {0.0, 0.0};
 
     // 1. P tile (two-cell halo) and mu tile (one-cell halo)
     for (int e = tid; e < L::PW * L::PH; e += nthr) {
@@ -349,7 +404,15 @@ __global__ void __launch_bounds__(TX * TY) adj_tile_kernel(const StepArgs<T, NC>
                 if (EX(i) != 0) sdl += gv[i] * fma(ka.da_f, fb[i], ka.db_f * fe[i]);
             }
             const bool owned = (xr >= 1 && xr <= TY && row < ny) && (xc < TX || jf == nx);
-            if (owned && !(a.xper && jf == nx)) djdl += double(sdl);  // a periodic face is counted once
+            if (owned && !(a.xper && jf == nx)) {  // a periodic face is counted once
+                djdl += double(sdl);
+                if (g.want_u) {  // Eq. 2.22: b_f feq(phi_b) of the crossing velocities
+                    T w[Q];
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) w[i] = ka.b_f * gv[i];
+                    add_du(ka, phib, w, xmask(), du);
+                }
+            }
             if (owned && write_faces) {
                 T* Ag = g.Ax + (long long)row * (nx + 1) + jf;
 #pragma unroll
@@ -409,7 +472,15 @@ __global__ void __launch_bounds__(TX * TY) adj_tile_kernel(const StepArgs<T, NC>
                 if (EY(i) != 0) sdl += gv[i] * fma(ka.da_f, fb[i], ka.db_f * fe[i]);
             }
             const bool owned = (yc >= 1 && yc <= TX && col < nx) && (yr < TY || kf == ny);
-            if (owned && !(a.yper && kf == ny)) djdl += double(sdl);
+            if (owned && !(a.yper && kf == ny)) {
+                djdl += double(sdl);
+                if (g.want_u) {
+                    T w[Q];
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) w[i] = ka.b_f * gv[i];
+                    add_du(ka, phib, w, ymask(), du);
+                }
+            }
             if (owned && write_faces) {
                 T* Ag = g.Ay + (long long)kf * nx + col;
 #pragma unroll
@@ -469,27 +540,41 @@ __global__ void __launch_bounds__(TX * TY) adj_tile_kernel(const StepArgs<T, NC>
             s += Pb[i] * fma(ka.da_bp, ft[i], ka.db_bp * fe[i]) + mu[i] * fma(ka.da_tp, ft[i], ka.db_tp * fe[i]);
         }
         djdl += double(s);
+        if (g.want_u) {  // Eqs. 2.21 and 2.13: b_bp feq(phi) in P and b_tp feq(phi) in ftilde^+
+            T w[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) w[i] = fma(ka.b_bp, Pb[i], ka.b_tp * mu[i]);
+            add_du(ka, phi, w, kAllQ, du);
+        }
 #pragma unroll
         for (int i = 0; i < Q; ++i) g.lam[i * cplane + t] = fma(ka.a_bp, Pb[i], fma(ka.a_tp, mu[i], phibar));
     }
-    block_partial<T>(djdl, g.partial + blockIdx.y * gridDim.x + blockIdx.x, g.accumulate);
+    const double v[3] = {djdl, du[0], du[1]};
+    block_partial3(v, g.partial + blockIdx.y * gridDim.x + blockIdx.x, g.pstride, g.accumulate);
 }
 
-// *dj_dalpha += (sum of the partials) / c_s^2, in a fixed order (one block of 1024).
-__global__ void __launch_bounds__(1024) adj_sum_kernel(const double* __restrict__ partial, int n, double inv_cs2,
-                                                       double* __restrict__ dj_dalpha) {
-    double acc = 0.0;
-#pragma unroll 8
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partial[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+// *dj_dalpha += (sum of the lambda partials) / c_s^2 and, if dj_du is set, dj_du[a] += (sum
+// of the u_a partials), each in a fixed order (one block of 1024 threads).
+__global__ void __launch_bounds__(1024) adj_sum_kernel(const double* __restrict__ partial, int n, long long stride,
+                                                       double inv_cs2, double* __restrict__ dj_dalpha,
+                                                       double* __restrict__ dj_du) {
     __shared__ double ws[32];
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < int(blockDim.x >> 5); ++w) s += ws[w];
-        *dj_dalpha += s * inv_cs2;
+    for (int q = dj_dalpha ? 0 : 1; q < (dj_du ? 3 : 1); ++q) {
+        const double* p = partial + q * stride;
+        double acc = 0.0;
+#pragma unroll 8
+        for (int i = threadIdx.x; i < n; i += blockDim.x) acc += p[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < int(blockDim.x >> 5); ++w) s += ws[w];
+            if (q == 0) *dj_dalpha += s * inv_cs2;
+            else dj_du[q - 1] += s;
+        }
+        __syncthreads();
     }
 }
 
@@ -503,17 +588,30 @@ __global__ void broadcast_phi_adjoint(const T* __restrict__ gphi, T* __restrict_
     }
 }
 
-// dJ/dphi0 = sum_i feq_i'(phi0) lam_i (f^0 = feq(phi0), opening of Section 4)
+// dJ/dphi0 = sum_i feq_i'(phi0) lam_i (f^0 = feq(phi0), opening of Section 4); with upart set
+// (3 gridDim.x doubles), the block's sums of sum_i lam_i d feq_i / d u_a(phi0) (f^0 depends on
+// u too) go to upart[gridDim.x + blockIdx.x] and upart[2 gridDim.x + blockIdx.x], and 0 to
+// upart[blockIdx.x].
 template <typename T, int NC>
-__global__ void init_adjoint_kernel(const T* __restrict__ phi0, const T* __restrict__ lam, T* __restrict__ gphi0,
-                                    long long n, const AdjConsts<T, NC> ka) {
+__global__ void __launch_bounds__(256) init_adjoint_kernel(const T* __restrict__ phi0, const T* __restrict__ lam,
+                                                           T* __restrict__ gphi0, long long n,
+                                                           const AdjConsts<T, NC> ka, double* __restrict__ upart) {
+    double du[2] = {0.0, 0.0};
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        T d[Q];
+        T d[Q], l[Q];
         dfeq_all(ka, phi0[c], d);
         T s = T(0);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) s = fma(d[i], lam[i * n + c], s);
+        for (int i = 0; i < Q; ++i) {
+            l[i] = lam[i * n + c];
+            s = fma(d[i], l[i], s);
+        }
         gphi0[c] = s;
+        if (upart) add_du(ka, phi0[c], l, kAllQ, du);
+    }
+    if (upart) {
+        const double v[3] = {0.0, du[0], du[1]};
+        block_partial3(v, upart + blockIdx.x, gridDim.x, 0);
     }
 }
 

@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
     float Ba[Q], Bb[Q], Bc[Q];    // adjoint of P accumulated for rows n-2, n-1, n
 #pragma unroll
     for (int i = 0; i < Q; ++i) Pm2[i] = Pm1[i] = Pn[i] = Ba[i] = Bb[i] = Bc[i] = 0.f;
-    double djdl = 0.0;
+    double djdl = 0.0, du[2] = {0.0, 0.0};
     bool failed = false;
     int t = 0;
     for (; t < R; ++t) {
@@ -148,7 +148,15 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
                 A[i] = fmaf(ka.a_f, gv[i], ka.b_f * sg);
                 if (EX(i) != 0) sdl += gv[i] * fmaf(ka.da_f, fb[i], ka.db_f * fe[i]);
             }
-            if (owner && q >= y0 && q < y1) djdl += double(sdl);
+            if (owner && q >= y0 && q < y1) {
+                djdl += double(sdl);
+                if (g.want_u) {  // Eq. 2.22: b_f feq(phi_b) of the crossing velocities
+                    float w[Q];
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) w[i] = ka.b_f * gv[i];
+                    add_du(ka, phib, w, xmask(), du);
+                }
+            }
             // scatter: normal weights into row q of this lane (L) and of the east lane (R);
             // tangential slope weights into rows q + 1 and q - 1 of both
 #pragma unroll
@@ -203,7 +211,15 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
                 A[i] = fmaf(ka.a_f, gv[i], ka.b_f * sg);
                 if (EY(i) != 0) sdl += gv[i] * fmaf(ka.da_f, fb[i], ka.db_f * fe[i]);
             }
-            if (owner && n < y1) djdl += double(sdl);
+            if (owner && n < y1) {
+                djdl += double(sdl);
+                if (g.want_u) {
+                    float w[Q];
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) w[i] = ka.b_f * gv[i];
+                    add_du(ka, phib, w, ymask(), du);
+                }
+            }
             // scatter: normal weights into rows n - 1 (L) and n (R) of this lane; x-slope weights
             // into the same rows of the lanes to the east (+) and west (-)
 #pragma unroll
@@ -237,6 +253,12 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
             }
             if (owner) {
                 djdl += double(s);
+                if (g.want_u) {  // Eqs. 2.21 and 2.13: b_bp feq(phi) in P and b_tp feq(phi) in ftilde^+
+                    float w[Q];
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) w[i] = fmaf(ka.b_bp, Ba[i], ka.b_tp * mu[i]);
+                    add_du(ka, phi, w, kAllQ, du);
+                }
                 float* out = g.lam + (long long)r * nx + j;
 #pragma unroll
                 for (int i = 0; i < Q; ++i) out[i * cplane] = fmaf(ka.a_bp, Ba[i], fmaf(ka.a_tp, mu[i], phibar));
@@ -265,7 +287,8 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
         for (int u = t; u < issued; ++u) mbar_wait_bounded(&bars[u % S], uint32_t((u / S) & 1), 100000000ull);
     }
     __syncwarp();
-    block_partial<float>(djdl, g.partial + blockIdx.y * gridDim.x + blockIdx.x, g.accumulate);
+    const double v[3] = {djdl, du[0], du[1]};
+    block_partial3(v, g.partial + blockIdx.y * gridDim.x + blockIdx.x, g.pstride, g.accumulate);
 }
 
 }  // namespace dugks

@@ -45,6 +45,7 @@ struct dugks_ctx {
     double bcv[4] = {0, 0, 0, 0};
     double c = 1, dt = 0, lambda = 0, cfl = 0;
     int nc = NC_LARGE;  // equilibrium polynomial coefficients used by the step (3, 4 or 16)
+    int nc_u = NC_LARGE;  // the same, large enough for b(phi) and int b'^2 of the u-derivative
     double feq_coef[Q][NC_LARGE];
     double a_bp = 0, b_bp = 0, a_tp = 0, b_tp = 0, a_f = 0, b_f = 0, hc = 0;
     std::vector<double> xf, yf;
@@ -73,7 +74,8 @@ struct dugks_ctx {
     // adjoint work buffers (allocated on first use)
     void* adj_ax = nullptr;
     void* adj_ay = nullptr;
-    double* adj_partial = nullptr;
+    double* adj_partial = nullptr;  // 3 adj_partials(): dJ/dlambda, dJ/du_x, dJ/du_y per block
+    double* adj_upart = nullptr;    // 3 x kInitBlocks: the initialisation's u partials
     double* adj_dalpha = nullptr;
     // source terms (dugks_set_source)
     double ux = 0, uy = 0;
@@ -95,6 +97,7 @@ struct dugks_ctx {
     double tbase = 0;       // t = tbase + tsteps * dt (tbase set by set_source, init_phi, load_state)
     long long tsteps = 0;
     int adj_kernel = DUGKS_ADJ_AUTO;  // dugks_set_adjoint_kernel
+    int feq_check = 0;                // dugks_set_feq_check: initialisations test the equilibrium
     std::string last_error;
 };
 
@@ -145,6 +148,96 @@ void aux_moment_poly(const dugks_coef* cf, double* out /* NC_LARGE */) {
             const int m = k + l - 1;
             out[m] += double(k) * double(l) * cf->b[k] * cf->b[l] / double(m);
         }
+}
+
+// Equilibrium (Eq. 2.3) per velocity as a polynomial in phi, coefficients
+// out[i][m] of phi^m, with e_i the unit direction and c_s^2 = c^2/3:
+//   feq_i = w_i [ phi + 3 (e_i.u)/c b + (3|e_i|^2 - 2)/2 (d - phi)
+//                 + (9 (e_i.u)^2 - 3 |u|^2) / (2 c^2) Cint ]
+// A tensor D adds D:(e_i e_i c^2 - c_s^2 I)/(2 c_s^2) = [(3 ex^2 - 1) dxx + 6 ex ey dxy + (3 ey^2 - 1) dyy]/2
+// in place of (3|e_i|^2 - 2)/2 d; the -phi part keeps the isotropic form.  *maxdeg: highest
+// degree with a nonzero coefficient (at least 1).
+void feq_coefficients(const dugks_vset* vset, const dugks_coef* coef, double (*out)[NC_LARGE], int* maxdeg) {
+    double cint[NC_LARGE];
+    aux_moment_poly(coef, cint);
+    const double wts[Q] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    const double ux = coef->u[0], uy = coef->u[1], c = vset->c;
+    *maxdeg = 1;
+    for (int i = 0; i < Q; ++i) {
+        const double eu = EX(i) * ux + EY(i) * uy;
+        const double e2 = double(EX(i) * EX(i) + EY(i) * EY(i));
+        const double kb = 3.0 * eu / c, kd = (3.0 * e2 - 2.0) / 2.0;
+        const double kxx = (3.0 * EX(i) * EX(i) - 1.0) / 2.0, kyy = (3.0 * EY(i) * EY(i) - 1.0) / 2.0;
+        const double kxy = 3.0 * EX(i) * EY(i);
+        const double kc = (9.0 * eu * eu - 3.0 * (ux * ux + uy * uy)) / (2.0 * c * c);
+        for (int m = 0; m < NC_LARGE; ++m) {
+            const double bm = m < coef->nb ? coef->b[m] : 0.0;
+            const double one = m == 1 ? 1.0 : 0.0;
+            double dpart;
+            if (coef->d_tensor) {
+                const double xx = m < coef->ndt ? coef->dxx[m] : 0.0, xy = m < coef->ndt ? coef->dxy[m] : 0.0;
+                const double yy = m < coef->ndt ? coef->dyy[m] : 0.0;
+                dpart = kxx * xx + kxy * xy + kyy * yy - kd * one;
+            } else {
+                const double dm = m < coef->nd ? coef->d[m] : 0.0;
+                dpart = kd * (dm - one);
+            }
+            const double v = wts[i] * (one + kb * bm + dpart + kc * cint[m]);
+            out[i][m] = v;
+            if (v != 0.0) *maxdeg = std::max(*maxdeg, m);
+        }
+    }
+}
+
+double poly_eval(const double* c, int n, double x) {
+    double s = c[n - 1];
+    for (int m = n - 2; m >= 0; --m) s = s * x + c[m];
+    return s;
+}
+
+// Positivity of the equilibrium over phi in [lo, hi] (the rest velocity as phi minus the
+// sum of the others, as the kernels form it).  *feq_min: the smallest f^eq_i(phi); return
+// value: the smallest margin min_i f^eq_i(phi) + kFeqTol max_i |f^eq_i(phi)|, negative when
+// some equilibrium is negative by more than kFeqTol of the largest one at the same phi.
+// 4097 samples per velocity, then a golden-section refinement around the smallest sample.
+constexpr double kFeqTol = 1e-3;
+double feq_margin_over(const double (*cf)[NC_LARGE], double lo, double hi, double* feq_min) {
+    auto eval = [&](double x, double& mn) {
+        double v[Q], s = 0.0;
+        for (int q = 1; q < Q; ++q) {
+            v[q] = poly_eval(cf[q], NC_LARGE, x);
+            s += v[q];
+        }
+        v[0] = x - s;
+        double mx = 0.0;
+        mn = INFINITY;
+        for (int q = 0; q < Q; ++q) {
+            mn = std::min(mn, v[q]);
+            mx = std::max(mx, std::fabs(v[q]));
+        }
+        return mn + kFeqTol * mx;
+    };
+    const int N = 4096;
+    double best = INFINITY, fmin = INFINITY, mn;
+    int kbest = 0;
+    for (int k = 0; k <= N; ++k) {
+        const double g = eval(lo + (hi - lo) * double(k) / N, mn);
+        fmin = std::min(fmin, mn);
+        if (g < best) { best = g; kbest = k; }
+    }
+    double a = lo + (hi - lo) * double(std::max(kbest - 1, 0)) / N;
+    double b = lo + (hi - lo) * double(std::min(kbest + 1, N)) / N;
+    const double gr = 0.5 * (std::sqrt(5.0) - 1.0);
+    for (int it = 0; it < 60 && b > a; ++it) {
+        const double x1 = b - gr * (b - a), x2 = a + gr * (b - a);
+        double m1, m2;
+        if (eval(x1, m1) < eval(x2, m2)) b = x2; else a = x1;
+        fmin = std::min(fmin, std::min(m1, m2));
+    }
+    best = std::min(best, eval(0.5 * (a + b), mn));
+    fmin = std::min(fmin, mn);
+    if (feq_min) *feq_min = fmin;
+    return best;
 }
 
 template <typename T>
@@ -476,7 +569,8 @@ cudaError_t launch_init(dugks_ctx* ctx, const Tin* phi0) {
     T* f = static_cast<T*>(ctx->buf[ctx->cur]);
     // the initialisation is not on the hot path: always the generic polynomial degree
     init_kernel<T, NC_LARGE, Tin><<<blocks, 256, 0, ctx->stream>>>(phi0, f, ctx->nx, ctx->ny, ctx->pitch, ctx->plane,
-                                                                  make_consts<T, NC_LARGE>(ctx));
+                                                                  make_consts<T, NC_LARGE>(ctx),
+                                                                  ctx->feq_check ? ctx->err_dev : nullptr);
     return cudaGetLastError();
 }
 
@@ -497,7 +591,8 @@ void free_ctx(dugks_ctx* ctx) {
     for (void* p : {ctx->buf[0], ctx->buf[1], ctx->fxm, ctx->fym, ctx->cxm, ctx->cym, static_cast<void*>(ctx->rowy),
                     ctx->adj_ax, ctx->adj_ay,
                     ctx->src_field, ctx->hist[0], ctx->hist[1], ctx->aux[0], ctx->aux[1],
-                    static_cast<void*>(ctx->adj_partial), static_cast<void*>(ctx->adj_dalpha)})
+                    static_cast<void*>(ctx->adj_partial), static_cast<void*>(ctx->adj_dalpha),
+                    static_cast<void*>(ctx->adj_upart)})
         if (p) cudaFree(p);
     for (void* p : {static_cast<void*>(ctx->dxv), static_cast<void*>(ctx->dyv), static_cast<void*>(ctx->staging),
                     static_cast<void*>(ctx->partial), static_cast<void*>(ctx->mass_dev),
@@ -532,6 +627,27 @@ AdjConsts<T, NC> make_adj_consts(const dugks_ctx* ctx) {
     ka.da_bp = T(2.0 * (dt + h) / (d1 * d1)); ka.db_bp = T(-6.0 * h / (d1 * d1));  // d/dlambda of Eq. 2.21 weights
     ka.da_tp = T(4.0 * dt / (d1 * d1)); ka.db_tp = T(-4.0 * dt / (d1 * d1));        // Eq. 2.13
     ka.da_f = T(2.0 * h / (d2 * d2)); ka.db_f = T(-2.0 * h / (d2 * d2));            // Eq. 2.22
+    // d feq_i / d u_a = A_ia b(phi) + B_ia Cint(phi) (Eq. 2.3 with B = u b, C = u u Cint, Remark 3)
+    double cint[NC_LARGE] = {};
+    if (!ctx->c_zero)
+        for (int kk = 1; kk < ctx->nb; ++kk)
+            for (int l = 1; l < ctx->nb; ++l) {
+                const int m = kk + l - 1;
+                cint[m] += double(kk) * double(l) * ctx->bcoef[kk] * ctx->bcoef[l] / double(m);
+            }
+    for (int m = 0; m < NC; ++m) {
+        ka.bpoly[m] = T(m < ctx->nb ? ctx->bcoef[m] : 0.0);
+        ka.cpoly[m] = T(cint[m]);
+    }
+    const double wts[Q] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    const double c = ctx->c, u[2] = {ctx->ux, ctx->uy};
+    for (int i = 0; i < Q; ++i) {
+        const double e[2] = {double(EX(i)), double(EY(i))}, eu = e[0] * u[0] + e[1] * u[1];
+        for (int ax = 0; ax < 2; ++ax) {
+            ka.Au[ax][i] = T(3.0 * wts[i] * e[ax] / c);
+            ka.Bu[ax][i] = T(ctx->c_zero ? 0.0 : wts[i] * (9.0 * e[ax] * eu - 3.0 * u[ax]) / (c * c));
+        }
+    }
     return ka;
 }
 
@@ -556,6 +672,10 @@ long long adj_wall_cells(const dugks_ctx* ctx) {
 }
 int adj_wall_blocks(const dugks_ctx* ctx) { return int((adj_wall_cells(ctx) + kAdjThreads - 1) / kAdjThreads); }
 int adj_partials(const dugks_ctx* ctx) { return adj_tile_blocks(ctx) + adj_wall_blocks(ctx); }
+// blocks of init_adjoint_kernel
+int init_blocks(const dugks_ctx* ctx) {
+    return int(std::min<long long>(((long long)ctx->nx * ctx->ny + 255) / 256, 65535));
+}
 
 dugks_status adj_alloc(dugks_ctx* ctx) {
     if (adj_tile_grid(ctx).y > 65535u) {
@@ -567,18 +687,18 @@ dugks_status adj_alloc(dugks_ctx* ctx) {
     const size_t nxf = size_t(ctx->nx + 1) * ctx->ny, nyf = size_t(ctx->nx) * (ctx->ny + 1);
     if ((e = cudaMalloc(&ctx->adj_ax, Q * nxf * ctx->elem)) != cudaSuccess ||
         (e = cudaMalloc(&ctx->adj_ay, Q * nyf * ctx->elem)) != cudaSuccess ||
-        (e = cudaMalloc(&ctx->adj_partial,
-                        sizeof(double) * size_t(adj_partials(ctx)))) !=
-            cudaSuccess ||
-        (e = cudaMalloc(&ctx->adj_dalpha, sizeof(double))) != cudaSuccess)
+        (e = cudaMalloc(&ctx->adj_partial, 3 * sizeof(double) * size_t(adj_partials(ctx)))) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->adj_dalpha, 3 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&ctx->adj_upart, 3 * sizeof(double) * size_t(init_blocks(ctx)))) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaMalloc(adjoint buffers)");
     return DUGKS_OK;
 }
 
 
-// *dj_dalpha += (sum of the block partials) / c_s^2
-cudaError_t launch_adj_sum(dugks_ctx* ctx, double* dj_dalpha) {
-    adj_sum_kernel<<<1, 1024, 0, ctx->stream>>>(ctx->adj_partial, adj_partials(ctx), 3.0 / (ctx->c * ctx->c), dj_dalpha);
+// *dj_dalpha += (sum of the lambda partials) / c_s^2; dj_du[a] += sum of the u_a partials (dj_du nullable)
+cudaError_t launch_adj_sum(dugks_ctx* ctx, double* dj_dalpha, double* dj_du) {
+    adj_sum_kernel<<<1, 1024, 0, ctx->stream>>>(ctx->adj_partial, adj_partials(ctx), adj_partials(ctx),
+                                                3.0 / (ctx->c * ctx->c), dj_dalpha, dj_du);
     return cudaGetLastError();
 }
 
@@ -631,19 +751,22 @@ cudaError_t launch_adjoint_rows(dugks_ctx* ctx, const StepArgs<float, NC>& a, co
     nseg = (ctx->ny + seg - 1) / seg;
     if ((long long)strips * nseg > cap) return cudaErrorInvalidConfiguration;
     if (!g.accumulate && (long long)strips * nseg < cap)  // slots this launch leaves alone are summed too
-        if ((e = cudaMemsetAsync(g.partial + strips * nseg, 0, sizeof(double) * size_t(cap - strips * nseg),
-                                 ctx->stream)) != cudaSuccess)
-            return e;
+        for (int q = 0; q < 3; ++q)
+            if ((e = cudaMemsetAsync(g.partial + q * cap + strips * nseg, 0,
+                                     sizeof(double) * size_t(cap - strips * nseg), ctx->stream)) != cudaSuccess)
+                return e;
     adj_rows_kernel<NC><<<dim3(strips, unsigned(nseg)), 32, L::bytes(kAdjRowStages), ctx->stream>>>(
         tm[0], tm[1], a, k, ka, g, seg, kAdjRowStages);
     return cudaGetLastError();
 }
 
 // One adjoint step.  dj_dalpha != nullptr: the step's partials overwrite the
-// partial buffer and are summed into *dj_dalpha; nullptr: they are added to the
-// partial buffer (a reverse sweep zeroes it first and sums it at the end).
+// partial buffer and are summed into *dj_dalpha (and dj_du[0..1] if set); nullptr:
+// they are added to the partial buffer (a reverse sweep zeroes it first and sums it
+// at the end).  want_u: also form the u-derivative.
 template <typename T, int NC>
-cudaError_t launch_adjoint_step(dugks_ctx* ctx, const void* f, const void* mu, void* lam, double* dj_dalpha) {
+cudaError_t launch_adjoint_step(dugks_ctx* ctx, const void* f, const void* mu, void* lam, double* dj_dalpha,
+                                double* dj_du, bool want_u) {
     StepArgs<T, NC> a = make_args<T, NC>(ctx, 0);
     a.fin = static_cast<const T*>(f);  // the adjoint reads contiguous [Q][ny][nx] states
     a.pitch = ctx->nx;
@@ -657,12 +780,14 @@ cudaError_t launch_adjoint_step(dugks_ctx* ctx, const void* f, const void* mu, v
     g.Ax = static_cast<T*>(ctx->adj_ax);
     g.Ay = static_cast<T*>(ctx->adj_ay);
     g.partial = ctx->adj_partial;
+    g.pstride = adj_partials(ctx);
     g.accumulate = dj_dalpha ? 0 : 1;
+    g.want_u = want_u ? 1 : 0;
     if constexpr (sizeof(T) == 4 && NC != NC_LARGE) {
         if (adj_rows_ok(ctx, f, mu)) {
             cudaError_t e = launch_adjoint_rows<NC>(ctx, a, k, ka, g, f, mu);
             if (e != cudaSuccess) return e;
-            if (dj_dalpha) return launch_adj_sum(ctx, dj_dalpha);
+            if (dj_dalpha) return launch_adj_sum(ctx, dj_dalpha, dj_du);
             return cudaGetLastError();
         }
     }
@@ -675,32 +800,38 @@ cudaError_t launch_adjoint_step(dugks_ctx* ctx, const void* f, const void* mu, v
     adj_tile_kernel<T, NC, kAdjTX, kAdjTY><<<adj_tile_grid(ctx), kAdjTX * kAdjTY, smem, ctx->stream>>>(a, k, ka, g,
                                                                                                      wb > 0 ? 1 : 0);
     if (wb > 0) adj_wall_kernel<T, NC><<<wb, kAdjThreads, 0, ctx->stream>>>(a, k, ka, g, tb);
-    if (dj_dalpha) return launch_adj_sum(ctx, dj_dalpha);
+    if (dj_dalpha) return launch_adj_sum(ctx, dj_dalpha, dj_du);
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_step_any(dugks_ctx* ctx, const void* f, const void* mu, void* lam, double* dj_dalpha) {
+cudaError_t launch_adjoint_step_any(dugks_ctx* ctx, const void* f, const void* mu, void* lam, double* dj_dalpha,
+                                    double* dj_du, bool want_u) {
+    const int nc = want_u ? std::max(ctx->nc, ctx->nc_u) : ctx->nc;
     if (ctx->precision == 32) {
-        switch (ctx->nc) {
-            case 3: return launch_adjoint_step<float, 3>(ctx, f, mu, lam, dj_dalpha);
-            case 4: return launch_adjoint_step<float, 4>(ctx, f, mu, lam, dj_dalpha);
-            default: return launch_adjoint_step<float, NC_LARGE>(ctx, f, mu, lam, dj_dalpha);
+        switch (nc) {
+            case 3: return launch_adjoint_step<float, 3>(ctx, f, mu, lam, dj_dalpha, dj_du, want_u);
+            case 4: return launch_adjoint_step<float, 4>(ctx, f, mu, lam, dj_dalpha, dj_du, want_u);
+            default: return launch_adjoint_step<float, NC_LARGE>(ctx, f, mu, lam, dj_dalpha, dj_du, want_u);
         }
     }
-    switch (ctx->nc) {
-        case 3: return launch_adjoint_step<double, 3>(ctx, f, mu, lam, dj_dalpha);
-        case 4: return launch_adjoint_step<double, 4>(ctx, f, mu, lam, dj_dalpha);
-        default: return launch_adjoint_step<double, NC_LARGE>(ctx, f, mu, lam, dj_dalpha);
+    switch (nc) {
+        case 3: return launch_adjoint_step<double, 3>(ctx, f, mu, lam, dj_dalpha, dj_du, want_u);
+        case 4: return launch_adjoint_step<double, 4>(ctx, f, mu, lam, dj_dalpha, dj_du, want_u);
+        default: return launch_adjoint_step<double, NC_LARGE>(ctx, f, mu, lam, dj_dalpha, dj_du, want_u);
     }
 }
 
+// dJ/dphi0 from lam^0; with dj_du set, the initialisation's share of dJ/du (f^0 = feq(phi0)
+// depends on u) is added to dj_du[0..1]
 template <typename T>
-cudaError_t launch_init_adjoint(dugks_ctx* ctx, const void* phi0, const void* lam, void* gphi0) {
+cudaError_t launch_init_adjoint(dugks_ctx* ctx, const void* phi0, const void* lam, void* gphi0, double* dj_du) {
     const long long n = (long long)ctx->nx * ctx->ny;
-    const int blocks = int(std::min<long long>((n + 255) / 256, 65535));
+    const int blocks = init_blocks(ctx);
     init_adjoint_kernel<T, NC_LARGE><<<blocks, 256, 0, ctx->stream>>>(
         static_cast<const T*>(phi0), static_cast<const T*>(lam), static_cast<T*>(gphi0), n,
-        make_adj_consts<T, NC_LARGE>(ctx));
+        make_adj_consts<T, NC_LARGE>(ctx), dj_du ? ctx->adj_upart : nullptr);
+    if (dj_du)
+        adj_sum_kernel<<<1, 1024, 0, ctx->stream>>>(ctx->adj_upart, blocks, blocks, 0.0, nullptr, dj_du);
     return cudaGetLastError();
 }
 
@@ -871,6 +1002,28 @@ dugks_status dugks_check_config(const dugks_mesh* mesh, const dugks_vset* vset, 
     return DUGKS_OK;
 }
 
+dugks_status dugks_check_feq(const dugks_vset* vset, const dugks_coef* coef, double phi_min, double phi_max,
+                             double* feq_min_out) {
+    if (!vset || !coef || vset->kind != DUGKS_D2Q9) return DUGKS_ERR_ARG;
+    if (coef->nb < 0 || coef->nb > 8 || coef->nd < 0 || coef->nd > 8) return DUGKS_ERR_ARG;
+    if (coef->d_tensor != 0 && coef->d_tensor != 1) return DUGKS_ERR_ARG;
+    if (coef->d_tensor && (coef->ndt < 0 || coef->ndt > 8)) return DUGKS_ERR_ARG;
+    if (!std::isfinite(phi_min) || !std::isfinite(phi_max) || phi_min > phi_max) return DUGKS_ERR_ARG;
+    if (!std::isfinite(vset->c) || !(vset->c > 0.0) || !finite_all(coef->u, 2) || !finite_all(coef->b, coef->nb) ||
+        !finite_all(coef->d, coef->nd))
+        return DUGKS_ERR_CONFIG;
+    if (coef->d_tensor &&
+        (!finite_all(coef->dxx, coef->ndt) || !finite_all(coef->dxy, coef->ndt) || !finite_all(coef->dyy, coef->ndt)))
+        return DUGKS_ERR_CONFIG;
+    double cf[Q][NC_LARGE];
+    int maxdeg = 1;
+    feq_coefficients(vset, coef, cf, &maxdeg);
+    double fmin = 0.0;
+    const double margin = feq_margin_over(cf, phi_min, phi_max, &fmin);
+    if (feq_min_out) *feq_min_out = fmin;
+    return margin < 0.0 ? DUGKS_ERR_CONFIG : DUGKS_OK;
+}
+
 dugks_status dugks_create(const dugks_mesh* mesh, const dugks_vset* vset, const dugks_coef* coef, double dt,
                           const dugks_options* opts, dugks_ctx** out) {
     if (!out) return DUGKS_ERR_ARG;
@@ -926,42 +1079,18 @@ dugks_status dugks_create(const dugks_mesh* mesh, const dugks_vset* vset, const 
     ctx->b_f = h / (2.0 * lam + h);
     ctx->hc = h * vset->c;
 
-    // Equilibrium (Eq. 2.3) per velocity as a polynomial in phi, with
-    // e_i the unit direction, c_s^2 = c^2/3:
-    //   feq_i = w_i [ phi + 3 (e_i.u)/c b + (3|e_i|^2 - 2)/2 (d - phi)
-    //                 + (9 (e_i.u)^2 - 3 |u|^2) / (2 c^2) Cint ]
-    double cint[NC_LARGE];
-    aux_moment_poly(coef, cint);
-    const double wts[Q] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
-    const double ux = coef->u[0], uy = coef->u[1], c = vset->c;
+    const double c = vset->c;
     int maxdeg = 1;
-    // A tensor D adds D:(e_i e_i c^2 - c_s^2 I)/(2 c_s^2) = [(3 ex^2 - 1) dxx + 6 ex ey dxy + (3 ey^2 - 1) dyy]/2
-    // in place of (3|e_i|^2 - 2)/2 d; the -phi part keeps the isotropic form.
-    for (int i = 0; i < Q; ++i) {
-        const double eu = EX(i) * ux + EY(i) * uy;
-        const double e2 = double(EX(i) * EX(i) + EY(i) * EY(i));
-        const double kb = 3.0 * eu / c, kd = (3.0 * e2 - 2.0) / 2.0;
-        const double kxx = (3.0 * EX(i) * EX(i) - 1.0) / 2.0, kyy = (3.0 * EY(i) * EY(i) - 1.0) / 2.0;
-        const double kxy = 3.0 * EX(i) * EY(i);
-        const double kc = (9.0 * eu * eu - 3.0 * (ux * ux + uy * uy)) / (2.0 * c * c);
-        for (int m = 0; m < NC_LARGE; ++m) {
-            const double bm = m < coef->nb ? coef->b[m] : 0.0;
-            const double one = m == 1 ? 1.0 : 0.0;
-            double dpart;
-            if (coef->d_tensor) {
-                const double xx = m < coef->ndt ? coef->dxx[m] : 0.0, xy = m < coef->ndt ? coef->dxy[m] : 0.0;
-                const double yy = m < coef->ndt ? coef->dyy[m] : 0.0;
-                dpart = kxx * xx + kxy * xy + kyy * yy - kd * one;
-            } else {
-                const double dm = m < coef->nd ? coef->d[m] : 0.0;
-                dpart = kd * (dm - one);
-            }
-            const double v = wts[i] * (one + kb * bm + dpart + kc * cint[m]);
-            ctx->feq_coef[i][m] = v;
-            if (v != 0.0) maxdeg = std::max(maxdeg, m);
-        }
-    }
+    feq_coefficients(vset, coef, ctx->feq_coef, &maxdeg);
     ctx->nc = maxdeg <= 2 ? 3 : (maxdeg == 3 ? 4 : NC_LARGE);
+    {  // with u = 0 the step's equilibrium has no b terms, but d feq / d u has b and C/(u u)
+        int degb = 0;
+        for (int m = 0; m < ctx->nb; ++m)
+            if (ctx->bcoef[m] != 0.0) degb = m;
+        const int degc = (ctx->c_zero || degb < 1) ? 0 : 2 * degb - 1;
+        const int du = std::max(maxdeg, std::max(degb, degc));
+        ctx->nc_u = du <= 2 ? 3 : (du == 3 ? 4 : NC_LARGE);
+    }
 
     const int lane = 128 / int(ctx->elem);  // rows padded to 128 bytes
     ctx->pitch = ((long long)ctx->nx + lane - 1) / lane * lane;
@@ -1069,6 +1198,25 @@ dugks_status dugks_init_phi_host(dugks_ctx* ctx, const double* phi0_host) {
     if (!ctx || !phi0_host) return DUGKS_ERR_ARG;
     DeviceGuard guard(ctx->device);
     const size_t n = size_t(ctx->nx) * ctx->ny;
+    if (ctx->feq_check) {  // the initial equilibrium must be non-negative over the range of phi0
+        double lo = INFINITY, hi = -INFINITY;
+        for (size_t c = 0; c < n; ++c) {
+            lo = std::min(lo, phi0_host[c]);
+            hi = std::max(hi, phi0_host[c]);
+        }
+        if (!std::isfinite(lo) || !std::isfinite(hi)) {
+            ctx->last_error = "phi0 holds a non-finite value";
+            return DUGKS_ERR_CONFIG;
+        }
+        double fmin = 0.0;
+        if (feq_margin_over(ctx->feq_coef, lo, hi, &fmin) < 0.0) {
+            char buf[192];
+            snprintf(buf, sizeof(buf), "the equilibrium of phi0 is negative (min %.3e over phi in [%.6g, %.6g])", fmin, lo,
+                     hi);
+            ctx->last_error = buf;
+            return DUGKS_ERR_CONFIG;
+        }
+    }
     CK(cudaMemcpyAsync(ctx->staging, phi0_host, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     cudaError_t e = ctx->precision == 32 ? launch_init<float, double>(ctx, ctx->staging)
                                          : launch_init<double, double>(ctx, ctx->staging);
@@ -1158,10 +1306,20 @@ dugks_status dugks_sync(dugks_ctx* ctx) {
     CK(cudaStreamSynchronize(ctx->stream));
     int err = 0;
     CK(cudaMemcpy(&err, ctx->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
-    if (err) {
+    if (err & 1) {
         ctx->last_error = "a bounded TMA wait in the step kernel expired";
         return DUGKS_ERR_TIMEOUT;
     }
+    if (err & 4) {
+        ctx->last_error = "dugks_init_phi: the equilibrium of phi0 is negative in some cell";
+        return DUGKS_ERR_CONFIG;
+    }
+    return DUGKS_OK;
+}
+
+dugks_status dugks_set_feq_check(dugks_ctx* ctx, int on) {
+    if (!ctx || (on != 0 && on != 1)) return DUGKS_ERR_ARG;
+    ctx->feq_check = on;
     return DUGKS_OK;
 }
 
@@ -1279,7 +1437,7 @@ dugks_status dugks_set_source(dugks_ctx* ctx, int nterms, const double* rate, co
 }
 
 dugks_status dugks_adjoint_step(dugks_ctx* ctx, const void* f_dev, const void* mu_dev, void* lam_dev,
-                                double* dj_dalpha_dev) {
+                                double* dj_dalpha_dev, double* dj_du_dev) {
     if (!ctx || !f_dev || !mu_dev || !lam_dev || !dj_dalpha_dev) return DUGKS_ERR_ARG;
     if (ctx->nsrc > 0) {
         ctx->last_error = "the adjoint covers the step without source terms";
@@ -1288,12 +1446,13 @@ dugks_status dugks_adjoint_step(dugks_ctx* ctx, const void* f_dev, const void* m
     DeviceGuard guard(ctx->device);
     dugks_status st = adj_alloc(ctx);
     if (st != DUGKS_OK) return st;
-    CK(launch_adjoint_step_any(ctx, f_dev, mu_dev, lam_dev, dj_dalpha_dev));
+    CK(launch_adjoint_step_any(ctx, f_dev, mu_dev, lam_dev, dj_dalpha_dev, dj_du_dev, dj_du_dev != nullptr));
     return DUGKS_OK;
 }
 
 dugks_status dugks_adjoint(dugks_ctx* ctx, const void* phi0_dev, long long nsteps, int checkpoint_every,
-                           const void* grad_phiN_dev, void* grad_phi0_dev, double* grad_alpha_out) {
+                           const void* grad_phiN_dev, void* grad_phi0_dev, double* grad_alpha_out,
+                           double* grad_u_out) {
     if (!ctx || !phi0_dev || !grad_phiN_dev || !grad_phi0_dev || nsteps < 0 || checkpoint_every < 1)
         return DUGKS_ERR_ARG;
     if (ctx->nsrc > 0) {
@@ -1336,9 +1495,12 @@ dugks_status dugks_adjoint(dugks_ctx* ctx, const void* phi0_dev, long long nstep
         if ((st = dugks_save_state(ctx, ckpt[s])) != DUGKS_OK) { release(); return st; }
         if ((st = dugks_step(ctx, std::min(K, nsteps - s * K))) != DUGKS_OK) { release(); return st; }
     }
-    if ((e = cudaMemsetAsync(ctx->adj_dalpha, 0, sizeof(double), ctx->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(ctx->adj_partial, 0, sizeof(double) * size_t(adj_partials(ctx)), ctx->stream)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(ctx->adj_dalpha, 0, 3 * sizeof(double), ctx->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(ctx->adj_partial, 0, 3 * sizeof(double) * size_t(adj_partials(ctx)), ctx->stream)) !=
+            cudaSuccess)
         return fail(e, "cudaMemsetAsync");
+    const bool want_u = grad_u_out != nullptr;
+    double* du_dev = want_u ? ctx->adj_dalpha + 1 : nullptr;
     const long long n = (long long)ctx->nx * ctx->ny;
     const int blocks = int(std::min<long long>((n + 255) / 256, 65535));
     if (ctx->precision == 32)
@@ -1358,21 +1520,27 @@ dugks_status dugks_adjoint(dugks_ctx* ctx, const void* phi0_dev, long long nstep
             if (q + 1 < ns && (st = dugks_step(ctx, 1)) != DUGKS_OK) { release(); return st; }
         }
         for (long long q = ns - 1; q >= 0; --q) {
-            if ((e = launch_adjoint_step_any(ctx, seg[q], lam[cur], lam[1 - cur], nullptr)) != cudaSuccess)
+            if ((e = launch_adjoint_step_any(ctx, seg[q], lam[cur], lam[1 - cur], nullptr, nullptr, want_u)) !=
+                cudaSuccess)
                 return fail(e, "adjoint step");
             cur ^= 1;
         }
     }
-    if ((e = launch_adj_sum(ctx, ctx->adj_dalpha)) != cudaSuccess) return fail(e, "adjoint sum");
-    e = ctx->precision == 32 ? launch_init_adjoint<float>(ctx, phi0_dev, lam[cur], grad_phi0_dev)
-                             : launch_init_adjoint<double>(ctx, phi0_dev, lam[cur], grad_phi0_dev);
+    if ((e = launch_adj_sum(ctx, ctx->adj_dalpha, du_dev)) != cudaSuccess) return fail(e, "adjoint sum");
+    e = ctx->precision == 32 ? launch_init_adjoint<float>(ctx, phi0_dev, lam[cur], grad_phi0_dev, du_dev)
+                             : launch_init_adjoint<double>(ctx, phi0_dev, lam[cur], grad_phi0_dev, du_dev);
     if (e != cudaSuccess) return fail(e, "init adjoint");
-    double da = 0.0;
-    if ((e = cudaMemcpyAsync(&da, ctx->adj_dalpha, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+    double res[3] = {0.0, 0.0, 0.0};
+    if ((e = cudaMemcpyAsync(res, ctx->adj_dalpha, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream)) !=
+        cudaSuccess)
         return fail(e, "cudaMemcpyAsync");
     if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return fail(e, "cudaStreamSynchronize");
     release();
-    if (grad_alpha_out) *grad_alpha_out = da;
+    if (grad_alpha_out) *grad_alpha_out = res[0];
+    if (grad_u_out) {
+        grad_u_out[0] = res[1];
+        grad_u_out[1] = res[2];
+    }
     return DUGKS_OK;
 }
 
@@ -1613,6 +1781,8 @@ extern "C" dugks_status dugks_phi_mass_noalloc(const void* f_dev, int precision,
     if (noalloc_scratch(dev, &partial) != cudaSuccess) return DUGKS_ERR_CUDA;
     const int blocks = int((n + 255) / 256);  // one partial per 256 cells, each written exactly once
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // an error the caller left pending is neither cleared nor reported as this call's
+    const cudaError_t before = cudaPeekAtLastError();
     if (precision == DUGKS_FP32)
         phi_mass_kernel<float, float><<<blocks, 256, 0, s>>>(static_cast<const float*>(f_dev),
                                                              static_cast<float*>(phi_dev_out), nx, ny, nx, n, dx_dev,
@@ -1622,5 +1792,9 @@ extern "C" dugks_status dugks_phi_mass_noalloc(const void* f_dev, int precision,
                                                                static_cast<double*>(phi_dev_out), nx, ny, nx, n,
                                                                dx_dev, dy_dev, partial);
     sum_partials_kernel<<<1, 256, 0, s>>>(partial, blocks, mass_dev_out);
-    return cudaGetLastError() == cudaSuccess ? DUGKS_OK : DUGKS_ERR_CUDA;
+    if (before == cudaSuccess && cudaPeekAtLastError() != cudaSuccess) {
+        cudaGetLastError();  // this call's launch failure: clear it and report it
+        return DUGKS_ERR_CUDA;
+    }
+    return DUGKS_OK;
 }

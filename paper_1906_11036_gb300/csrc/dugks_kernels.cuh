@@ -1054,18 +1054,28 @@ __global__ void __launch_bounds__(32, DUGKS_VP_SRC_MIN_WARPS) fused_step_vp_src(
 // initialisation and moments
 // ---------------------------------------------------------------------------
 
-// ftilde_i = feq_i(phi0) (opening of Section 4).  phi0 is [ny][nx] contiguous.
+// ftilde_i = feq_i(phi0) (opening of Section 4).  phi0 is [ny][nx] contiguous.  With err
+// set, an equilibrium negative by more than 1e-3 of the cell's largest one (Eq. 2.3 allows
+// it for large |B|/c or D) sets bit 2 (value 4) of the error word.
 template <typename T, int NC, typename Tin>
 __global__ void init_kernel(const Tin* __restrict__ phi0, T* __restrict__ f, int nx, int ny, long long pitch,
-                            long long plane, const Consts<T, NC> k) {
+                            long long plane, const Consts<T, NC> k, int* err) {
     const long long n = (long long)nx * ny;
+    bool neg = false;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int kr = int(c / nx), j = int(c % nx);
         T fe[Q];
         feq_all(k, T(phi0[c]), fe);
+        T mn = fe[0], mx = fabs(fe[0]);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) f[i * plane + kr * pitch + j] = fe[i];
+        for (int i = 0; i < Q; ++i) {
+            f[i * plane + kr * pitch + j] = fe[i];
+            mn = fmin(mn, fe[i]);
+            mx = fmax(mx, fabs(fe[i]));
+        }
+        neg |= mn + T(1e-3) * mx < T(0);
     }
+    if (neg && err) atomicOr(err, 4);
 }
 
 // phi = sum_i ftilde_i (optionally stored as Tout), and per-block partial

@@ -91,6 +91,7 @@ def library():
         L = ctypes.CDLL(LIB)
         vp, P = ctypes.c_void_p, ctypes.POINTER
         L.dugks_check_config.argtypes = [P(Mesh), P(VSet), P(Coef), ctypes.c_double]
+        L.dugks_check_feq.argtypes = [P(VSet), P(Coef), ctypes.c_double, ctypes.c_double, P(ctypes.c_double)]
         L.dugks_create.argtypes = [P(Mesh), P(VSet), P(Coef), ctypes.c_double, P(Options), P(vp)]
         L.dugks_destroy.argtypes = [vp]
         L.dugks_init_phi.argtypes = [vp, vp]
@@ -104,10 +105,12 @@ def library():
         L.dugks_sync.argtypes = [vp]
         L.dugks_wait_timeout_check.argtypes = [vp, ctypes.c_int]
         L.dugks_set_adjoint_kernel.argtypes = [vp, ctypes.c_int]
+        L.dugks_set_feq_check.argtypes = [vp, ctypes.c_int]
         L.dugks_info.argtypes = [vp, P(Info)]
-        L.dugks_adjoint_step.argtypes = [vp, vp, vp, vp, vp]
+        L.dugks_adjoint_step.argtypes = [vp, vp, vp, vp, vp, vp]
         L.dugks_set_source.argtypes = [vp, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int), vp, ctypes.c_double]
-        L.dugks_adjoint.argtypes = [vp, vp, ctypes.c_longlong, ctypes.c_int, vp, vp, P(ctypes.c_double)]
+        L.dugks_adjoint.argtypes = [vp, vp, ctypes.c_longlong, ctypes.c_int, vp, vp, P(ctypes.c_double),
+                                    P(ctypes.c_double)]
         L.dugks_phi_mass_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp]
         L.dugks_batch_create.argtypes = [ctypes.c_int, P(Mesh), P(VSet), P(Coef), P(ctypes.c_double), P(Options),
                                          P(vp)]
@@ -197,6 +200,15 @@ def check_config(problem: inputs.Problem) -> int:
     """Host-only validation (no CUDA call); returns the status code."""
     m, v, c, keep = marshal(problem)
     return int(library().dugks_check_config(ctypes.byref(m), ctypes.byref(v), ctypes.byref(c), float(problem.dt)))
+
+
+def check_feq(problem: inputs.Problem, phi_min: float, phi_max: float) -> tuple[int, float]:
+    """Host-only positivity test of the equilibrium over [phi_min, phi_max]:
+    (status, smallest f^eq)."""
+    m, v, c, keep = marshal(problem)
+    out = ctypes.c_double(0.0)
+    st = library().dugks_check_feq(ctypes.byref(v), ctypes.byref(c), float(phi_min), float(phi_max), ctypes.byref(out))
+    return int(st), float(out.value)
 
 
 class Solver:
@@ -332,40 +344,53 @@ class Solver:
         """Let one bounded device wait expire on purpose (no fault): the next sync raises DUGKS_ERR_TIMEOUT."""
         self._check(self.L.dugks_wait_timeout_check(self.h, int(limit_us)), "dugks_wait_timeout_check")
 
+    def set_feq_check(self, on: bool = True):
+        """Later initialisations reject a negative equilibrium of phi0 (see dugks_check_feq)."""
+        self._check(self.L.dugks_set_feq_check(self.h, 1 if on else 0), "dugks_set_feq_check")
+
     ADJ_KERNELS = {"auto": 0, "tiled": 1, "rows": 2}
 
     def set_adjoint_kernel(self, kind: str):
         """Which kernel runs an FP32 adjoint step: "auto", "tiled" or "rows" (cross-check hook)."""
         self._check(self.L.dugks_set_adjoint_kernel(self.h, self.ADJ_KERNELS[kind]), "dugks_set_adjoint_kernel")
 
-    def adjoint_step(self, f, mu, dj_dalpha=None):
+    def adjoint_step(self, f, mu, dj_dalpha=None, dj_du=None, with_u=False):
         """lam = (d f^{n+1}/d f^n)^T mu at state f (CUDA tensors [9, ny, nx]); the
         explicit alpha-derivative is accumulated into dj_dalpha (a CUDA float64
-        tensor of one element, created if None).  Returns (lam, dj_dalpha)."""
+        tensor of one element, created if None).  Returns (lam, dj_dalpha); with
+        with_u (or dj_du given: a CUDA float64 tensor of two elements) the explicit
+        u-derivative is accumulated too and (lam, dj_dalpha, dj_du) is returned."""
         t = self.torch
         f = f.to(device=self.device, dtype=self.dtype).contiguous()
         mu = mu.to(device=self.device, dtype=self.dtype).contiguous()
         lam = t.empty_like(f)
         if dj_dalpha is None:
             dj_dalpha = t.zeros(1, dtype=t.float64, device=self.device)
+        with_u = with_u or dj_du is not None
+        if with_u and dj_du is None:
+            dj_du = t.zeros(2, dtype=t.float64, device=self.device)
+        du_ptr = ctypes.c_void_p(dj_du.data_ptr()) if with_u else None
         self._check(self.L.dugks_adjoint_step(self.h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(mu.data_ptr()),
-                                              ctypes.c_void_p(lam.data_ptr()), ctypes.c_void_p(dj_dalpha.data_ptr())),
-                    "dugks_adjoint_step")
-        return lam, dj_dalpha
+                                              ctypes.c_void_p(lam.data_ptr()), ctypes.c_void_p(dj_dalpha.data_ptr()),
+                                              du_ptr), "dugks_adjoint_step")
+        return (lam, dj_dalpha, dj_du) if with_u else (lam, dj_dalpha)
 
-    def gradient(self, phi0, nsteps: int, grad_phiN, checkpoint_every: int = 20):
+    def gradient(self, phi0, nsteps: int, grad_phiN, checkpoint_every: int = 20, with_u: bool = False):
         """(dJ/dphi0, dJ/dalpha) through nsteps steps, given dJ/dphi^N (checkpointed
-        reverse sweep in the library).  Leaves the solver's state at an
-        intermediate step."""
+        reverse sweep in the library); with_u: (dJ/dphi0, dJ/dalpha, (dJ/du_x,
+        dJ/du_y)).  Leaves the solver's state at an intermediate step."""
         t = self.torch
         phi0 = phi0.to(device=self.device, dtype=self.dtype).contiguous()
         g = grad_phiN.to(device=self.device, dtype=self.dtype).contiguous()
         out = t.empty_like(phi0)
         da = ctypes.c_double(0.0)
+        du = (ctypes.c_double * 2)(0.0, 0.0)
         self._check(self.L.dugks_adjoint(self.h, ctypes.c_void_p(phi0.data_ptr()), int(nsteps), int(checkpoint_every),
                                          ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(out.data_ptr()),
-                                         ctypes.byref(da)), "dugks_adjoint")
-        return out, da.value
+                                         ctypes.byref(da),
+                                         ctypes.cast(du, ctypes.POINTER(ctypes.c_double)) if with_u else None),
+                    "dugks_adjoint")
+        return (out, da.value, (du[0], du[1])) if with_u else (out, da.value)
 
     def info(self) -> dict:
         i = Info()

@@ -373,6 +373,30 @@ def burgers3d(n: int = 256, ny: int | None = None, nz: int | None = None, lattic
     return p, burgers3d_phi0(xc, yc, zc, seed)
 
 
+def adjoint_workload(n: int = 512, steps: int = 400):
+    """The adjoint workload: the Burgers-type NCDE on n^2 periodic cells, `steps`
+    steps, misfit J = 1/2 sum_cells |V| (phi^N - phi_target)^2 to a seeded target of
+    the same form as phi0 (seed 5).  Returns (problem, phi0, target, cell areas)."""
+    p, phi0 = burgers(n, steps=steps)
+    xc, yc = p.centres()
+    return p, phi0, burgers_phi0(xc, yc, seed=5), np.outer(np.diff(p.yf), np.diff(p.xf))
+
+
+def unit_directions(shape, count: int, seed: int = 5):
+    """`count` seeded random directions of unit 2-norm (standard normal entries)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        d = rng.standard_normal(shape)
+        out.append(d / np.linalg.norm(d))
+    return out
+
+
+def batched_sample(count: int = 16, seed: int = 17, n: int = 256):
+    """Indices of `count` instances of the batched workload, drawn without repetition."""
+    return sorted(int(i) for i in np.random.default_rng(seed).choice(n, size=count, replace=False))
+
+
 PRESETS = {
     "gaussian_hill": gaussian_hill,
     "burgers": burgers,

@@ -3,9 +3,13 @@ the FP64 oracle's adjoint, which test_oracle_adjoint.py pins to central
 finite differences.
 
 Tolerances: FP64 GPU 1e-11 relative (rounding order only); FP32 GPU 1e-4
-relative on the gradient (the FP64 accumulation of dJ/dalpha keeps alpha's
-error at FP32 rounding of the summands).
+relative on the gradient (the FP64 accumulation of dJ/dalpha and dJ/du keeps
+their error at FP32 rounding of the summands).  The adjoint workload (512^2,
+400 steps) is checked against stored FP64 central differences of the oracle
+(tests/golden/oracle_adjoint_fd.npz, written by make_adjoint_fd.py there).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -86,6 +90,51 @@ def test_adjoint_step_matches_oracle(name, prec):
     assert abs(da - da_ref) <= tol * 10 * max(abs(da_ref), 1e-12)
 
 
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("name", list(CASES))
+def test_adjoint_step_u_derivative_matches_oracle(name, prec):
+    """The explicit u-derivative of one step (u of B = u b(phi)): cells, faces,
+    ghosts; lam and dJ/dalpha are unchanged by asking for it."""
+    adj = "rows" if name.startswith("periodic_") else "auto"
+    p = CASES[name]()
+    rng = np.random.default_rng(len(name) + 100)
+    o = Oracle(p)
+    f = o.init(1.0 + 0.2 * rng.standard_normal((p.ny, p.nx))) + 0.01 * rng.standard_normal((9, p.ny, p.nx))
+    mu = rng.standard_normal(f.shape)
+    lam_ref, da_ref, du_ref = o.adjoint_step_full(f, mu)
+    s = _solver(p, prec, adj)
+    dt = s.dtype
+    lam, da, du = s.adjoint_step(torch.tensor(f, dtype=dt, device="cuda"), torch.tensor(mu, dtype=dt, device="cuda"),
+                                 with_u=True)
+    lam = lam.double().cpu().numpy()
+    da, du = float(da.item()), du.cpu().numpy()
+    s.close()
+    tol = 1e-11 if prec == 64 else 2e-5
+    assert _rel(lam, lam_ref) <= tol, _rel(lam, lam_ref)
+    assert abs(da - da_ref) <= tol * 10 * max(abs(da_ref), 1e-12)
+    scale = max(float(np.abs(du_ref).max()), 1e-12)
+    assert np.abs(du - du_ref).max() <= tol * 10 * scale, (du, du_ref)
+
+
+def test_u_derivative_with_zero_velocity():
+    """u = 0: the step's equilibrium has no b terms, but d feq / d u does (b and
+    int b'^2 of higher degree than the step's own polynomial)."""
+    p = I.burgers(24, 20)[0].with_(u=(0.0, 0.0), b=(0.0, 0.2, 0.3, 0.1))
+    rng = np.random.default_rng(11)
+    o = Oracle(p)
+    f = o.init(1.0 + 0.2 * rng.standard_normal((p.ny, p.nx))) + 0.01 * rng.standard_normal((9, p.ny, p.nx))
+    mu = rng.standard_normal(f.shape)
+    _, _, du_ref = o.adjoint_step_full(f, mu)
+    for prec in (64, 32):
+        s = _solver(p, prec)
+        _, _, du = s.adjoint_step(torch.tensor(f, dtype=s.dtype, device="cuda"),
+                                  torch.tensor(mu, dtype=s.dtype, device="cuda"), with_u=True)
+        du = du.cpu().numpy()
+        s.close()
+        tol = 1e-10 if prec == 64 else 2e-4
+        assert np.abs(du - du_ref).max() <= tol * float(np.abs(du_ref).max()), (prec, du, du_ref)
+
+
 def test_row_marching_and_tiled_fp32_adjoints_agree():
     """On a periodic grid the FP32 adjoint step runs as a row march; the tiled
     kernel computes the same quantities: they agree to FP32 rounding, and both
@@ -124,10 +173,17 @@ def test_checkpointed_gradient_matches_oracle(prec, kind):
     phiN = s.get_phi().double().cpu().numpy()
     gN = torch.tensor(area * (phiN - target), dtype=dt, device="cuda")
     g0, da = s.gradient(torch.tensor(phi0, dtype=dt, device="cuda"), p.steps, gN, checkpoint_every=20)
-    s.close()
     tol = 1e-10 if prec == 64 else 1e-4
     assert _rel(g0.double().cpu().numpy(), gref) <= tol
     assert abs(da - daref) <= tol * abs(daref)
+    # with dJ/du: the same phi0 and alpha gradients, and dJ/du against the oracle's
+    g1, da1, du = s.gradient(torch.tensor(phi0, dtype=dt, device="cuda"), p.steps, gN, checkpoint_every=20,
+                             with_u=True)
+    s.close()
+    _, _, duref, _ = Oracle(p).gradient(phi0, p.steps, lambda phiN: area * (phiN - target), threads=8,
+                                        checkpoint_every=20, with_u=True)
+    assert _rel(g1.double().cpu().numpy(), gref) <= tol and abs(da1 - daref) <= tol * abs(daref)
+    assert np.abs(np.asarray(du) - duref).max() <= tol * float(np.abs(duref).max()), (du, duref)
 
 
 def test_autograd_function_and_checkpoint_length_invariance():
@@ -156,36 +212,40 @@ def test_autograd_function_and_checkpoint_length_invariance():
         assert _rel(g, gref) <= 1e-10 and abs(da - daref) <= 1e-10 * abs(daref)
 
 
-def test_adjoint_workload_512_fp32_against_oracle_and_fd():
+GOLDEN_FD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_adjoint_fd.npz")
+
+
+def test_adjoint_workload_512_fp32_against_stored_fd():
     """The adjoint workload at full size: 512^2 periodic Burgers-type NCDE, 400
     FP32 steps checkpointed every 20; gradient of the L2 misfit to a seeded
-    target w.r.t. phi0 and alpha, against the FP64 oracle's adjoint and, on two
-    random directions, against FP64 central differences (eps = 1e-4)."""
-    p, phi0 = I.burgers(512, steps=400)
-    xc, yc = p.centres()
-    area = np.outer(np.diff(p.yf), np.diff(p.xf))
-    target = I.burgers_phi0(xc, yc, seed=5)
+    target w.r.t. phi0, alpha and u, against stored FP64 central differences of
+    the oracle (eps = 1e-4) along 32 seeded unit directions, in alpha and in
+    u_x, u_y, and against the oracle's own adjoint on a fixed sample of cells."""
+    z = np.load(GOLDEN_FD)
+    n, steps = int(z["n"]), int(z["steps"])
+    p, phi0, target, area = I.adjoint_workload(n, steps)
     s = _solver(p, 32)
     s.init_phi(torch.tensor(phi0, dtype=torch.float32, device="cuda"))
     s.step(p.steps)
     phiN = s.get_phi().double().cpu().numpy()
+    J = 0.5 * float((area * (phiN - target) ** 2).sum())
     gN = torch.tensor(area * (phiN - target), dtype=torch.float32, device="cuda")
-    g0, da = s.gradient(torch.tensor(phi0, dtype=torch.float32, device="cuda"), p.steps, gN, checkpoint_every=20)
+    g0, da, du = s.gradient(torch.tensor(phi0, dtype=torch.float32, device="cuda"), p.steps, gN,
+                            checkpoint_every=20, with_u=True)
     s.close()
     g0 = g0.double().cpu().numpy()
-    o = Oracle(p)
-    gref, daref, _ = o.gradient(phi0, p.steps, lambda ph: area * (ph - target), threads=16, checkpoint_every=20)
-    print(f"adjoint 512^2 x 400 FP32: rel-L2(grad phi0) {_rel(g0, gref):.2e}, rel(dJ/dalpha) {abs(da - daref) / abs(daref):.2e}")
-    assert _rel(g0, gref) <= 1e-4
-    assert abs(da - daref) <= 1e-4 * abs(daref)
-
-    def J(phi0_):
-        ph = o.phi(o.run(o.init(phi0_), p.steps, 16))
-        return 0.5 * float((area * (ph - target) ** 2).sum())
-
-    rng = np.random.default_rng(5)
-    for _ in range(2):
-        d = rng.standard_normal(phi0.shape)
-        d /= np.linalg.norm(d)
-        fd = (J(phi0 + 1e-4 * d) - J(phi0 - 1e-4 * d)) / 2e-4
-        assert abs(fd - float((g0 * d).sum())) <= 1e-3 * abs(fd)
+    dirs = I.unit_directions(phi0.shape, int(z["ndir"]), seed=5)
+    gd = np.array([float((g0 * d).sum()) for d in dirs])
+    rel_dirs = np.abs(gd - z["fd_dirs"]) / np.abs(z["fd_dirs"])
+    rel_alpha = abs(da - float(z["fd_alpha"])) / abs(float(z["fd_alpha"]))
+    rel_u = np.abs(np.asarray(du) - z["fd_u"]) / np.abs(z["fd_u"])
+    samp = g0.reshape(-1)[z["grad_sample_idx"]]
+    rel_samp = _rel(samp, z["grad_sample"])
+    print(f"adjoint {n}^2 x {steps} FP32 vs FP64 FD: max rel over {len(dirs)} directions {rel_dirs.max():.2e}, "
+          f"dJ/dalpha {rel_alpha:.2e}, dJ/du {rel_u.max():.2e}; vs oracle adjoint on {samp.size} cells "
+          f"{rel_samp:.2e}; J {J:.6e} (oracle {float(z['J']):.6e})")
+    assert abs(J - float(z["J"])) <= 1e-5 * abs(float(z["J"]))
+    assert rel_dirs.max() <= 1e-3
+    assert rel_alpha <= 1e-3
+    assert rel_u.max() <= 1e-3
+    assert rel_samp <= 1e-4

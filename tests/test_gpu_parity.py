@@ -269,3 +269,36 @@ def test_expired_bounded_wait_is_reported_without_a_fault():
     t.step(3)
     t.sync()
     t.close()
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_negative_initial_equilibrium_refused_when_checked(prec):
+    """With the equilibrium check on, the Burgers form at c = 1 (f^eq down to -0.24)
+    is refused: on the host path before any device work, on the device path by the
+    next sync.  The same state at c = 10 passes, and with the check off (the default)
+    nothing is tested."""
+    from paper_1906_11036_gb300.dugks import DugksError, Solver
+
+    p, phi0 = I.burgers(40, 33)
+    bad = p.with_(c=1.0, dt=p.dt * 10.0)
+    s = Solver(bad, precision=prec)
+    s.set_feq_check(True)
+    with pytest.raises(DugksError) as ei:
+        s.init_phi(phi0)                                   # host path
+    assert ei.value.status == 2
+    s.init_phi(torch.tensor(phi0, device="cuda"))         # device path
+    with pytest.raises(DugksError) as ei:
+        s.sync()
+    assert ei.value.status == 2
+    s.close()
+    s = Solver(bad, precision=prec)                        # check off: no test
+    s.init_phi(torch.tensor(phi0, device="cuda"))
+    s.sync()
+    s.close()
+    s = Solver(p, precision=prec)
+    s.set_feq_check(True)
+    s.init_phi(phi0)
+    s.init_phi(torch.tensor(phi0, device="cuda"))
+    s.step(3)
+    s.sync()
+    s.close()

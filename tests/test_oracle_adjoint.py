@@ -10,7 +10,9 @@ here independently of its code:
   * the explicit alpha-derivative against central differences in alpha;
   * the gradient of J = 1/2 sum |V| (phi^N - phi_t)^2 over many steps with
     respect to phi0 (random directions) and alpha, against central
-    differences of J (eps = 1e-4, FP64).
+    differences of J (eps = 1e-4, FP64);
+  * d feq / d u and the explicit u-derivative of the step (u of B = u b(phi):
+    the B coefficients of Eq. 2.3), and dJ/du over many steps, the same way.
 """
 import numpy as np
 import pytest
@@ -91,3 +93,60 @@ def test_multi_step_gradient_against_central_differences():
     ea = eps * p.alpha
     fda = (J(phi0, p.alpha + ea) - J(phi0, p.alpha - ea)) / (2 * ea)
     assert abs(fda - galpha) <= 1e-6 * abs(fda)
+
+
+def test_equilibrium_u_derivative_matches_central_differences():
+    """d feq / d u (B = u b(phi), C = u u int b'^2) against central differences of Eq. 2.3 in u."""
+    for name in ("burgers_periodic", "nonuniform_walls", "poly", "xwall", "czero"):
+        p = CASES[name]()
+        o = Oracle(p)
+        for phi in (0.4, 1.0, 1.7):
+            got = o.equilibrium_du(phi)
+            for a in range(2):
+                up, um = list(p.u), list(p.u)
+                up[a] += 1e-6
+                um[a] -= 1e-6
+                fd = (Oracle(p.with_(u=tuple(up))).equilibrium(phi) - Oracle(p.with_(u=tuple(um))).equilibrium(phi)) / 2e-6
+                np.testing.assert_allclose(got[a], fd, rtol=1e-7, atol=1e-9)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_adjoint_step_u_derivative(name):
+    """The explicit u-derivative of one step, contracted with w, against central
+    differences of the forward step in u (cells, faces and ghosts all depend on u)."""
+    p = CASES[name]()
+    o = Oracle(p)
+    rng = np.random.default_rng(abs(hash(name + "u")) % 2 ** 32)
+    f = o.init(1.0 + 0.2 * rng.standard_normal((p.ny, p.nx))) + 0.01 * rng.standard_normal((9, p.ny, p.nx))
+    w = rng.standard_normal(f.shape)
+    _, _, du = o.adjoint_step_full(f, w)
+    for a in range(2):
+        up, um = list(p.u), list(p.u)
+        up[a] += 1e-6
+        um[a] -= 1e-6
+        fa = Oracle(p.with_(u=tuple(up))).step(f)
+        fb = Oracle(p.with_(u=tuple(um))).step(f)
+        ju = float((((fa - fb) / 2e-6) * w).sum())
+        assert abs(ju - du[a]) <= 1e-6 * max(abs(ju), 1.0), (a, ju, du[a])
+
+
+def test_multi_step_u_gradient_against_central_differences():
+    """dJ/du of the reduced adjoint workload (the initial f^0 = feq(phi0) depends on u
+    as well as every step) against central differences of J in u_x and u_y."""
+    p, phi0 = I.burgers(16, 12, steps=30)
+    xc, yc = p.centres()
+    area = np.outer(np.diff(p.yf), np.diff(p.xf))
+    target = I.burgers_phi0(xc, yc, seed=5)
+
+    def J(q):
+        o_ = Oracle(q)
+        phiN = o_.phi(o_.run(o_.init(phi0), q.steps))
+        return 0.5 * float((area * (phiN - target) ** 2).sum())
+
+    _, _, du, _ = Oracle(p).gradient(phi0, p.steps, lambda phiN: area * (phiN - target), with_u=True)
+    for a in range(2):
+        up, um = list(p.u), list(p.u)
+        up[a] += 1e-4
+        um[a] -= 1e-4
+        fd = (J(p.with_(u=tuple(up))) - J(p.with_(u=tuple(um)))) / 2e-4
+        assert abs(fd - du[a]) <= 1e-6 * abs(fd), (a, fd, du[a])

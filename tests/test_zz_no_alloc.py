@@ -7,8 +7,8 @@ that must avoid the implicit synchronisation of cudaMalloc/cudaFree.  Its
 partial sums live in a fixed array inside the library, shared by all calls,
 so two calls in a row on different grids must each match the reference.
 
-This file is collected last so that a failure here stops a run only after
-every other test has run.
+The file name sorts after every other test file, so pytest collects it last:
+a run with -x that stops at a failure here has already run all other tests.
 """
 import ctypes
 
