@@ -20,7 +20,11 @@ step kernel, i.e. one pass of the whole method over the grid.
 * cpu_baseline (rank 0, N = 1): the FP64 CPU oracle on a bounded sample, on
                all host cores and on one, with the CPU model.
 * batched    : the 256-instance workload, 1000 steps as 20 graph replays,
-               against the single-instance step's rate, bit-identity checked.
+               against the single-instance step's rate, bit-identity checked,
+               16 sampled instances against stored FP64 oracle runs.
+* parity     : the single-instance workloads run for their configured steps
+               against stored FP64 oracle runs (tests/golden); the adjoint
+               gradient against stored FP64 central differences.
 
 --impl reference times that oracle as it stands on the host cores.
 Multi-GPU runs are independent replicas (one per rank, weak scaling).
@@ -256,20 +260,36 @@ def adjoint_ratio(args):
     ev[3].synchronize()
     t_fwd = ev[0].elapsed_time(ev[1]) / 200
     t_adj = ev[2].elapsed_time(ev[3]) / 50
+    # the whole gradient of the misfit J = 1/2 sum |V| (phi^N - target)^2 w.r.t. phi0, alpha and u
+    _, _, target, area = I.adjoint_workload(512, p.steps)
     s.init_phi(phi0_t)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     s.step(p.steps)
-    phiN = s.get_phi()
+    phiN = s.get_phi().double().cpu().numpy()
     torch.cuda.synchronize()
     t_run = time.perf_counter() - t0
+    gN = torch.tensor(area * (phiN - target), dtype=torch.float32, device="cuda")
     t0 = time.perf_counter()
-    s.gradient(phi0_t, p.steps, phiN, checkpoint_every=20)
+    g0, dalpha, du = s.gradient(phi0_t, p.steps, gN, checkpoint_every=20, with_u=True)
     t_grad = time.perf_counter() - t0
+    g0 = g0.double().cpu().numpy()
     s.close()
-    out = {"workload": "burgers_512x512, 400 FP32 steps, checkpoint every 20",
+    out = {"workload": "burgers_512x512, 400 FP32 steps, checkpoint every 20; gradient w.r.t. phi0, alpha, u",
            "forward_ms_per_step": t_fwd, "adjoint_ms_per_step": t_adj, "adjoint_step_ratio": t_adj / t_fwd,
            "forward_run_s": t_run, "gradient_s": t_grad, "gradient_to_forward_ratio": t_grad / t_run}
+    path = os.path.join(GOLDEN, "oracle_adjoint_fd.npz")
+    if os.path.exists(path):
+        # against FP64 central differences of the oracle (eps = 1e-4) stored by make_adjoint_fd.py
+        z = np.load(path)
+        dirs = I.unit_directions(phi0.shape, int(z["ndir"]), seed=5)
+        gd = np.array([float((g0 * d).sum()) for d in dirs])
+        out["vs_fp64_fd"] = {
+            "directions": int(z["ndir"]), "eps": float(z["eps"]),
+            "max_rel_err_dirs": float(np.max(np.abs(gd - z["fd_dirs"]) / np.abs(z["fd_dirs"]))),
+            "rel_err_dalpha": abs(dalpha - float(z["fd_alpha"])) / abs(float(z["fd_alpha"])),
+            "max_rel_err_du": float(np.max(np.abs(np.asarray(du) - z["fd_u"]) / np.abs(z["fd_u"]))),
+            "rel_l2_vs_oracle_adjoint_sampled": _rel_l2(g0.reshape(-1)[z["grad_sample_idx"]], z["grad_sample"])}
     # the same step on 2048^2 (state, mu and lambda larger than L2): roofline of the adjoint step,
     # algorithmic bytes = read ftilde^n and mu, write lambda = 3 x 36 B per cell in FP32
     p, phi0 = I.burgers(2048, steps=20)
@@ -342,6 +362,18 @@ def batched_run(single_value: float | None, steps: int = 1000, check: int = 8):
         torch.cuda.synchronize()
         same += int(torch.equal(fb, fs))
         s.close()
+    # the 16 sampled instances against the FP64 oracle's runs stored by make_batched_oracle.py
+    vs_oracle = None
+    path = os.path.join(GOLDEN, "oracle_batched16.npz")
+    if os.path.exists(path) and steps == 1000:
+        z = np.load(path)
+        errs = []
+        for i in (int(v) for v in z["ids"]):
+            phi_t = b.get_phi(i)
+            b.sync()  # the copy runs on the batch's stream
+            phi = phi_t.double().cpu().numpy().reshape(-1)
+            errs.append(_rel_l2(phi[z[f"sample_{i}"]], z[f"phi_{i}"]))
+        vs_oracle = {"instances": len(errs), "max_rel_l2": max(errs), "median_rel_l2": float(np.median(errs))}
     b.close()
     v_b = cells * Q * steps / t_batch
     peak, peak_kind = measured_peak()
@@ -350,6 +382,8 @@ def batched_run(single_value: float | None, steps: int = 1000, check: int = 8):
            "ms_per_step": 1e3 * t_batch / steps, "tile_rows": rows,
            "roofline_frac": v_b * 8 / 1e9 / peak, "peak_kind": peak_kind,
            "bit_identical_to_single_instance": f"{same}/{len(picks)} instances checked"}
+    if vs_oracle is not None:
+        out["vs_fp64_oracle"] = vs_oracle
     if single_value:
         out["single_instance_value"] = single_value
         out["batched_to_single_instance"] = v_b / single_value
@@ -430,6 +464,47 @@ def three_d(n: int = 256, steps: int = 20):
     return out
 
 
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden")
+
+
+def _rel_l2(a, b) -> float:
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def parity_vs_stored_oracle():
+    """Error of the GPU path against the FP64 oracle on the full-size, full-length
+    single-instance workloads: each is run from its initial field for its
+    configured steps and phi is compared, at the stored sample cells, with the
+    oracle's run stored under tests/golden (written by make_oracle_runs.py there,
+    which calls only the oracle): relative L2 over the samples and the relative
+    change of the mass against the oracle's."""
+    import torch
+
+    from paper_1906_11036_gb300 import inputs as I
+    from paper_1906_11036_gb300.dugks import Solver
+
+    out = {}
+    for name, precs in (("gaussian_hill", (64, 32)), ("burgers", (32,)), ("nonuniform", (32,))):
+        path = os.path.join(GOLDEN, f"oracle_{name}.npz")
+        if not os.path.exists(path):
+            out[name] = "no stored oracle run"
+            continue
+        g = np.load(path)
+        p, phi0 = I.PRESETS[name]()
+        for prec in precs:
+            s = Solver(p, precision=prec)
+            s.init_phi(torch.tensor(phi0, dtype=s.dtype, device="cuda"))
+            s.step(p.steps)
+            phi, m = s.get_phi(mass=True)
+            s.close()
+            got = phi.double().cpu().numpy().reshape(-1)[g["sample"]]
+            out[f"{name}_fp{prec}"] = {"workload": f"{p.name}, {p.steps} steps, FP{prec}",
+                                       "rel_l2_vs_oracle": _rel_l2(got, g["phi"]), "samples": int(got.size),
+                                       "mass_rel_vs_oracle": abs(m - float(g["mass"])) / abs(float(g["mass"]))}
+    return out
+
+
 def max_over_ranks(times, world: int, device="cpu"):
     """Element-wise maximum of per-rank timings over all ranks (the slowest
     replica sets the job's time); identity for a single process."""
@@ -470,6 +545,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-sources", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--no-parity", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -548,6 +624,7 @@ def main():
     batched = None  # after the main line's value is known
     sources = sources_vs_plain() if (world == 1 and not args.no_sources) else None
     d3 = three_d() if (world == 1 and not args.no_3d) else None
+    parity = parity_vs_stored_oracle() if (world == 1 and not args.no_parity) else None
 
     t_dev, t_e2e = max_over_ranks([t_dev, t_e2e], world, device="cuda")
     if rank != 0:
@@ -589,6 +666,8 @@ def main():
         line["sources"] = sources
     if d3 is not None:
         line["three_d"] = d3
+    if parity is not None:
+        line["parity"] = parity
     if world == 1 and not args.no_cpu_baseline:
         import oracle
 

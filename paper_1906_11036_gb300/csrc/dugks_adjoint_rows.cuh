@@ -32,11 +32,13 @@ struct AdjRowLayout {
     static size_t bytes(int stages) { return size_t(stages) * (STAGE_BYTES + 8) + 128; }
 };
 
-template <int NC>
+// S: ring stages (a power of two keeps the stage index a mask); WU: also form the u-derivative
+template <int NC, int S, bool WU>
 __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
     adj_rows_kernel(const __grid_constant__ CUtensorMap tf, const __grid_constant__ CUtensorMap tmu,
                     const StepArgs<float, NC> a, const Consts<float, NC> k, const AdjConsts<float, NC> ka,
-                    const AdjArgs<float> g, const int seg_rows, const int S) {
+                    const AdjArgs<float> g, const int seg_rows) {
+    static_assert(S >= 3, "the ring holds rows n - 2 .. n");
     using L = AdjRowLayout;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* stages = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -54,7 +56,7 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
     const bool from_smem = j >= 0 && j < nx;    // else read the periodic image from global memory
     const bool owner = lane >= 2 && lane <= 29 && j < nx;
     const int R = y1 - y0 + 4;                  // rows y0-2 .. y1+1
-    auto wrow = [&](int r) { return ((r % ny) + ny) % ny; };
+    auto wrow = [&](int r) { return r < 0 ? r + ny : (r >= ny ? r - ny : r); };  // r in [-2, ny + 1], ny >= 4
 
     // column metrics of this lane's cell and of its east face
     const FaceM<float> fE = a.fx[jw + 2];
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
             }
             if (owner && q >= y0 && q < y1) {
                 djdl += double(sdl);
-                if (g.want_u) {  // Eq. 2.22: b_f feq(phi_b) of the crossing velocities
+                if (WU) {  // Eq. 2.22: b_f feq(phi_b) of the crossing velocities
                     float w[Q];
 #pragma unroll
                     for (int i = 0; i < Q; ++i) w[i] = ka.b_f * gv[i];
@@ -213,7 +215,7 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
             }
             if (owner && n < y1) {
                 djdl += double(sdl);
-                if (g.want_u) {
+                if (WU) {
                     float w[Q];
 #pragma unroll
                     for (int i = 0; i < Q; ++i) w[i] = ka.b_f * gv[i];
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
             }
             if (owner) {
                 djdl += double(s);
-                if (g.want_u) {  // Eqs. 2.21 and 2.13: b_bp feq(phi) in P and b_tp feq(phi) in ftilde^+
+                if (WU) {  // Eqs. 2.21 and 2.13: b_bp feq(phi) in P and b_tp feq(phi) in ftilde^+
                     float w[Q];
 #pragma unroll
                     for (int i = 0; i < Q; ++i) w[i] = fmaf(ka.b_bp, Ba[i], ka.b_tp * mu[i]);

@@ -755,8 +755,12 @@ cudaError_t launch_adjoint_rows(dugks_ctx* ctx, const StepArgs<float, NC>& a, co
             if ((e = cudaMemsetAsync(g.partial + q * cap + strips * nseg, 0,
                                      sizeof(double) * size_t(cap - strips * nseg), ctx->stream)) != cudaSuccess)
                 return e;
-    adj_rows_kernel<NC><<<dim3(strips, unsigned(nseg)), 32, L::bytes(kAdjRowStages), ctx->stream>>>(
-        tm[0], tm[1], a, k, ka, g, seg, kAdjRowStages);
+    if (g.want_u)
+        adj_rows_kernel<NC, kAdjRowStages, true><<<dim3(strips, unsigned(nseg)), 32, L::bytes(kAdjRowStages),
+                                                   ctx->stream>>>(tm[0], tm[1], a, k, ka, g, seg);
+    else
+        adj_rows_kernel<NC, kAdjRowStages, false><<<dim3(strips, unsigned(nseg)), 32, L::bytes(kAdjRowStages),
+                                                    ctx->stream>>>(tm[0], tm[1], a, k, ka, g, seg);
     return cudaGetLastError();
 }
 
