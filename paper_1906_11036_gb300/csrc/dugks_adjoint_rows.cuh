@@ -1,26 +1,39 @@
 // dugks_adjoint_rows.cuh -- the adjoint of one FP32 DUGKS step (reverse mode
-// of the step of Section 2, arXiv:1906.11036) as a row march, for grids that
-// are periodic on both axes.
+// of the step of Section 2, arXiv:1906.11036) as a row march on velocity
+// pairs, for grids that are periodic on both axes.
 //
 // The arithmetic is that of adj_tile_kernel (same face adjoints, same
 // transposed weights), reorganised like the forward step: one warp owns a
 // strip of 28 columns (lanes 2..29; lanes 0, 1, 30, 31 are halo columns, two
 // on each side because a y-face adjoint needs the x-slope of its cell) and
 // marches up a row segment.  Rows of ftilde^n and mu arrive by TMA into a
-// private ring of stages.  Instead of gathering the adjoint of P from stored
-// face adjoints, every face scatters its contributions as soon as it is
-// formed: into three rolling accumulators Pb for the rows n-2, n-1, n (this
-// lane's and, through a shuffle, the neighbour lane's).  When the new row n has
-// been processed, row n-2 has received every contribution (x-faces of rows
-// n-3..n-1, y-faces below and above it) and is finished (Eqs. 2.21, 2.13
-// transposed), and its stage is refilled.
+// private ring of stages.  Every face scatters its contributions to the
+// adjoint of P as soon as it is formed, into three rolling accumulators for
+// the rows n-2, n-1, n.  When the new row n has been processed, row n-2 has
+// received every contribution (x-faces of rows n-3..n-1, y-faces below and
+// above it) and is finished (Eqs. 2.21, 2.13 transposed), and its stage is
+// refilled.
+//
+// The eight moving velocities are packed as the opposite pairs (1,3), (2,4),
+// (5,7), (6,8) on the packed FP32 instructions; the second velocity of a pair
+// has the opposite direction, so a per-velocity weight is a pair (a + s b,
+// a - s b) with s the direction sign of the first.  Work per face:
+//   * phi_b from the moments phi, Mx, My of P of the two cells (the
+//     reconstruction is linear in P), so fbar is formed only for the
+//     velocities that cross the face;
+//   * an x-face is the sum of a half from its left cell and a half from its
+//     right cell, each formed by the lane that owns the cell (one shuffle per
+//     crossing value); the flux adjoint of the face returns to the right lane
+//     by one shuffle per crossing value, and each lane applies its own weights;
+//   * a y-face's transposed x-slope weights differ between its two rows only
+//     by the face's (tl, tr), so they cross lanes once.
 #pragma once
 #include "dugks_adjoint.cuh"
 
 namespace dugks {
 
 #ifndef DUGKS_ADJ_ROWS_MIN_WARPS
-#define DUGKS_ADJ_ROWS_MIN_WARPS 16  // 126 registers, no spills; 4 stages keep 16 warps in shared memory
+#define DUGKS_ADJ_ROWS_MIN_WARPS 16
 #endif
 
 struct AdjRowLayout {
@@ -32,13 +45,76 @@ struct AdjRowLayout {
     static size_t bytes(int stages) { return size_t(stages) * (STAGE_BYTES + 8) + 128; }
 };
 
+// Constants of the FP32 adjoint on velocity pairs (pair q = (PA(q), PB(q)))
+template <int NC>
+struct AdjConstsP {
+    float2 hbp[4][NC];          // b_bp (feq_PA, feq_PB) in powers of phi: P = a_bp ft + hbp(phi) (Eq. 2.21)
+    float2 fq[4][NC];           // (feq_PA, feq_PB)
+    float2 dq[4][NC];           // (feq_PA', feq_PB') (the top coefficient is zero)
+    float2 Au[2][4], Bu[2][4];  // d feq / d u_a = Au b(phi) + Bu Cint(phi) per pair (u of B = u b)
+    float Au0[2], Bu0[2];       // the rest velocity's
+    float bpoly[NC], cpoly[NC];
+    float a_bp, b_bp, a_tp, b_tp, a_f, b_f;
+    float da_bp, db_bp, da_tp, db_tp, da_f, db_f;  // d/dlambda of the weights
+    float hc;
+};
+
+template <int NC>
+__device__ __forceinline__ F2 ap_hbp(const AdjConstsP<NC>& k, int q, F2 x) {
+    F2 s{k.hbp[q][NC - 1]};
+#pragma unroll
+    for (int m = NC - 2; m >= 0; --m) s = fma2(s, x, F2{k.hbp[q][m]});
+    return s;
+}
+template <int NC>
+__device__ __forceinline__ F2 ap_feq(const AdjConstsP<NC>& k, int q, F2 x) {
+    F2 s{k.fq[q][NC - 1]};
+#pragma unroll
+    for (int m = NC - 2; m >= 0; --m) s = fma2(s, x, F2{k.fq[q][m]});
+    return s;
+}
+template <int NC>
+__device__ __forceinline__ F2 ap_dfeq(const AdjConstsP<NC>& k, int q, F2 x) {
+    F2 s{k.dq[q][NC - 2]};
+#pragma unroll
+    for (int m = NC - 3; m >= 0; --m) s = fma2(s, x, F2{k.dq[q][m]});
+    return s;
+}
+__device__ __forceinline__ float hsum(F2 a) { return a.v.x + a.v.y; }
+__device__ __forceinline__ float hdot(F2 a, F2 b) { return fmaf(a.v.x, b.v.x, a.v.y * b.v.y); }
+
+// du[a] += b(phi) sum_q w_q . Au[a][q] + Cint(phi) sum_q w_q . Bu[a][q] over the pairs in
+// qmask (bit q), plus the rest velocity weighted by wz
+template <int NC>
+__device__ __forceinline__ void ap_add_du(const AdjConstsP<NC>& k, float phi, const F2 (&w)[4], unsigned qmask,
+                                          float wz, double (&du)[2]) {
+    float bv = k.bpoly[NC - 1], cv = k.cpoly[NC - 1];
+#pragma unroll
+    for (int m = NC - 2; m >= 0; --m) {
+        bv = fmaf(bv, phi, k.bpoly[m]);
+        cv = fmaf(cv, phi, k.cpoly[m]);
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        F2 sa = f2(0.f), sb = f2(0.f);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (qmask & (1u << q)) {
+                sa = fma2(w[q], F2{k.Au[a][q]}, sa);
+                sb = fma2(w[q], F2{k.Bu[a][q]}, sb);
+            }
+        const float ta = fmaf(wz, k.Au0[a], hsum(sa)), tb = fmaf(wz, k.Bu0[a], hsum(sb));
+        du[a] += double(fmaf(bv, ta, cv * tb));
+    }
+}
+
 // S: ring stages (a power of two keeps the stage index a mask); WU: also form the u-derivative
 template <int NC, int S, bool WU>
 __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
     adj_rows_kernel(const __grid_constant__ CUtensorMap tf, const __grid_constant__ CUtensorMap tmu,
-                    const StepArgs<float, NC> a, const Consts<float, NC> k, const AdjConsts<float, NC> ka,
-                    const AdjArgs<float> g, const int seg_rows) {
-    static_assert(S >= 3, "the ring holds rows n - 2 .. n");
+                    const StepArgs<float, NC> a, const AdjConstsP<NC> k, const AdjArgs<float> g,
+                    const int seg_rows) {
+    static_assert(S >= 3 && (S & (S - 1)) == 0, "the ring holds rows n - 2 .. n; a power of two");
     using L = AdjRowLayout;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* stages = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -58,9 +134,11 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
     const int R = y1 - y0 + 4;                  // rows y0-2 .. y1+1
     auto wrow = [&](int r) { return r < 0 ? r + ny : (r >= ny ? r - ny : r); };  // r in [-2, ny + 1], ny >= 4
 
-    // column metrics of this lane's cell and of its east face
-    const FaceM<float> fE = a.fx[jw + 2];
-    const CellM<float> cxj = a.cx[jw + 1], cxe = a.cx[((jw + 1) % nx) + 1];
+    // this lane's cell: its east face (it is the left cell) and its west face (the right cell)
+    const FaceM<float> fE = a.fx[jw + 2], fW = a.fx[jw + 1];
+    const CellM<float> cxj = a.cx[jw + 1];
+    const float hx_e = k.hc * fE.tl, hx_w = k.hc * fW.tr;  // weights of this cell's y-slope at the two faces
+    const float mhig = -k.hc * cxj.ig;                     // x-slope factor of this cell at its y-faces
 
     if (lane == 0) {
         for (int q = 0; q < S; ++q) mbar_init(&bars[q], 1);
@@ -68,202 +146,268 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
     }
     __syncwarp();
     auto issue = [&](int t) {  // row y0 - 2 + t into stage t % S
-        const int st = t % S, row = wrow(y0 - 2 + t);
+        const int st = t & (S - 1), row = wrow(y0 - 2 + t);
         mbar_arrive_expect_tx(&bars[st], uint32_t(2 * L::BOX_BYTES));
         tma_load_3d(stages + size_t(st) * L::STAGE_BYTES, &tf, &bars[st], xs, row, 0);
         tma_load_3d(stages + size_t(st) * L::STAGE_BYTES + L::MU_OFF, &tmu, &bars[st], xs, row, 0);
     };
     if (lane == 0)
         for (int t = 0; t < min(S, R); ++t) issue(t);
-    // row r's ftilde (which = 0) or mu (1): stage of row r, or the periodic image in global memory
-    auto row_vals = [&](int r, int which, float (&v)[Q]) {
+    // row r's ftilde (which = 0) or mu (1) as pairs: stage of row r, or the periodic image in global memory
+    auto row_v9 = [&](int r, int which, V9& v) {
         const int t = r - (y0 - 2);
         if (from_smem) {
-            const float* st = reinterpret_cast<const float*>(stages + size_t(t % S) * L::STAGE_BYTES +
+            const float* st = reinterpret_cast<const float*>(stages + size_t(t & (S - 1)) * L::STAGE_BYTES +
                                                              (which ? L::MU_OFF : 0)) + (j - xs);
+            v.z = st[0];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) v[i] = st[i * L::BOXW];
+            for (int q = 0; q < 4; ++q) v.p[q] = f2(st[PA(q) * L::BOXW], st[PB(q) * L::BOXW]);
         } else {
             const float* src = (which ? g.mu : g.f) + (long long)wrow(r) * nx + jw;
+            v.z = src[0];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) v[i] = src[i * cplane];
+            for (int q = 0; q < 4; ++q) v.p[q] = f2(src[PA(q) * cplane], src[PB(q) * cplane]);
         }
     };
 
-    float Pm2[Q], Pm1[Q], Pn[Q];  // P = fbar^+ of rows n-2, n-1, n (this lane's column)
-    float Ba[Q], Bb[Q], Bc[Q];    // adjoint of P accumulated for rows n-2, n-1, n
+    V9 Pm2, Pm1, Pn;  // P = fbar^+ of rows n-2, n-1, n (this lane's column)
+    V9 Ba, Bb, Bc;    // adjoint of P accumulated for rows n-2, n-1, n
 #pragma unroll
-    for (int i = 0; i < Q; ++i) Pm2[i] = Pm1[i] = Pn[i] = Ba[i] = Bb[i] = Bc[i] = 0.f;
+    for (int q = 0; q < 4; ++q) Pm2.p[q] = Pm1.p[q] = Ba.p[q] = Bb.p[q] = Bc.p[q] = f2(0.f);
+    Pm2.z = Pm1.z = Ba.z = Bb.z = Bc.z = 0.f;
+    float ph1 = 0.f, mx1 = 0.f, my1 = 0.f, my2 = 0.f;  // moments: phi, Mx of row n-1; My of rows n-1, n-2
+    F2 gx1[2] = {f2(0.f), f2(0.f)};                     // x-slopes of P of row n-1 (pairs 2, 3)
+    float gmx1 = 0.f;                                   // x-slope of Mx of row n-1
     double djdl = 0.0, du[2] = {0.0, 0.0};
     bool failed = false;
     int t = 0;
     for (; t < R; ++t) {
         const int n = y0 - 2 + t;
-        const bool ok = mbar_wait_bounded(&bars[t % S], uint32_t((t / S) & 1), 2000000000ull);
+        const bool ok = mbar_wait_bounded(&bars[t & (S - 1)], uint32_t((t / S) & 1), 2000000000ull);
         if (__any_sync(0xffffffffu, !ok)) { failed = true; break; }
-        // P of the new row (Eq. 2.21; periodic, no ghosts)
+        // P of the new row (Eq. 2.21; periodic, no ghosts), its moments and x-slopes
+        float phn;
         {
-            float ft[Q], fe[Q];
-            row_vals(n, 0, ft);
-            float phi = 0.f;
+            V9 F;
+            row_v9(n, 0, F);
+            phn = vsum(F);
+            const F2 x2 = f2(phn);
+            F2 hs = f2(0.f);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) phi += ft[i];
-            feq_all(k, phi, fe);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) Pn[i] = fmaf(k.a_bp, ft[i], k.b_bp * fe[i]);
+            for (int q = 0; q < 4; ++q) {
+                const F2 h = ap_hbp(k, q, x2);
+                Pn.p[q] = fma2(f2(k.a_bp), F.p[q], h);
+                hs = hs + h;
+            }
+            Pn.z = fmaf(k.a_bp, F.z, fmaf(k.b_bp, phn, -hsum(hs)));  // rest velocity: zeroth moment
         }
-        float mq[Q];  // mu of row n - 1
-        if (n >= y0) row_vals(n - 1, 1, mq);
+        const float d0 = Pn.p[0].v.x - Pn.p[0].v.y, d1 = Pn.p[1].v.x - Pn.p[1].v.y;
+        const float d2 = Pn.p[2].v.x - Pn.p[2].v.y, d3 = Pn.p[3].v.x - Pn.p[3].v.y;
+        const float mxn = (d0 + d2) - d3, myn = (d1 + d2) + d3;  // e_x, e_y of the pairs' first velocities
+        const F2 igx2 = f2(cxj.ig);
+        const F2 gxn[2] = {(shfl_dn2(Pn.p[2]) - shfl_up2(Pn.p[2])) * igx2,
+                           (shfl_dn2(Pn.p[3]) - shfl_up2(Pn.p[3])) * igx2};
+        const float gmxn = (__shfl_down_sync(0xffffffffu, mxn, 1) - __shfl_up_sync(0xffffffffu, mxn, 1)) * cxj.ig;
+
+        V9 mq;  // mu of row n - 1
         if (n >= y0) {
-            // x-face east of this lane's cell in row q = n - 1 (faces of rows y0-1 .. y1)
-            const int q = n - 1;
-            const float igq = a.cy[wrow(q) + 1].ig;
-            float Gy[Q], fb[Q], A[Q];
+            // x-faces of row n - 1 (rows y0-1 .. y1); crossing pairs 0, 2, 3 in slots 0, 1, 2
+            row_v9(n - 1, 1, mq);
+            const float igq = a.cy[wrow(n - 1) + 1].ig;
+            F2 fb[3];
+            float phib;
+            {
+                // this lane's half of its east face (left cell) and of its west face (right cell)
+                F2 hl[3], hr[3];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) Gy[i] = EY(i) != 0 ? (Pn[i] - Pm2[i]) * igq : 0.f;
-            float phib = 0.f;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const float en = float(EX(i)), et = float(EY(i));
-                const float PR = __shfl_down_sync(0xffffffffu, Pm1[i], 1);
-                const float GR = EY(i) != 0 ? __shfl_down_sync(0xffffffffu, Gy[i], 1) : 0.f;
-                fb[i] = ((1.f - fE.w) + en * fE.hcd) * Pm1[i] - et * k.hc * fE.tl * Gy[i] +
-                        (fE.w - en * fE.hcd) * PR - et * k.hc * fE.tr * GR;
-                phib += fb[i];
-            }
-            float gv[Q], fe[Q];
-            float sg = 0.f;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                gv[i] = 0.f;
-                fe[i] = 0.f;
-                if (EX(i) != 0) {
-                    const float muR = __shfl_down_sync(0xffffffffu, mq[i], 1);
-                    gv[i] = float(EX(i)) * (cxe.r * muR - cxj.r * mq[i]);
-                    fe[i] = feq_i(k, i, phib);
-                    sg += gv[i] * dfeq_i(ka, i, phib);
+                for (int s = 0; s < 3; ++s) {
+                    const int q = s == 0 ? 0 : s + 1;
+                    hl[s] = sgn2(1.f - fE.w, fE.hcd, QX(q)) * Pm1.p[q];
+                    hr[s] = sgn2(fW.w, -fW.hcd, QX(q)) * Pm1.p[q];
+                    if (q != 0) {  // e_y = (+1, -1): the tangential term -e_y hc t G
+                        const F2 gy = (Pn.p[q] - Pm2.p[q]) * f2(igq);
+                        hl[s] = fma2(f2(-hx_e, hx_e), gy, hl[s]);
+                        hr[s] = fma2(f2(-hx_w, hx_w), gy, hr[s]);
+                    }
                 }
-            }
-            float sdl = 0.f;
+                const float gmy = (myn - my2) * igq;  // y-slope of My
+                const float pl = fmaf(1.f - fE.w, ph1, fmaf(fE.hcd, mx1, -hx_e * gmy));
+                const float pr = fmaf(fW.w, ph1, -fmaf(fW.hcd, mx1, hx_w * gmy));
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                A[i] = fmaf(ka.a_f, gv[i], ka.b_f * sg);
-                if (EX(i) != 0) sdl += gv[i] * fmaf(ka.da_f, fb[i], ka.db_f * fe[i]);
+                for (int s = 0; s < 3; ++s) fb[s] = hl[s] + shfl_dn2(hr[s]);
+                phib = pl + __shfl_down_sync(0xffffffffu, pr, 1);
             }
-            if (owner && q >= y0 && q < y1) {
-                djdl += double(sdl);
+            // adjoint of the face's f (Eq. 2.12 flux): e_x (r_R mu_R - r_L mu_L)
+            F2 gv[3];
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                const int q = s == 0 ? 0 : s + 1;
+                const F2 rm = mq.p[q] * f2(float(QX(q)) * cxj.r, -float(QX(q)) * cxj.r);
+                gv[s] = shfl_dn2(rm) - rm;
+            }
+            // Eq. 2.22 transposed: A = a_f gv + b_f sum_m gv_m feq_m'(phi_b)
+            const F2 pb2 = f2(phib);
+            F2 sgp = f2(0.f), sdp = f2(0.f);
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                const int q = s == 0 ? 0 : s + 1;
+                const F2 fe = ap_feq(k, q, pb2);
+                sgp = fma2(gv[s], ap_dfeq(k, q, pb2), sgp);
+                sdp = fma2(gv[s], fma2(f2(k.da_f), fb[s], f2(k.db_f) * fe), sdp);
+            }
+            const float sg = hsum(sgp), bsg = k.b_f * sg;
+            if (owner && n - 1 >= y0 && n - 1 < y1) {
+                djdl += double(hsum(sdp));
                 if (WU) {  // Eq. 2.22: b_f feq(phi_b) of the crossing velocities
-                    float w[Q];
+                    F2 w[4];
+                    w[1] = f2(0.f);
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) w[i] = ka.b_f * gv[i];
-                    add_du(ka, phib, w, xmask(), du);
+                    for (int s = 0; s < 3; ++s) w[s == 0 ? 0 : s + 1] = f2(k.b_f) * gv[s];
+                    ap_add_du(k, phib, w, 0xDu, 0.f, du);
                 }
             }
-            // scatter: normal weights into row q of this lane (L) and of the east lane (R);
-            // tangential slope weights into rows q + 1 and q - 1 of both
+            // the face's A at its right cell (the lane to the east)
+            const float bsgW = k.b_f * __shfl_up_sync(0xffffffffu, sg, 1);
+            F2 A[3], AW[3];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                Bb[i] = fmaf((1.f - fE.w) + float(EX(i)) * fE.hcd, A[i], Bb[i]);
-                const float rs = __shfl_up_sync(0xffffffffu, (fE.w - float(EX(i)) * fE.hcd) * A[i], 1);
-                Bb[i] += rs;
-                if (EY(i) != 0) {
-                    const float c = -float(EY(i)) * k.hc * igq * A[i];
-                    const float tL = c * fE.tl;
-                    const float tR = __shfl_up_sync(0xffffffffu, c * fE.tr, 1);
-                    Bc[i] += tL + tR;
-                    Ba[i] -= tL + tR;
-                }
+            for (int s = 0; s < 3; ++s) {
+                A[s] = fma2(f2(k.a_f), gv[s], f2(bsg));
+                AW[s] = fma2(f2(k.a_f), shfl_up2(gv[s]), f2(bsgW));
+            }
+            // normal weights into row n - 1; pair 1 and the rest velocity do not cross (A = b_f sg)
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                const int q = s == 0 ? 0 : s + 1;
+                Bb.p[q] = fma2(sgn2(1.f - fE.w, fE.hcd, QX(q)), A[s], Bb.p[q]);
+                Bb.p[q] = fma2(sgn2(fW.w, -fW.hcd, QX(q)), AW[s], Bb.p[q]);
+            }
+            const float nz = fmaf(1.f - fE.w, bsg, fW.w * bsgW);
+            Bb.p[1] = Bb.p[1] + f2(nz);
+            Bb.z += nz;
+            // this cell's y-slope (rows n and n - 2) at both faces: pairs 1, 2, 3 (e_y = +1, -1)
+            const float mig = -igq;
+            {
+                const float tt = mig * fmaf(hx_e, bsg, hx_w * bsgW);
+                const F2 t1 = f2(tt, -tt);
+                Bc.p[1] = Bc.p[1] + t1;
+                Ba.p[1] = Ba.p[1] - t1;
+            }
+#pragma unroll
+            for (int s = 1; s < 3; ++s) {
+                const F2 T = fma2(f2(hx_e), A[s], f2(hx_w) * AW[s]) * f2(mig, -mig);
+                Bc.p[s + 1] = Bc.p[s + 1] + T;
+                Ba.p[s + 1] = Ba.p[s + 1] - T;
             }
         }
         if (n >= y0 && n <= y1) {
-            // y-face between rows n - 1 and n of this lane's column (faces y0 .. y1)
+            // y-face between rows n - 1 and n of this lane's column (faces y0 .. y1); crossing
+            // pairs 1, 2, 3 (e_y = +1 for the first velocity) in slots 0, 1, 2
             const FaceM<float> m = a.fy[n + 1];
-            const float ig = cxj.ig;
-            float mn[Q], fb[Q], A[Q];
-            row_vals(n, 1, mn);
-            float phib = 0.f;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const float en = float(EY(i)), et = float(EX(i));
-                float GL = 0.f, GR = 0.f;  // x-slopes of the cells below and above the face
-                if (EX(i) != 0) {
-                    GL = (__shfl_down_sync(0xffffffffu, Pm1[i], 1) - __shfl_up_sync(0xffffffffu, Pm1[i], 1)) * ig;
-                    GR = (__shfl_down_sync(0xffffffffu, Pn[i], 1) - __shfl_up_sync(0xffffffffu, Pn[i], 1)) * ig;
-                }
-                fb[i] = ((1.f - m.w) + en * m.hcd) * Pm1[i] - et * k.hc * m.tl * GL + (m.w - en * m.hcd) * Pn[i] -
-                        et * k.hc * m.tr * GR;
-                phib += fb[i];
-            }
+            V9 mn;
+            row_v9(n, 1, mn);
             const float rL = a.cy[wrow(n - 1) + 1].r, rR = a.cy[wrow(n) + 1].r;
-            float gv[Q], fe[Q];
-            float sg = 0.f;
+            F2 fb[3], gv[3];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                gv[i] = 0.f;
-                fe[i] = 0.f;
-                if (EY(i) != 0) {
-                    gv[i] = float(EY(i)) * (rR * mn[i] - rL * mq[i]);
-                    fe[i] = feq_i(k, i, phib);
-                    sg += gv[i] * dfeq_i(ka, i, phib);
+            for (int s = 0; s < 3; ++s) {
+                const int q = s + 1;
+                F2 v = fma2(sgn2(1.f - m.w, m.hcd, 1), Pm1.p[q], sgn2(m.w, -m.hcd, 1) * Pn.p[q]);
+                if (q >= 2) {  // e_x = QX(q) of the first velocity: the tangential term -e_x hc (tl G_L + tr G_R)
+                    const F2 gt = fma2(f2(m.tl), gx1[q - 2], f2(m.tr) * gxn[q - 2]);
+                    v = fma2(f2(-float(QX(q)) * k.hc, float(QX(q)) * k.hc), gt, v);
                 }
+                fb[s] = v;
+                gv[s] = fma2(mn.p[q], f2(rR, -rR), mq.p[q] * f2(-rL, rL));  // e_y (r_R mu_R - r_L mu_L)
             }
-            float sdl = 0.f;
+            const float phib = fmaf(1.f - m.w, ph1,
+                                    fmaf(m.w, phn, fmaf(m.hcd, my1 - myn, -k.hc * fmaf(m.tl, gmx1, m.tr * gmxn))));
+            const F2 pb2 = f2(phib);
+            F2 sgp = f2(0.f), sdp = f2(0.f);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                A[i] = fmaf(ka.a_f, gv[i], ka.b_f * sg);
-                if (EY(i) != 0) sdl += gv[i] * fmaf(ka.da_f, fb[i], ka.db_f * fe[i]);
+            for (int s = 0; s < 3; ++s) {
+                const F2 fe = ap_feq(k, s + 1, pb2);
+                sgp = fma2(gv[s], ap_dfeq(k, s + 1, pb2), sgp);
+                sdp = fma2(gv[s], fma2(f2(k.da_f), fb[s], f2(k.db_f) * fe), sdp);
             }
+            const float bsg = k.b_f * hsum(sgp);
+            F2 A[3];
+#pragma unroll
+            for (int s = 0; s < 3; ++s) A[s] = fma2(f2(k.a_f), gv[s], f2(bsg));
             if (owner && n < y1) {
-                djdl += double(sdl);
+                djdl += double(hsum(sdp));
                 if (WU) {
-                    float w[Q];
+                    F2 w[4];
+                    w[0] = f2(0.f);
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) w[i] = ka.b_f * gv[i];
-                    add_du(ka, phib, w, ymask(), du);
+                    for (int s = 0; s < 3; ++s) w[s + 1] = f2(k.b_f) * gv[s];
+                    ap_add_du(k, phib, w, 0xEu, 0.f, du);
                 }
             }
-            // scatter: normal weights into rows n - 1 (L) and n (R) of this lane; x-slope weights
-            // into the same rows of the lanes to the east (+) and west (-)
+            // normal weights into rows n - 1 (below) and n (above); pair 0 and the rest velocity
+            // do not cross (A = b_f sg)
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                Bb[i] = fmaf((1.f - m.w) + float(EY(i)) * m.hcd, A[i], Bb[i]);
-                Bc[i] = fmaf(m.w - float(EY(i)) * m.hcd, A[i], Bc[i]);
-                if (EX(i) != 0) {
-                    const float c = -float(EX(i)) * k.hc * ig * A[i];
-                    const float uL = c * m.tl, uR = c * m.tr;
-                    Bb[i] += __shfl_up_sync(0xffffffffu, uL, 1) - __shfl_down_sync(0xffffffffu, uL, 1);
-                    Bc[i] += __shfl_up_sync(0xffffffffu, uR, 1) - __shfl_down_sync(0xffffffffu, uR, 1);
-                }
+            for (int s = 0; s < 3; ++s) {
+                Bb.p[s + 1] = fma2(sgn2(1.f - m.w, m.hcd, 1), A[s], Bb.p[s + 1]);
+                Bc.p[s + 1] = fma2(sgn2(m.w, -m.hcd, 1), A[s], Bc.p[s + 1]);
+            }
+            const float nb = (1.f - m.w) * bsg, nc = m.w * bsg;
+            Bb.p[0] = Bb.p[0] + f2(nb);
+            Bb.z += nb;
+            Bc.p[0] = Bc.p[0] + f2(nc);
+            Bc.z += nc;
+            // the x-slopes of both cells (this lane's weights Z = -hc ig e_x A, transposed central
+            // difference across lanes), times tl for row n - 1 and tr for row n: pairs 0, 2, 3
+            {
+                const float z0 = mhig * bsg;  // pair 0: e_x = (+1, -1), A = b_f sg
+                const float dz = __shfl_up_sync(0xffffffffu, z0, 1) - __shfl_down_sync(0xffffffffu, z0, 1);
+                const F2 d = f2(dz, -dz);
+                Bb.p[0] = fma2(f2(m.tl), d, Bb.p[0]);
+                Bc.p[0] = fma2(f2(m.tr), d, Bc.p[0]);
+            }
+#pragma unroll
+            for (int s = 1; s < 3; ++s) {
+                const int q = s + 1;
+                const F2 Z = A[s] * f2(float(QX(q)) * mhig, -float(QX(q)) * mhig);
+                const F2 d = shfl_up2(Z) - shfl_dn2(Z);
+                Bb.p[q] = fma2(f2(m.tl), d, Bb.p[q]);
+                Bc.p[q] = fma2(f2(m.tr), d, Bc.p[q]);
             }
         }
         if (n >= y0 + 2) {
             // row n - 2 has every contribution: transpose Eqs. 2.21 and 2.13 and phi = sum f
             const int r = n - 2;
-            float ft[Q], mu[Q], fe[Q], dfe[Q];
-            row_vals(r, 0, ft);
-            row_vals(r, 1, mu);
-            float phi = 0.f;
+            V9 ft, mu;
+            row_v9(r, 0, ft);
+            row_v9(r, 1, mu);
+            const float phi = vsum(ft);
+            const F2 x2 = f2(phi);
+            F2 w[4];
+            F2 pb = f2(0.f), dsum = f2(0.f), fsum = f2(0.f), sp = f2(0.f);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) phi += ft[i];
-            feq_all(k, phi, fe);
-            dfeq_all(ka, phi, dfe);
-            float phibar = 0.f, s = 0.f;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                phibar += (ka.b_bp * Ba[i] + ka.b_tp * mu[i]) * dfe[i];
-                s += Ba[i] * fmaf(ka.da_bp, ft[i], ka.db_bp * fe[i]) + mu[i] * fmaf(ka.da_tp, ft[i], ka.db_tp * fe[i]);
+            for (int q = 0; q < 4; ++q) {
+                const F2 de = ap_dfeq(k, q, x2), fe = ap_feq(k, q, x2);
+                w[q] = fma2(f2(k.b_bp), Ba.p[q], f2(k.b_tp) * mu.p[q]);
+                pb = fma2(w[q], de, pb);
+                dsum = dsum + de;
+                fsum = fsum + fe;
+                sp = fma2(Ba.p[q], fma2(f2(k.da_bp), ft.p[q], f2(k.db_bp) * fe), sp);
+                sp = fma2(mu.p[q], fma2(f2(k.da_tp), ft.p[q], f2(k.db_tp) * fe), sp);
             }
+            const float de0 = 1.f - hsum(dsum), fe0 = phi - hsum(fsum);  // rest velocity: zeroth moment
+            const float wz = fmaf(k.b_bp, Ba.z, k.b_tp * mu.z);
+            const float phibar = fmaf(wz, de0, hsum(pb));
             if (owner) {
-                djdl += double(s);
-                if (WU) {  // Eqs. 2.21 and 2.13: b_bp feq(phi) in P and b_tp feq(phi) in ftilde^+
-                    float w[Q];
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) w[i] = fmaf(ka.b_bp, Ba[i], ka.b_tp * mu[i]);
-                    add_du(ka, phi, w, kAllQ, du);
-                }
+                djdl += double(hsum(sp) + fmaf(Ba.z, fmaf(k.da_bp, ft.z, k.db_bp * fe0),
+                                               mu.z * fmaf(k.da_tp, ft.z, k.db_tp * fe0)));
+                if (WU) ap_add_du(k, phi, w, 0xFu, wz, du);  // b_bp feq(phi) in P, b_tp feq(phi) in ftilde^+
                 float* out = g.lam + (long long)r * nx + j;
+                const F2 ph2 = f2(phibar);
 #pragma unroll
-                for (int i = 0; i < Q; ++i) out[i * cplane] = fmaf(ka.a_bp, Ba[i], fmaf(ka.a_tp, mu[i], phibar));
+                for (int q = 0; q < 4; ++q) {
+                    const F2 l = fma2(f2(k.a_bp), Ba.p[q], fma2(f2(k.a_tp), mu.p[q], ph2));
+                    out[PA(q) * cplane] = l.v.x;
+                    out[PB(q) * cplane] = l.v.y;
+                }
+                out[0] = fmaf(k.a_bp, Ba.z, fmaf(k.a_tp, mu.z, phibar));
             }
         }
         // the stage of row n - 2 is no longer read: refill it
@@ -272,21 +416,27 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
             fence_proxy_async_smem();
             issue(t - 2 + S);
         }
+        Pm2 = Pm1;
+        Pm1 = Pn;
+        Ba = Bb;
+        Bb = Bc;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            Pm2[i] = Pm1[i];
-            Pm1[i] = Pn[i];
-            Ba[i] = Bb[i];
-            Bb[i] = Bc[i];
-            Bc[i] = 0.f;
-        }
+        for (int q = 0; q < 4; ++q) Bc.p[q] = f2(0.f);
+        Bc.z = 0.f;
+        my2 = my1;
+        my1 = myn;
+        ph1 = phn;
+        mx1 = mxn;
+        gmx1 = gmxn;
+        gx1[0] = gxn[0];
+        gx1[1] = gxn[1];
     }
     if (failed && lane == 0) {
         atomicOr(a.err, 1);
         // let the copies still in flight land before the warp exits: rows t .. issued - 1
         const int released = max(0, t - 2);
         const int issued = min(R, released + S);
-        for (int u = t; u < issued; ++u) mbar_wait_bounded(&bars[u % S], uint32_t((u / S) & 1), 100000000ull);
+        for (int u = t; u < issued; ++u) mbar_wait_bounded(&bars[u & (S - 1)], uint32_t((u / S) & 1), 100000000ull);
     }
     __syncwarp();
     const double v[3] = {djdl, du[0], du[1]};

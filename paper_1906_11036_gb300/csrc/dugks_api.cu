@@ -651,6 +651,38 @@ AdjConsts<T, NC> make_adj_consts(const dugks_ctx* ctx) {
     return ka;
 }
 
+// the FP32 adjoint's constants on velocity pairs, from the scalar ones
+template <int NC>
+AdjConstsP<NC> make_adj_consts_p(const dugks_ctx* ctx) {
+    const Consts<float, NC> k = make_consts<float, NC>(ctx);
+    const AdjConsts<float, NC> ka = make_adj_consts<float, NC>(ctx);
+    AdjConstsP<NC> p;
+    for (int q = 0; q < 4; ++q) {
+        for (int m = 0; m < NC; ++m) {
+            p.hbp[q][m] = make_float2(k.hbp[PA(q)][m], k.hbp[PB(q)][m]);
+            p.fq[q][m] = make_float2(k.feq[PA(q)][m], k.feq[PB(q)][m]);
+            p.dq[q][m] = make_float2(ka.dfeq[PA(q)][m], ka.dfeq[PB(q)][m]);
+        }
+        for (int ax = 0; ax < 2; ++ax) {
+            p.Au[ax][q] = make_float2(ka.Au[ax][PA(q)], ka.Au[ax][PB(q)]);
+            p.Bu[ax][q] = make_float2(ka.Bu[ax][PA(q)], ka.Bu[ax][PB(q)]);
+        }
+    }
+    for (int ax = 0; ax < 2; ++ax) {
+        p.Au0[ax] = ka.Au[ax][0];
+        p.Bu0[ax] = ka.Bu[ax][0];
+    }
+    for (int m = 0; m < NC; ++m) {
+        p.bpoly[m] = ka.bpoly[m];
+        p.cpoly[m] = ka.cpoly[m];
+    }
+    p.a_bp = ka.a_bp; p.b_bp = ka.b_bp; p.a_tp = ka.a_tp; p.b_tp = ka.b_tp; p.a_f = ka.a_f; p.b_f = ka.b_f;
+    p.da_bp = ka.da_bp; p.db_bp = ka.db_bp; p.da_tp = ka.da_tp; p.db_tp = ka.db_tp;
+    p.da_f = ka.da_f; p.db_f = ka.db_f;
+    p.hc = k.hc;
+    return p;
+}
+
 // adjoint: tiles of kAdjTX x kAdjTY cells (adj_tile_kernel); the wall fold uses 128-thread blocks
 constexpr int kAdjThreads = 128;
 constexpr int kAdjTX = 32, kAdjTY = 8;
@@ -721,8 +753,7 @@ bool adj_rows_ok(const dugks_ctx* ctx, const void* f, const void* mu) {
 }
 
 template <int NC>
-cudaError_t launch_adjoint_rows(dugks_ctx* ctx, const StepArgs<float, NC>& a, const Consts<float, NC>& k,
-                                const AdjConsts<float, NC>& ka, const AdjArgs<float>& g, const void* f,
+cudaError_t launch_adjoint_rows(dugks_ctx* ctx, const StepArgs<float, NC>& a, const AdjArgs<float>& g, const void* f,
                                 const void* mu) {
     EncodeTiledFn encode = tiled_encoder(ctx);
     if (!encode) return cudaErrorNotSupported;
@@ -755,12 +786,13 @@ cudaError_t launch_adjoint_rows(dugks_ctx* ctx, const StepArgs<float, NC>& a, co
             if ((e = cudaMemsetAsync(g.partial + q * cap + strips * nseg, 0,
                                      sizeof(double) * size_t(cap - strips * nseg), ctx->stream)) != cudaSuccess)
                 return e;
+    const AdjConstsP<NC> kp = make_adj_consts_p<NC>(ctx);
     if (g.want_u)
         adj_rows_kernel<NC, kAdjRowStages, true><<<dim3(strips, unsigned(nseg)), 32, L::bytes(kAdjRowStages),
-                                                   ctx->stream>>>(tm[0], tm[1], a, k, ka, g, seg);
+                                                   ctx->stream>>>(tm[0], tm[1], a, kp, g, seg);
     else
         adj_rows_kernel<NC, kAdjRowStages, false><<<dim3(strips, unsigned(nseg)), 32, L::bytes(kAdjRowStages),
-                                                    ctx->stream>>>(tm[0], tm[1], a, k, ka, g, seg);
+                                                    ctx->stream>>>(tm[0], tm[1], a, kp, g, seg);
     return cudaGetLastError();
 }
 
@@ -789,7 +821,7 @@ cudaError_t launch_adjoint_step(dugks_ctx* ctx, const void* f, const void* mu, v
     g.want_u = want_u ? 1 : 0;
     if constexpr (sizeof(T) == 4 && NC != NC_LARGE) {
         if (adj_rows_ok(ctx, f, mu)) {
-            cudaError_t e = launch_adjoint_rows<NC>(ctx, a, k, ka, g, f, mu);
+            cudaError_t e = launch_adjoint_rows<NC>(ctx, a, g, f, mu);
             if (e != cudaSuccess) return e;
             if (dj_dalpha) return launch_adj_sum(ctx, dj_dalpha, dj_du);
             return cudaGetLastError();

@@ -2,6 +2,8 @@
 must equal the single-instance fused step bit for bit (same arithmetic, any
 tile shape), the single-instance step being parity-tested against the FP64
 oracle; small instances are also checked against the oracle directly."""
+import os
+
 import numpy as np
 import pytest
 
@@ -11,6 +13,8 @@ from oracle import Oracle  # noqa: E402
 from paper_1906_11036_gb300 import inputs as I  # noqa: E402
 
 pytestmark = pytest.mark.gpu
+
+GOLDEN_BATCHED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_batched16.npz")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -91,7 +95,9 @@ def test_batch_small_instances_vs_oracle():
 def test_batched_workload_256_instances():
     """The batched workload: 256 periodic instances with sides from {64..512}
     (seed 7), 1000 steps.  16 sampled instances equal their single-instance
-    runs bit for bit; every instance conserves mass to FP32 rounding."""
+    runs bit for bit; every instance conserves mass to FP32 rounding; 16
+    instances drawn by inputs.batched_sample() match stored FP64 oracle runs
+    (relative L2 over 2048 sample cells <= 2e-5, mass to 2e-5)."""
     from paper_1906_11036_gb300.dugks import BatchSolver
 
     items = I.batched()
@@ -116,6 +122,19 @@ def test_batched_workload_256_instances():
     for i in range(len(items)):
         m = b.get_phi(i, mass=True)[1]
         assert abs(m - m0[i]) <= 1e-5 * abs(m0[i])
+    # 16 sampled instances against the FP64 oracle's runs (stored by make_batched_oracle.py)
+    z = np.load(GOLDEN_BATCHED)
+    assert int(z["steps"]) == 1000
+    errs = {}
+    for i in (int(v) for v in z["ids"]):
+        phi, m = b.get_phi(i, mass=True)
+        got = phi.double().cpu().numpy().reshape(-1)[z[f"sample_{i}"]]
+        ref = z[f"phi_{i}"]
+        errs[i] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        assert abs(m - float(z[f"mass_{i}"])) <= 2e-5 * abs(float(z[f"mass_{i}"]))
+    print("batched vs FP64 oracle, rel-L2 per sampled instance:",
+          ", ".join(f"{i}:{e:.2e}" for i, e in errs.items()))
+    assert max(errs.values()) <= 2e-5
     sample = np.random.default_rng(7).choice(len(items), 16, replace=False)
     states = {int(i): b.save_state(int(i)) for i in sample}
     b.sync()
