@@ -246,8 +246,9 @@ dugks_status dugks_set_source(dugks_ctx *ctx, int nterms, const double *rate, co
  * when dj_du_dev is not NULL, dj_du_dev[a] += mu . d ftilde^{n+1} / d u_a
  * (a = x, y).  f_dev, mu_dev, lam_dev: device, [9][ny][nx] contiguous,
  * precision's type (lam_dev must not alias f_dev or mu_dev); dj_dalpha_dev:
- * device double; dj_du_dev: device, 2 doubles, or NULL; both accumulated in
- * a fixed order (deterministic).  Asynchronous. */
+ * device double, or NULL (then only lam is returned); dj_du_dev: device, 2
+ * doubles, or NULL (it needs dj_dalpha_dev); both accumulated in a fixed
+ * order (deterministic).  Asynchronous. */
 dugks_status dugks_adjoint_step(dugks_ctx *ctx, const void *f_dev, const void *mu_dev, void *lam_dev,
                                 double *dj_dalpha_dev, double *dj_du_dev);
 
@@ -262,8 +263,8 @@ dugks_status dugks_set_feq_check(dugks_ctx *ctx, int on);
 
 /* Which kernel runs an FP32 adjoint step (a cross-check hook; results agree to
  * FP32 rounding).  DUGKS_ADJ_AUTO (the default): the row-marching kernel on
- * grids periodic in both directions with nx a multiple of 4 from about 3 M
- * cells, else the tiled kernel; DUGKS_ADJ_TILED: always the tiled kernel;
+ * grids periodic in both directions with nx a multiple of 4 from 1 M cells
+ * (1024^2), else the tiled kernel; DUGKS_ADJ_TILED: always the tiled kernel;
  * DUGKS_ADJ_ROWS: the row-marching kernel wherever it applies, whatever the
  * size.  DUGKS_ERR_ARG for a null ctx or an unknown value. */
 enum { DUGKS_ADJ_AUTO = 0, DUGKS_ADJ_TILED = 1, DUGKS_ADJ_ROWS = 2 };

@@ -84,10 +84,10 @@ __device__ __forceinline__ float hsum(F2 a) { return a.v.x + a.v.y; }
 __device__ __forceinline__ float hdot(F2 a, F2 b) { return fmaf(a.v.x, b.v.x, a.v.y * b.v.y); }
 
 // du[a] += b(phi) sum_q w_q . Au[a][q] + Cint(phi) sum_q w_q . Bu[a][q] over the pairs in
-// qmask (bit q), plus the rest velocity weighted by wz
+// qmask (bit q), plus the rest velocity weighted by wz (a row's sum, added in FP64 per row)
 template <int NC>
 __device__ __forceinline__ void ap_add_du(const AdjConstsP<NC>& k, float phi, const F2 (&w)[4], unsigned qmask,
-                                          float wz, double (&du)[2]) {
+                                          float wz, float (&du)[2]) {
     float bv = k.bpoly[NC - 1], cv = k.cpoly[NC - 1];
 #pragma unroll
     for (int m = NC - 2; m >= 0; --m) {
@@ -104,7 +104,7 @@ __device__ __forceinline__ void ap_add_du(const AdjConstsP<NC>& k, float phi, co
                 sb = fma2(w[q], F2{k.Bu[a][q]}, sb);
             }
         const float ta = fmaf(wz, k.Au0[a], hsum(sa)), tb = fmaf(wz, k.Bu0[a], hsum(sb));
-        du[a] += double(fmaf(bv, ta, cv * tb));
+        du[a] += fmaf(bv, ta, cv * tb);
     }
 }
 
@@ -183,6 +183,12 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
     int t = 0;
     for (; t < R; ++t) {
         const int n = y0 - 2 + t;
+        // row metrics, loaded before the wait: ig of row n - 1 (x-faces), r of rows n - 1, n and
+        // the y-face below row n
+        const float igq = a.cy[wrow(n - 1) + 1].ig;
+        const float rL = a.cy[wrow(n - 1) + 1].r, rR = a.cy[wrow(n) + 1].r;
+        const FaceM<float> m = a.fy[min(max(n, -1), ny + 1) + 1];
+        float rl = 0.f, ru[2] = {0.f, 0.f};  // this row's dJ/dlambda and dJ/du terms (FP32), added in FP64
         const bool ok = mbar_wait_bounded(&bars[t & (S - 1)], uint32_t((t / S) & 1), 2000000000ull);
         if (__any_sync(0xffffffffu, !ok)) { failed = true; break; }
         // P of the new row (Eq. 2.21; periodic, no ghosts), its moments and x-slopes
@@ -213,7 +219,6 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
         if (n >= y0) {
             // x-faces of row n - 1 (rows y0-1 .. y1); crossing pairs 0, 2, 3 in slots 0, 1, 2
             row_v9(n - 1, 1, mq);
-            const float igq = a.cy[wrow(n - 1) + 1].ig;
             F2 fb[3];
             float phib;
             {
@@ -257,13 +262,13 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
             }
             const float sg = hsum(sgp), bsg = k.b_f * sg;
             if (owner && n - 1 >= y0 && n - 1 < y1) {
-                djdl += double(hsum(sdp));
+                rl += hsum(sdp);
                 if (WU) {  // Eq. 2.22: b_f feq(phi_b) of the crossing velocities
                     F2 w[4];
                     w[1] = f2(0.f);
 #pragma unroll
                     for (int s = 0; s < 3; ++s) w[s == 0 ? 0 : s + 1] = f2(k.b_f) * gv[s];
-                    ap_add_du(k, phib, w, 0xDu, 0.f, du);
+                    ap_add_du(k, phib, w, 0xDu, 0.f, ru);
                 }
             }
             // the face's A at its right cell (the lane to the east)
@@ -302,10 +307,8 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
         if (n >= y0 && n <= y1) {
             // y-face between rows n - 1 and n of this lane's column (faces y0 .. y1); crossing
             // pairs 1, 2, 3 (e_y = +1 for the first velocity) in slots 0, 1, 2
-            const FaceM<float> m = a.fy[n + 1];
             V9 mn;
             row_v9(n, 1, mn);
-            const float rL = a.cy[wrow(n - 1) + 1].r, rR = a.cy[wrow(n) + 1].r;
             F2 fb[3], gv[3];
 #pragma unroll
             for (int s = 0; s < 3; ++s) {
@@ -333,13 +336,13 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
 #pragma unroll
             for (int s = 0; s < 3; ++s) A[s] = fma2(f2(k.a_f), gv[s], f2(bsg));
             if (owner && n < y1) {
-                djdl += double(hsum(sdp));
+                rl += hsum(sdp);
                 if (WU) {
                     F2 w[4];
                     w[0] = f2(0.f);
 #pragma unroll
                     for (int s = 0; s < 3; ++s) w[s + 1] = f2(k.b_f) * gv[s];
-                    ap_add_du(k, phib, w, 0xEu, 0.f, du);
+                    ap_add_du(k, phib, w, 0xEu, 0.f, ru);
                 }
             }
             // normal weights into rows n - 1 (below) and n (above); pair 0 and the rest velocity
@@ -396,9 +399,8 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
             const float wz = fmaf(k.b_bp, Ba.z, k.b_tp * mu.z);
             const float phibar = fmaf(wz, de0, hsum(pb));
             if (owner) {
-                djdl += double(hsum(sp) + fmaf(Ba.z, fmaf(k.da_bp, ft.z, k.db_bp * fe0),
-                                               mu.z * fmaf(k.da_tp, ft.z, k.db_tp * fe0)));
-                if (WU) ap_add_du(k, phi, w, 0xFu, wz, du);  // b_bp feq(phi) in P, b_tp feq(phi) in ftilde^+
+                rl += hsum(sp) + fmaf(Ba.z, fmaf(k.da_bp, ft.z, k.db_bp * fe0), mu.z * fmaf(k.da_tp, ft.z, k.db_tp * fe0));
+                if (WU) ap_add_du(k, phi, w, 0xFu, wz, ru);  // b_bp feq(phi) in P, b_tp feq(phi) in ftilde^+
                 float* out = g.lam + (long long)r * nx + j;
                 const F2 ph2 = f2(phibar);
 #pragma unroll
@@ -409,6 +411,11 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
                 }
                 out[0] = fmaf(k.a_bp, Ba.z, fmaf(k.a_tp, mu.z, phibar));
             }
+        }
+        djdl += double(rl);
+        if (WU) {
+            du[0] += double(ru[0]);
+            du[1] += double(ru[1]);
         }
         // the stage of row n - 2 is no longer read: refill it
         __syncwarp();

@@ -76,6 +76,7 @@ struct dugks_ctx {
     void* adj_ay = nullptr;
     double* adj_partial = nullptr;  // 3 adj_partials(): dJ/dlambda, dJ/du_x, dJ/du_y per block
     double* adj_upart = nullptr;    // 3 x kInitBlocks: the initialisation's u partials
+    int adj_used = 0;               // partial slots the last adjoint launch wrote (the sums read these)
     double* adj_dalpha = nullptr;
     // source terms (dugks_set_source)
     double ux = 0, uy = 0;
@@ -729,7 +730,7 @@ dugks_status adj_alloc(dugks_ctx* ctx) {
 
 // *dj_dalpha += (sum of the lambda partials) / c_s^2; dj_du[a] += sum of the u_a partials (dj_du nullable)
 cudaError_t launch_adj_sum(dugks_ctx* ctx, double* dj_dalpha, double* dj_du) {
-    adj_sum_kernel<<<1, 1024, 0, ctx->stream>>>(ctx->adj_partial, adj_partials(ctx), adj_partials(ctx),
+    adj_sum_kernel<<<1, 1024, 0, ctx->stream>>>(ctx->adj_partial, ctx->adj_used, adj_partials(ctx),
                                                 3.0 / (ctx->c * ctx->c), dj_dalpha, dj_du);
     return cudaGetLastError();
 }
@@ -740,16 +741,16 @@ cudaError_t launch_adj_sum(dugks_ctx* ctx, double* dj_dalpha, double* dj_du) {
 #define DUGKS_ADJ_ROW_STAGES 4
 #endif
 constexpr int kAdjRowStages = DUGKS_ADJ_ROW_STAGES;  // row stages in flight per warp (>= 3)
-// It is used from about 3 M cells up (2048^2: 344 us against 465 us for the tiled kernel; on
-// 1024^2 and below, with too few warps in flight, the tiled kernel is faster), or wherever it
-// applies when dugks_set_adjoint_kernel asked for it.
+// It is used from 1 M cells up (2048^2: 243 us against 506 us for the tiled kernel, 1024^2:
+// 91 against 144 us; on 512^2, with too few warps in flight, the tiled kernel is faster), or
+// wherever it applies when dugks_set_adjoint_kernel asked for it.
 bool adj_rows_ok(const dugks_ctx* ctx, const void* f, const void* mu) {
     const bool applies = ctx->precision == 32 && ctx->nc != NC_LARGE && ctx->xper && ctx->yper && ctx->nx % 4 == 0 &&
                          ctx->nx >= 8 && ctx->ny >= 4 && (reinterpret_cast<uintptr_t>(f) % 16) == 0 &&
                          (reinterpret_cast<uintptr_t>(mu) % 16) == 0;
     if (!applies || ctx->adj_kernel == DUGKS_ADJ_TILED) return false;
     if (ctx->adj_kernel == DUGKS_ADJ_ROWS) return true;
-    return (long long)ctx->nx * ctx->ny >= 3LL * 1024 * 1024;
+    return (long long)ctx->nx * ctx->ny >= 1024LL * 1024;
 }
 
 template <int NC>
@@ -781,11 +782,7 @@ cudaError_t launch_adjoint_rows(dugks_ctx* ctx, const StepArgs<float, NC>& a, co
     const int seg = int((ctx->ny + nseg - 1) / nseg);
     nseg = (ctx->ny + seg - 1) / seg;
     if ((long long)strips * nseg > cap) return cudaErrorInvalidConfiguration;
-    if (!g.accumulate && (long long)strips * nseg < cap)  // slots this launch leaves alone are summed too
-        for (int q = 0; q < 3; ++q)
-            if ((e = cudaMemsetAsync(g.partial + q * cap + strips * nseg, 0,
-                                     sizeof(double) * size_t(cap - strips * nseg), ctx->stream)) != cudaSuccess)
-                return e;
+    ctx->adj_used = int(strips * nseg);  // the sums read the slots this launch writes
     const AdjConstsP<NC> kp = make_adj_consts_p<NC>(ctx);
     if (g.want_u)
         adj_rows_kernel<NC, kAdjRowStages, true><<<dim3(strips, unsigned(nseg)), 32, L::bytes(kAdjRowStages),
@@ -796,13 +793,13 @@ cudaError_t launch_adjoint_rows(dugks_ctx* ctx, const StepArgs<float, NC>& a, co
     return cudaGetLastError();
 }
 
-// One adjoint step.  dj_dalpha != nullptr: the step's partials overwrite the
-// partial buffer and are summed into *dj_dalpha (and dj_du[0..1] if set); nullptr:
-// they are added to the partial buffer (a reverse sweep zeroes it first and sums it
-// at the end).  want_u: also form the u-derivative.
+// One adjoint step.  accumulate: the step's partials are added to the partial buffer (a
+// reverse sweep zeroes it first and sums it at the end); else they overwrite it and, with
+// dj_dalpha set, are summed into *dj_dalpha (and dj_du[0..1] if set).  want_u: also form
+// the u-derivative.
 template <typename T, int NC>
 cudaError_t launch_adjoint_step(dugks_ctx* ctx, const void* f, const void* mu, void* lam, double* dj_dalpha,
-                                double* dj_du, bool want_u) {
+                                double* dj_du, bool want_u, bool accumulate) {
     StepArgs<T, NC> a = make_args<T, NC>(ctx, 0);
     a.fin = static_cast<const T*>(f);  // the adjoint reads contiguous [Q][ny][nx] states
     a.pitch = ctx->nx;
@@ -817,7 +814,7 @@ cudaError_t launch_adjoint_step(dugks_ctx* ctx, const void* f, const void* mu, v
     g.Ay = static_cast<T*>(ctx->adj_ay);
     g.partial = ctx->adj_partial;
     g.pstride = adj_partials(ctx);
-    g.accumulate = dj_dalpha ? 0 : 1;
+    g.accumulate = accumulate ? 1 : 0;
     g.want_u = want_u ? 1 : 0;
     if constexpr (sizeof(T) == 4 && NC != NC_LARGE) {
         if (adj_rows_ok(ctx, f, mu)) {
@@ -828,6 +825,7 @@ cudaError_t launch_adjoint_step(dugks_ctx* ctx, const void* f, const void* mu, v
         }
     }
     const int tb = adj_tile_blocks(ctx);
+    ctx->adj_used = adj_partials(ctx);
     const size_t smem = AdjTile<T, kAdjTX, kAdjTY>::bytes();
     cudaError_t e = cudaFuncSetAttribute(adj_tile_kernel<T, NC, kAdjTX, kAdjTY>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -841,19 +839,19 @@ cudaError_t launch_adjoint_step(dugks_ctx* ctx, const void* f, const void* mu, v
 }
 
 cudaError_t launch_adjoint_step_any(dugks_ctx* ctx, const void* f, const void* mu, void* lam, double* dj_dalpha,
-                                    double* dj_du, bool want_u) {
+                                    double* dj_du, bool want_u, bool accumulate) {
     const int nc = want_u ? std::max(ctx->nc, ctx->nc_u) : ctx->nc;
     if (ctx->precision == 32) {
         switch (nc) {
-            case 3: return launch_adjoint_step<float, 3>(ctx, f, mu, lam, dj_dalpha, dj_du, want_u);
-            case 4: return launch_adjoint_step<float, 4>(ctx, f, mu, lam, dj_dalpha, dj_du, want_u);
-            default: return launch_adjoint_step<float, NC_LARGE>(ctx, f, mu, lam, dj_dalpha, dj_du, want_u);
+            case 3: return launch_adjoint_step<float, 3>(ctx, f, mu, lam, dj_dalpha, dj_du, want_u, accumulate);
+            case 4: return launch_adjoint_step<float, 4>(ctx, f, mu, lam, dj_dalpha, dj_du, want_u, accumulate);
+            default: return launch_adjoint_step<float, NC_LARGE>(ctx, f, mu, lam, dj_dalpha, dj_du, want_u, accumulate);
         }
     }
     switch (nc) {
-        case 3: return launch_adjoint_step<double, 3>(ctx, f, mu, lam, dj_dalpha, dj_du, want_u);
-        case 4: return launch_adjoint_step<double, 4>(ctx, f, mu, lam, dj_dalpha, dj_du, want_u);
-        default: return launch_adjoint_step<double, NC_LARGE>(ctx, f, mu, lam, dj_dalpha, dj_du, want_u);
+        case 3: return launch_adjoint_step<double, 3>(ctx, f, mu, lam, dj_dalpha, dj_du, want_u, accumulate);
+        case 4: return launch_adjoint_step<double, 4>(ctx, f, mu, lam, dj_dalpha, dj_du, want_u, accumulate);
+        default: return launch_adjoint_step<double, NC_LARGE>(ctx, f, mu, lam, dj_dalpha, dj_du, want_u, accumulate);
     }
 }
 
@@ -1474,7 +1472,7 @@ dugks_status dugks_set_source(dugks_ctx* ctx, int nterms, const double* rate, co
 
 dugks_status dugks_adjoint_step(dugks_ctx* ctx, const void* f_dev, const void* mu_dev, void* lam_dev,
                                 double* dj_dalpha_dev, double* dj_du_dev) {
-    if (!ctx || !f_dev || !mu_dev || !lam_dev || !dj_dalpha_dev) return DUGKS_ERR_ARG;
+    if (!ctx || !f_dev || !mu_dev || !lam_dev || (dj_du_dev && !dj_dalpha_dev)) return DUGKS_ERR_ARG;
     if (ctx->nsrc > 0) {
         ctx->last_error = "the adjoint covers the step without source terms";
         return DUGKS_ERR_UNSUPPORTED;
@@ -1482,7 +1480,7 @@ dugks_status dugks_adjoint_step(dugks_ctx* ctx, const void* f_dev, const void* m
     DeviceGuard guard(ctx->device);
     dugks_status st = adj_alloc(ctx);
     if (st != DUGKS_OK) return st;
-    CK(launch_adjoint_step_any(ctx, f_dev, mu_dev, lam_dev, dj_dalpha_dev, dj_du_dev, dj_du_dev != nullptr));
+    CK(launch_adjoint_step_any(ctx, f_dev, mu_dev, lam_dev, dj_dalpha_dev, dj_du_dev, dj_du_dev != nullptr, false));
     return DUGKS_OK;
 }
 
@@ -1556,7 +1554,7 @@ dugks_status dugks_adjoint(dugks_ctx* ctx, const void* phi0_dev, long long nstep
             if (q + 1 < ns && (st = dugks_step(ctx, 1)) != DUGKS_OK) { release(); return st; }
         }
         for (long long q = ns - 1; q >= 0; --q) {
-            if ((e = launch_adjoint_step_any(ctx, seg[q], lam[cur], lam[1 - cur], nullptr, nullptr, want_u)) !=
+            if ((e = launch_adjoint_step_any(ctx, seg[q], lam[cur], lam[1 - cur], nullptr, nullptr, want_u, true)) !=
                 cudaSuccess)
                 return fail(e, "adjoint step");
             cur ^= 1;

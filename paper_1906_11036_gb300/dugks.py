@@ -354,16 +354,22 @@ class Solver:
         """Which kernel runs an FP32 adjoint step: "auto", "tiled" or "rows" (cross-check hook)."""
         self._check(self.L.dugks_set_adjoint_kernel(self.h, self.ADJ_KERNELS[kind]), "dugks_set_adjoint_kernel")
 
-    def adjoint_step(self, f, mu, dj_dalpha=None, dj_du=None, with_u=False):
+    def adjoint_step(self, f, mu, dj_dalpha=None, dj_du=None, with_u=False, with_alpha=True):
         """lam = (d f^{n+1}/d f^n)^T mu at state f (CUDA tensors [9, ny, nx]); the
         explicit alpha-derivative is accumulated into dj_dalpha (a CUDA float64
         tensor of one element, created if None).  Returns (lam, dj_dalpha); with
         with_u (or dj_du given: a CUDA float64 tensor of two elements) the explicit
-        u-derivative is accumulated too and (lam, dj_dalpha, dj_du) is returned."""
+        u-derivative is accumulated too and (lam, dj_dalpha, dj_du) is returned.
+        with_alpha=False: lam only (returned as (lam, None))."""
         t = self.torch
         f = f.to(device=self.device, dtype=self.dtype).contiguous()
         mu = mu.to(device=self.device, dtype=self.dtype).contiguous()
         lam = t.empty_like(f)
+        if not with_alpha:
+            self._check(self.L.dugks_adjoint_step(self.h, ctypes.c_void_p(f.data_ptr()),
+                                                  ctypes.c_void_p(mu.data_ptr()), ctypes.c_void_p(lam.data_ptr()),
+                                                  None, None), "dugks_adjoint_step")
+            return lam, None
         if dj_dalpha is None:
             dj_dalpha = t.zeros(1, dtype=t.float64, device=self.device)
         with_u = with_u or dj_du is not None

@@ -116,6 +116,23 @@ def test_adjoint_step_u_derivative_matches_oracle(name, prec):
     assert np.abs(du - du_ref).max() <= tol * 10 * scale, (du, du_ref)
 
 
+def test_adjoint_step_without_alpha_returns_the_same_lambda():
+    """dj_dalpha = NULL: only lam is formed (no sum); it equals lam of the full call."""
+    for name in ("periodic_rows_64x37", "nonuniform_33x29"):
+        p = CASES[name]()
+        rng = np.random.default_rng(7)
+        o = Oracle(p)
+        f = o.init(1.0 + 0.2 * rng.standard_normal((p.ny, p.nx))) + 0.01 * rng.standard_normal((9, p.ny, p.nx))
+        mu = rng.standard_normal(f.shape)
+        s = _solver(p, 32, "rows" if name.startswith("periodic_") else "auto")
+        ft = torch.tensor(f, dtype=torch.float32, device="cuda")
+        mt = torch.tensor(mu, dtype=torch.float32, device="cuda")
+        lam1, _ = s.adjoint_step(ft, mt)
+        lam2, none = s.adjoint_step(ft, mt, with_alpha=False)
+        s.close()
+        assert none is None and torch.equal(lam1, lam2)
+
+
 def test_u_derivative_with_zero_velocity():
     """u = 0: the step's equilibrium has no b terms, but d feq / d u does (b and
     int b'^2 of higher degree than the step's own polynomial)."""
