@@ -507,6 +507,89 @@ def parity_vs_stored_oracle():
     return out
 
 
+def configs_table(args):
+    """One row per workload configuration (Gaussian hill 64^2 FP64, Burgers 1024^2
+    FP32, non-uniform 2048^2 FP32, 256 batched instances, the 512^2 adjoint):
+    the GPU rate and its error against the stored FP64 oracle runs, next to the
+    oracle as it stands timed on one host thread and on all of them (bounded
+    samples of the same workload).  `bench.py --configs` prints it as one JSON line."""
+    import torch
+
+    import oracle
+    from oracle import Oracle
+    from paper_1906_11036_gb300 import inputs as I
+    from paper_1906_11036_gb300.dugks import Solver
+
+    oracle.build()
+    nproc = os.cpu_count() or 1
+    sec = args.cpu_seconds
+    peak, peak_kind = measured_peak()
+    par = parity_vs_stored_oracle()
+    rows = []
+
+    def gpu_rate(p, phi0, prec, steps):
+        s = Solver(p, precision=prec)
+        s.init_phi(torch.tensor(phi0, dtype=s.dtype, device="cuda"))
+        s.step(min(steps, 20))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.step(steps)
+        e1.record(s.stream)
+        e1.synchronize()
+        s.close()
+        t = e0.elapsed_time(e1) / 1e3
+        return p.nx * p.ny * Q * steps / t, t / steps
+
+    for key, name, prec, big in (("1", "gaussian_hill", 64, False), ("2", "burgers", 32, True),
+                                 ("3", "nonuniform", 32, True)):
+        p, phi0 = I.PRESETS[name]()
+        v, t_step = gpu_rate(p, phi0, prec, p.steps)
+        r1, smp1, _ = oracle_rate(p, phi0, sec, 1, max_rows=64 if big else None)
+        rn, smpn, thr = oracle_rate(p, phi0, sec, nproc, max_rows=256 if big else None)
+        esz = 8 if prec == 64 else 4
+        pr = par.get(f"{name}_fp{prec}", {})
+        rows.append({"config": key, "workload": f"{p.name}, {p.steps} steps, FP{prec}", "gpu_cvu_s": v,
+                     "us_per_step": t_step * 1e6, "hbm_frac": 2 * Q * esz * p.nx * p.ny / t_step / 1e9 / peak,
+                     "l2_resident": 2 * Q * esz * p.nx * p.ny < 126e6,
+                     "rel_l2_vs_oracle": pr.get("rel_l2_vs_oracle"), "mass_rel_vs_oracle": pr.get("mass_rel_vs_oracle"),
+                     "oracle_cvu_s_1_thread": r1, "oracle_cvu_s_nproc": rn, "oracle_threads": thr,
+                     "oracle_sample_1_thread": smp1, "oracle_sample_nproc": smpn})
+    # 4: the batched workload; the oracle on one 512^2 instance of it
+    b = batched_run(None)
+    items = I.batched()
+    p4, phi4 = next(it for it in items if it[0].nx == 512)
+    r1, smp1, _ = oracle_rate(p4, phi4, sec, 1, max_rows=64)
+    rn, smpn, thr = oracle_rate(p4, phi4, sec, nproc)
+    rows.append({"config": "4", "workload": b["workload"] + ", 1000 steps", "gpu_cvu_s": b["value"],
+                 "us_per_step": b["ms_per_step"] * 1e3, "hbm_frac": b["roofline_frac"],
+                 "rel_l2_vs_oracle": (b.get("vs_fp64_oracle") or {}).get("max_rel_l2"),
+                 "oracle_cvu_s_1_thread": r1, "oracle_cvu_s_nproc": rn, "oracle_threads": thr,
+                 "oracle_sample_1_thread": "one 512^2 instance: " + smp1, "oracle_sample_nproc": "one 512^2 instance: " + smpn})
+    # 5: the adjoint workload; the oracle's adjoint step (single-threaded as it stands) on the full grid
+    a = adjoint_ratio(args)
+    p5, phi5 = I.burgers(512, steps=400)
+    o = Oracle(p5)
+    f = o.init(phi5)
+    mu = np.random.default_rng(3).standard_normal(f.shape)
+    t0 = time.perf_counter()
+    n5 = 0
+    while time.perf_counter() - t0 < sec:
+        o.adjoint_step_full(f, mu)
+        n5 += 1
+    r_adj = p5.nx * p5.ny * Q * n5 / (time.perf_counter() - t0)
+    fd = a.get("vs_fp64_fd", {})
+    rows.append({"config": "5", "workload": a["workload"], "gpu_adjoint_cvu_s": p5.nx * p5.ny * Q / (a["adjoint_ms_per_step"] * 1e-3),
+                 "adjoint_step_ratio": a["adjoint_step_ratio"], "gradient_to_forward_ratio": a["gradient_to_forward_ratio"],
+                 "hbm_frac_2048": a["large"]["roofline_frac"], "adjoint_step_ratio_2048": a["large"]["adjoint_step_ratio"],
+                 "max_rel_err_vs_fd_32_dirs": fd.get("max_rel_err_dirs"), "rel_err_dalpha_vs_fd": fd.get("rel_err_dalpha"),
+                 "max_rel_err_du_vs_fd": fd.get("max_rel_err_du"),
+                 "rel_l2_vs_oracle_adjoint_sampled": fd.get("rel_l2_vs_oracle_adjoint_sampled"),
+                 "oracle_adjoint_cvu_s_1_thread": r_adj,
+                 "oracle_sample": f"{n5} FP64 oracle adjoint steps on the full 512^2 grid (one thread: it is not threaded)"})
+    return {"configs": rows, "peak_gbs": peak, "peak_kind": peak_kind, "cpu_model": cpu_model(), "nproc": nproc}
+
+
 def max_over_ranks(times, world: int, device="cpu"):
     """Element-wise maximum of per-rank timings over all ranks (the slowest
     replica sets the job's time); identity for a single process."""
@@ -548,9 +631,16 @@ def main():
     ap.add_argument("--no-sources", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--configs", action="store_true", help="print the per-configuration table instead")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.configs:
+        import __graft_entry__
+
+        __graft_entry__.build()
+        print(json.dumps(configs_table(args)), flush=True)
+        return 0
 
     import torch
 

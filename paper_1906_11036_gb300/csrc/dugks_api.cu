@@ -741,6 +741,17 @@ cudaError_t launch_adj_sum(dugks_ctx* ctx, double* dj_dalpha, double* dj_du) {
 #define DUGKS_ADJ_ROW_STAGES 4
 #endif
 constexpr int kAdjRowStages = DUGKS_ADJ_ROW_STAGES;  // row stages in flight per warp (>= 3)
+// Segments: as many as the 16-row minimum allows up to 96 warps per SM over the launch.  Short
+// segments even out the end of the launch: 2048^2 took 186 us with 16-row segments against
+// 200 us with 29-row ones (36 warps per SM) and 215 us with 24 warps per SM.
+#ifndef DUGKS_ADJ_ROW_WARPS_PER_SM
+#define DUGKS_ADJ_ROW_WARPS_PER_SM 96
+#endif
+#ifndef DUGKS_ADJ_ROW_MIN_SEG
+#define DUGKS_ADJ_ROW_MIN_SEG 16
+#endif
+constexpr int kAdjRowWarpsPerSM = DUGKS_ADJ_ROW_WARPS_PER_SM;  // warps per SM over one launch (segment count)
+constexpr int kAdjRowMinSeg = DUGKS_ADJ_ROW_MIN_SEG;           // rows per segment at least
 // It is used from 1 M cells up (2048^2: 243 us against 506 us for the tiled kernel, 1024^2:
 // 91 against 144 us; on 512^2, with too few warps in flight, the tiled kernel is faster), or
 // wherever it applies when dugks_set_adjoint_kernel asked for it.
@@ -773,11 +784,12 @@ cudaError_t launch_adjoint_rows(dugks_ctx* ctx, const StepArgs<float, NC>& a, co
     int sms = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e != cudaSuccess) return e;
-    // about 36 warps per SM over the launch, segments of at least 16 rows, one partial per warp
+    // about kAdjRowWarpsPerSM warps per SM over the launch, segments of at least kAdjRowMinSeg
+    // rows, one partial per warp
     const int strips = (ctx->nx + L::WI - 1) / L::WI;
     const long long cap = adj_partials(ctx);
-    long long nseg = std::max<long long>(1, 36LL * sms / strips);
-    nseg = std::min<long long>(nseg, std::max(1, ctx->ny / 16));
+    long long nseg = std::max<long long>(1, (long long)kAdjRowWarpsPerSM * sms / strips);
+    nseg = std::min<long long>(nseg, std::max(1, ctx->ny / kAdjRowMinSeg));
     nseg = std::max<long long>(1, std::min<long long>(nseg, cap / strips));
     const int seg = int((ctx->ny + nseg - 1) / nseg);
     nseg = (ctx->ny + seg - 1) / seg;
