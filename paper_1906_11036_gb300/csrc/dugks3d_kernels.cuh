@@ -32,6 +32,8 @@
 // applies the non-equilibrium extrapolation P_g = feq(2 bv - phi) + P - feq(phi).
 // Cells beyond the domain only ever meet zero weights.
 #pragma once
+#include <cuda.h>
+
 #include "dugks_device.cuh"
 
 namespace dugks3 {
@@ -89,6 +91,7 @@ struct Args3 {
     const FaceM<T>* fm[3];  // per axis, faces f = -1 .. n+1 at index f+1
     const CellM<T>* cm[3];  // per axis, cells j = -1 .. n at index j+1
     int zseg;               // planes per CTA segment
+    int* err;               // device error word: bit 0 = a bounded TMA wait expired
 };
 
 template <typename T, int QQ, int NC>
@@ -342,6 +345,13 @@ using dugks::f2;
 using dugks::fma2;
 using dugks::sgn2;
 using dugks::shfl_up2;
+using dugks::fence_mbar_init;
+using dugks::fence_proxy_async_smem;
+using dugks::mbar_arrive_expect_tx;
+using dugks::mbar_init;
+using dugks::mbar_wait_bounded;
+using dugks::smem_u32;
+using dugks::tma_load_4d;
 
 // the opposite of velocity i
 template <int QQ>
@@ -403,21 +413,40 @@ __device__ __forceinline__ F2 hf3(const Consts3P<QQ, NC>& k, int q, F2 x) {
     return s;
 }
 
-template <int QQ, int NW>
+// TMA staging of ftilde: per warp and plane one box of 36 columns x 1 row x 1 plane x QQ
+// velocities ([QQ][36] floats), each box 128-byte aligned
+constexpr int BOX3W = 36;
+template <int QQ>
+__host__ __device__ constexpr int box3_bytes() { return (QQ * BOX3W * 4 + 127) / 128 * 128; }
+
+// shared memory of step3d_vp: P pairs, north faces and moments of three planes, then the
+// ftilde ring (TM: TMA boxes and their mbarriers, with 128 bytes of alignment slack;
+// else per-thread cp.async slots)
+template <int QQ, int NW, bool TM>
 __host__ __device__ constexpr size_t smem3_vp() {
     constexpr int NP = (QQ - 1) / 2;
-    return size_t(2 * (3 * NW * NP * 32) + NW * NCP * 32) * sizeof(float2) + size_t(3 * NW * 4 * 32 + 3 * NW * 32) * sizeof(float);
+    return size_t(3 * NW * NP * 32 + NW * NCP * 32) * sizeof(float2) + size_t(3 * NW * 4 * 32) * sizeof(float) +
+           (TM ? size_t(3 * NW) * (box3_bytes<QQ>() + 8) + 128
+               : size_t(3 * NW * NP * 32) * sizeof(float2) + size_t(3 * NW * 32) * sizeof(float));
 }
 
-template <int QQ, int NC, int NW>
-__global__ void __launch_bounds__(NW * 32, 1) step3d_vp(const Args3<float> a, const Consts3P<QQ, NC> k) {
+// TM: ftilde arrives by TMA (tin: 4-D map of the source state, x = nx a multiple of 4);
+// else by per-thread cp.async copies
+template <int QQ, int NC, int NW, bool TM>
+__global__ void __launch_bounds__(NW * 32, 1)
+    step3d_vp(const __grid_constant__ CUtensorMap tin, const Args3<float> a, const Consts3P<QQ, NC> k) {
     constexpr int NP = (QQ - 1) / 2;
+    constexpr int BOXB = box3_bytes<QQ>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     F2* sP = reinterpret_cast<F2*>(smem_raw);  // [3][NW][NP][32]: P pairs of three planes
-    F2* sF = sP + 3 * NW * NP * 32;            // [3][NW][NP][32]: ftilde pairs of three planes (cp.async)
-    F2* sY = sF + 3 * NW * NP * 32;            // [NW][NCP][32]: north y-face f of each row
+    F2* sY = sP + 3 * NW * NP * 32;            // [NW][NCP][32]: north y-face f of each row
     float* sM = reinterpret_cast<float*>(sY + NW * NCP * 32);  // [3][NW][4][32]: moments M0, Mx, My, Mz
-    float* sF0 = sM + 3 * NW * 4 * 32;                         // [3][NW][32]: ftilde of the rest velocity
+    unsigned char* ring = reinterpret_cast<unsigned char*>(sM + 3 * NW * 4 * 32);
+    // !TM: [3][NW][NP][32] ftilde pairs and [3][NW][32] rest ftilde; TM: [3][NW] boxes + mbarriers
+    F2* sF = reinterpret_cast<F2*>(ring);
+    float* sF0 = reinterpret_cast<float*>(sF + 3 * NW * NP * 32);
+    unsigned char* boxes = ring + ((128u - (smem_u32(ring) & 127u)) & 127u);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(boxes + size_t(3 * NW) * BOXB);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int x0 = blockIdx.x * 30, y0 = blockIdx.y * (NW - 2), z0 = blockIdx.z * a.zseg;
     if (z0 >= a.nz) return;  // uniform over the CTA
@@ -438,10 +467,36 @@ __global__ void __launch_bounds__(NW * 32, 1) step3d_vp(const Args3<float> a, co
     auto Ps = [&](int slot, int ww, int q, int l) -> F2 { return sP[((slot * NW + ww) * NP + q) * 32 + l]; };
     auto Ms = [&](int slot, int ww, int m, int l) -> float { return sM[((slot * NW + ww) * 4 + m) * 32 + l]; };
     auto slot_of = [&](int zz) { return (zz - z0 + 1) % 3; };
-    // start the copy of this thread's ftilde of plane zz into its slots of sF and sF0
+    // TM: this lane's column in its warp's box, or (edge strips) a periodic image or a clamped
+    // ghost source read from global memory
+    const int xs = (x0 - 1) & ~3;
+    const int col = j - xs;
+    const bool from_box = j >= 0 && j < nx;
+    int issued = z0 - 2, consumed = z0 - 2;  // TM: the last plane whose box was requested / awaited
+    bool fail = false;
+    if (TM) {
+        if (lane == 0) {
+            for (int sl = 0; sl < 3; ++sl) mbar_init(&bars[sl * NW + w], 1);
+            fence_mbar_init();
+        }
+        __syncwarp();
+    }
+    // start the copy of this thread's ftilde of plane zz into its slots of sF and sF0 (TM: the
+    // warp's box of plane zz, requested by lane 0 once every lane has read the slot's last plane)
     auto prefetch = [&](int zz) {
         const long long c = ((long long)wrapc(zz, nz, a.per[2]) * ny + sk) * nx + sj;
         const int sl = slot_of(zz);
+        if constexpr (TM) {
+            __syncwarp();
+            if (lane == 0) {
+                uint64_t* bar = &bars[sl * NW + w];
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(bar, uint32_t(QQ * BOX3W * 4));
+                tma_load_4d(boxes + size_t(sl * NW + w) * BOXB, &tin, bar, xs, sk, wrapc(zz, nz, a.per[2]), 0);
+            }
+            issued = zz;
+            return;
+        }
         auto cp4 = [&](const void* dst, int i) {
             asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
                              static_cast<unsigned>(__cvta_generic_to_shared(dst))),
@@ -461,15 +516,38 @@ __global__ void __launch_bounds__(NW * 32, 1) step3d_vp(const Args3<float> a, co
     // then prefetch plane `next`
     auto compute_P = [&](int zz, int slot, int next) -> float {
         const bool gz = !a.per[2] && (zz < 0 || zz >= nz);
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
         F2 F[NP];
-        const float F0 = sF0[(slot * NW + w) * 32 + lane];
+        float F0;
+        if constexpr (TM) {
+            // the n-th use of a slot waits for phase n & 1 of its mbarrier (bounded); after a
+            // timeout no further wait is made and the copies from the failed one on are drained
+            // at exit
+            if (!fail) {
+                if (mbar_wait_bounded(&bars[slot * NW + w], uint32_t(((zz - z0 + 1) / 3) & 1), 2000000000ull))
+                    consumed = zz;
+                else
+                    fail = true;
+            }
+            if (from_box) {
+                const float* bx = reinterpret_cast<const float*>(boxes + size_t(slot * NW + w) * BOXB) + col;
+                F0 = bx[0];
+#pragma unroll
+                for (int q = 0; q < NP; ++q) F[q] = f2(bx[PA3<QQ>(q) * BOX3W], bx[PB3<QQ>(q) * BOX3W]);
+            } else {
+                const float* src = a.fin + ((long long)wrapc(zz, nz, a.per[2]) * ny + sk) * nx + sj;
+                F0 = src[0];
+#pragma unroll
+                for (int q = 0; q < NP; ++q) F[q] = f2(src[PA3<QQ>(q) * a.plane], src[PB3<QQ>(q) * a.plane]);
+            }
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            F0 = sF0[(slot * NW + w) * 32 + lane];
+#pragma unroll
+            for (int q = 0; q < NP; ++q) F[q] = sF[((slot * NW + w) * NP + q) * 32 + lane];
+        }
         F2 fs = f2(0.f);
 #pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            F[q] = sF[((slot * NW + w) * NP + q) * 32 + lane];
-            fs = fs + F[q];
-        }
+        for (int q = 0; q < NP; ++q) fs = fs + F[q];
         const float phi = F0 + (fs.v.x + fs.v.y);
         // the slots of plane next held plane next-3, whose update this thread has done
         prefetch(next);
@@ -545,14 +623,19 @@ __global__ void __launch_bounds__(NW * 32, 1) step3d_vp(const Args3<float> a, co
     prefetch(z0 - 1);
     compute_P(z0 - 1, 0, z0);
     float P0n = compute_P(z0, 1, z0 + 1);  // rest component of P of the plane being updated
-    __syncthreads();
+    // TM: a bounded wait that expired anywhere in the CTA stops every warp at the same barrier
+    bool stop = false;
+    if constexpr (TM) stop = __syncthreads_or(fail) != 0;
+    else __syncthreads();
     F2 fB[NCP];
-    if (interior_row) z_face(0, 1, a.fm[2][z0 + 1], fB);
+#pragma unroll
+    for (int s = 0; s < NCP; ++s) fB[s] = f2(0.f);
+    if (interior_row && !stop) z_face(0, 1, a.fm[2][z0 + 1], fB);
 
     // z metrics of the plane being updated and of its top face, loaded a plane ahead
     CellM<float> czn = a.cm[2][z0 + 1];
     FaceM<float> fzn = a.fm[2][z0 + 2];
-    for (int z = z0; z < z1; ++z) {
+    for (int z = z0; z < z1 && !stop; ++z) {
         const int sm = (z - z0) % 3, so = (z - z0 + 1) % 3, sp = (z - z0 + 2) % 3;
         const float P0 = P0n;
         const CellM<float> czl = czn;
@@ -560,7 +643,11 @@ __global__ void __launch_bounds__(NW * 32, 1) step3d_vp(const Args3<float> a, co
         czn = a.cm[2][min(z + 2, nz)];
         fzn = a.fm[2][min(z + 3, nz + 1)];
         P0n = compute_P(z + 1, sp, z + 2);
-        __syncthreads();
+        if constexpr (TM) {
+            if (__syncthreads_or(fail)) break;
+        } else {
+            __syncthreads();
+        }
         F2 fEx[NCP], fNy[NCP], fTz[NCP];
 #pragma unroll
         for (int s = 0; s < NCP; ++s) fEx[s] = fNy[s] = fTz[s] = f2(0.f);
@@ -631,12 +718,17 @@ __global__ void __launch_bounds__(NW * 32, 1) step3d_vp(const Args3<float> a, co
         // and one waiting warp per plane.
         if (w <= NW - 2) asm volatile("bar.arrive %0, 64;" ::"r"(w + 1) : "memory");
         if (w >= 1) asm volatile("bar.sync %0, 64;" ::"r"(w) : "memory");
-        if (updates) {
+        if (updates) {  // (an updating lane's column is always in its warp's box)
             const long long c = ((long long)z * ny + kk) * nx + j;
+            const float* bx = reinterpret_cast<const float*>(boxes + size_t(so * NW + w) * BOXB) + col;
+            auto Fso = [&](int q) -> F2 {
+                if constexpr (TM) return f2(bx[PA3<QQ>(q) * BOX3W], bx[PB3<QQ>(q) * BOX3W]);
+                else return sF[((so * NW + w) * NP + q) * 32 + lane];
+            };
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
                 const F2 P = Ps(so, w, q, lane);
-                F2 v = fma2(F2{k.third2}, P - sF[((so * NW + w) * NP + q) * 32 + lane], P);  // ftilde^+ (Eq. 2.23)
+                F2 v = fma2(F2{k.third2}, P - Fso(q), P);  // ftilde^+ (Eq. 2.23)
                 if (XP3<QQ>(q, 0) >= 0)
                     v = fma2(sgn2(0.f, -cxj.r, QE3<QQ>(q, 0)), fEx[XP3<QQ>(q, 0)] - fWx[XP3<QQ>(q, 0)], v);
                 if (XP3<QQ>(q, 1) >= 0)
@@ -647,12 +739,19 @@ __global__ void __launch_bounds__(NW * 32, 1) step3d_vp(const Args3<float> a, co
                 a.fout[PA3<QQ>(q) * a.plane + c] = v.v.x;
                 a.fout[PB3<QQ>(q) * a.plane + c] = v.v.y;
             }
-            a.fout[c] = fmaf(k.third, P0 - sF0[(so * NW + w) * 32 + lane], P0);
+            a.fout[c] = fmaf(k.third, P0 - (TM ? bx[0] : sF0[(so * NW + w) * 32 + lane]), P0);
         }
 #pragma unroll
         for (int s = 0; s < NCP; ++s) fB[s] = fTz[s];
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");  // the last prefetch lands before exit
+    if constexpr (TM) {
+        // the boxes still in flight land before the CTA exits (bounded waits)
+        if (fail) atomicOr(a.err, 1);
+        for (int zz = consumed + 1; zz <= issued; ++zz)
+            mbar_wait_bounded(&bars[slot_of(zz) * NW + w], uint32_t(((zz - z0 + 1) / 3) & 1), 100000000ull);
+    } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");  // the last prefetch lands before exit
+    }
 }
 
 // phi = sum_i ftilde_i (optional output) and per-block partial sums of |V| phi in double
