@@ -500,10 +500,20 @@ def parity_vs_stored_oracle():
             s.step(p.steps)
             phi, m = s.get_phi(mass=True)
             s.close()
-            got = phi.double().cpu().numpy().reshape(-1)[g["sample"]]
+            full = phi.double().cpu().numpy()
+            got = full.reshape(-1)[g["sample"]]
             out[f"{name}_fp{prec}"] = {"workload": f"{p.name}, {p.steps} steps, FP{prec}",
                                        "rel_l2_vs_oracle": _rel_l2(got, g["phi"]), "samples": int(got.size),
                                        "mass_rel_vs_oracle": abs(m - float(g["mass"])) / abs(float(g["mass"]))}
+            if name == "gaussian_hill":
+                # GRE (Eq. 4.1.1) against the closed form of Eq. 4.4.3; the oracle's stored run (every
+                # cell) beside it: the kinetic scheme's own distance from the PDE at this c
+                xc, yc = p.centres()
+                ex = I.gaussian_hill_exact(xc, yc, p.steps * p.dt, p.u, p.alpha)
+                ref = np.zeros(p.nx * p.ny)
+                ref[g["sample"]] = g["phi"]
+                out[f"{name}_fp{prec}"]["gre_vs_closed_form"] = I.gre(full, ex)
+                out[f"{name}_fp{prec}"]["oracle_gre_vs_closed_form"] = I.gre(ref.reshape(p.ny, p.nx), ex)
     return out
 
 

@@ -145,6 +145,25 @@ def gaussian_hill_phi0(xc, yc, x0=1.0, y0=1.0, s2=0.01):
     return np.exp(-((X - x0) ** 2 + (Y - y0) ** 2) / (2.0 * s2))
 
 
+def gaussian_hill_exact(xc, yc, t, u, alpha, s2=0.01, L=2.0, x0=1.0, y0=1.0, images=3):
+    """Closed form of the linear CDE for the Gaussian hill (Eq. 4.4.3 with K = alpha I,
+    sigma0^2 = s2, peak 1 at t = 0), summed over periodic images of the box of side L."""
+    X, Y = np.meshgrid(xc, yc)
+    s = s2 + 2 * alpha * t
+    out = np.zeros_like(X)
+    for m in range(-images, images + 1):
+        for n in range(-images, images + 1):
+            dx = X - x0 - u[0] * t - m * L
+            dy = Y - y0 - u[1] * t - n * L
+            out += s2 / s * np.exp(-(dx * dx + dy * dy) / (2 * s))
+    return out
+
+
+def gre(num, exact):
+    """Global relative error, Eq. 4.1.1."""
+    return float(np.abs(num - exact).sum() / np.abs(exact).sum())
+
+
 def burgers_phi0(xc, yc, seed=2):
     rng = np.random.default_rng(seed)
     X, Y = np.meshgrid(xc, yc)

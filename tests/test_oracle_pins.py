@@ -212,23 +212,8 @@ def test_plane_wave_rate_converges_to_kinetic_dispersion(kv, u, nthreads):
 # closed-form solutions of the PDE (Eq. 2.1)
 # ---------------------------------------------------------------------------
 
-def gaussian_hill_exact(xc, yc, t, u, alpha, s2=0.01, L=2.0, x0=1.0, y0=1.0, images=3):
-    """Eq. 4.4.3 with K = alpha I, sigma0^2 = s2, peak 1 at t = 0, summed over
-    periodic images of the box of side L."""
-    X, Y = np.meshgrid(xc, yc)
-    s = s2 + 2 * alpha * t
-    out = np.zeros_like(X)
-    for m in range(-images, images + 1):
-        for n in range(-images, images + 1):
-            dx = X - x0 - u[0] * t - m * L
-            dy = Y - y0 - u[1] * t - n * L
-            out += s2 / s * np.exp(-(dx * dx + dy * dy) / (2 * s))
-    return out
-
-
-def gre(num, exact):
-    """Global relative error, Eq. 4.1.1."""
-    return np.abs(num - exact).sum() / np.abs(exact).sum()
+gaussian_hill_exact = I.gaussian_hill_exact  # Eq. 4.4.3 summed over periodic images
+gre = I.gre  # Eq. 4.1.1
 
 
 def test_gaussian_hill_second_order(nthreads):
