@@ -311,9 +311,10 @@ dugks_status dugks_batch_save_state(dugks_batch *b, int i, void *f_dev_out);
 /* Synchronise; DUGKS_ERR_TIMEOUT if a bounded device wait expired. */
 dugks_status dugks_batch_sync(dugks_batch *b);
 /* Autotuner: times steps_per_trial steps for each candidate tile height (rows
- * per tile, 8 ... 128) on snapshots of the current states, keeps the fastest
- * and restores the states.  Outputs (nullable): the chosen rows per tile and
- * milliseconds per step. */
+ * per tile, 8 ... 128), each with and without the split of every instance's
+ * last fifth of rows into 8-row tiles queued after all the others, on
+ * snapshots of the current states; keeps the fastest and restores the states.
+ * Outputs (nullable): the chosen rows per tile and milliseconds per step. */
 dugks_status dugks_batch_autotune(dugks_batch *b, int steps_per_trial, int *best_rows_out, float *best_ms_out);
 const char *dugks_batch_last_error(const dugks_batch *b);
 

@@ -102,13 +102,17 @@ struct dugks_ctx {
     std::string last_error;
 };
 
+constexpr int kBatchShortRows = 8;       // rows of the short tiles at the end of the batched queue
+constexpr double kBatchLongFrac = 0.8;   // share of an instance's rows in long tiles
+
 struct dugks_batch {
     int n = 0, device = 0, nc = 3;
     std::vector<dugks_ctx*> ctx;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     void* d_insts = nullptr;   // BatchInst<nc>[n]
-    int* d_tile_inst = nullptr;
+    BatchTile* d_tiles = nullptr;  // the tile queue
+    bool split = true;             // long segments, then short tiles at the end of the queue
     int* d_counters = nullptr;  // one per launch of a graph (plus the remainder)
     int* d_err = nullptr;
     int ntiles = 0, seg_target = 48, blocks = 0, stages = 4;
@@ -898,7 +902,9 @@ dugks_status batch_build_tables(dugks_batch* b) {
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
         return (long long)b->ctx[x]->nx * b->ctx[x]->ny > (long long)b->ctx[y]->nx * b->ctx[y]->ny;
     });
-    std::vector<int> tile_inst;
+    // each instance: segments of seg_target rows over about kBatchLongFrac of its rows, then
+    // segments of kBatchShortRows; the short tiles of all instances follow all the long ones
+    std::vector<BatchTile> tiles, shorts;
     for (int oi : order) {
         dugks_ctx* c = b->ctx[oi];
         BatchInst<NC>& I = h[size_t(oi)];
@@ -909,24 +915,33 @@ dugks_status batch_build_tables(dugks_batch* b) {
         I.args[0].err = I.args[1].err = b->d_err;
         I.k = make_constsp<NC>(c);
         I.rw = c->rowy;
-        I.nstrips = (c->nx + WarpLayout<float>::WI - 1) / WarpLayout<float>::WI;
-        I.seg_rows = std::max(1, std::min(b->seg_target, c->ny));
-        I.nseg = (c->ny + I.seg_rows - 1) / I.seg_rows;
-        I.tile_begin = int(tile_inst.size());
-        for (int t = 0; t < I.nstrips * I.nseg; ++t) tile_inst.push_back(oi);
+        const int nstrips = (c->nx + WarpLayout<float>::WI - 1) / WarpLayout<float>::WI;
+        const int L = std::max(1, std::min(b->seg_target, c->ny));
+        int nlong = (c->ny + L - 1) / L, ylong = c->ny;
+        if (b->split && L > 2 * kBatchShortRows) {
+            nlong = int(kBatchLongFrac * c->ny / L);
+            ylong = nlong * L;
+        }
+        for (int sg = 0; sg < nlong; ++sg)
+            for (int st = 0; st < nstrips; ++st)
+                tiles.push_back(BatchTile{oi, st, sg * L, std::min(sg * L + L, c->ny)});
+        for (int y = ylong; y < c->ny; y += kBatchShortRows)
+            for (int st = 0; st < nstrips; ++st)
+                shorts.push_back(BatchTile{oi, st, y, std::min(y + kBatchShortRows, c->ny)});
     }
-    b->ntiles = int(tile_inst.size());
+    tiles.insert(tiles.end(), shorts.begin(), shorts.end());
+    b->ntiles = int(tiles.size());
     cudaError_t e;
     if (b->d_insts) cudaFree(b->d_insts);
-    if (b->d_tile_inst) cudaFree(b->d_tile_inst);
+    if (b->d_tiles) cudaFree(b->d_tiles);
     b->d_insts = nullptr;
-    b->d_tile_inst = nullptr;
+    b->d_tiles = nullptr;
     if ((e = cudaMalloc(&b->d_insts, sizeof(BatchInst<NC>) * h.size())) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_tile_inst, sizeof(int) * tile_inst.size())) != cudaSuccess)
+        (e = cudaMalloc(&b->d_tiles, sizeof(BatchTile) * tiles.size())) != cudaSuccess)
         return batch_fail(b, e, "cudaMalloc(batch tables)");
     if ((e = cudaMemcpy(b->d_insts, h.data(), sizeof(BatchInst<NC>) * h.size(), cudaMemcpyHostToDevice)) !=
             cudaSuccess ||
-        (e = cudaMemcpy(b->d_tile_inst, tile_inst.data(), sizeof(int) * tile_inst.size(), cudaMemcpyHostToDevice)) !=
+        (e = cudaMemcpy(b->d_tiles, tiles.data(), sizeof(BatchTile) * tiles.size(), cudaMemcpyHostToDevice)) !=
             cudaSuccess)
         return batch_fail(b, e, "cudaMemcpy(batch tables)");
     if (b->graph) {
@@ -942,7 +957,7 @@ template <int NC>
 cudaError_t batch_launch(dugks_batch* b, int* counter, int parity) {
     const size_t smem = WarpLayout<float>::bytes(b->stages);
     batch_step_vp<NC><<<b->blocks, 32, smem, b->stream>>>(static_cast<const BatchInst<NC>*>(b->d_insts),
-                                                          b->d_tile_inst, b->ntiles, parity, counter, b->stages,
+                                                          b->d_tiles, b->ntiles, parity, counter, b->stages,
                                                           b->d_err);
     return cudaGetLastError();
 }
@@ -1661,7 +1676,7 @@ dugks_status dugks_batch_destroy(dugks_batch* b) {
         DeviceGuard guard(b->device);
         if (b->stream) cudaStreamSynchronize(b->stream);
         if (b->graph) cudaGraphExecDestroy(b->graph);
-        for (void* p : {b->d_insts, static_cast<void*>(b->d_tile_inst), static_cast<void*>(b->d_counters),
+        for (void* p : {b->d_insts, static_cast<void*>(b->d_tiles), static_cast<void*>(b->d_counters),
                         static_cast<void*>(b->d_err)})
             if (p) cudaFree(p);
     }
@@ -1740,14 +1755,19 @@ dugks_status dugks_batch_autotune(dugks_batch* b, int steps_per_trial, int* best
         if (st != DUGKS_OK) { release(); return st; }
     }
     const int p_saved = b->parity;
+    // tile heights, each with and without the short tiles at the end of the queue
     const int cands[] = {8, 16, 24, 32, 48, 64, 96, 128};
     int best = b->seg_target;
+    bool best_split = b->split;
     float best_ms = 1e30f;
     cudaEvent_t ev0, ev1;
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);
-    for (int cand : cands) {
+    for (int trial = 0; trial < 2 * int(sizeof(cands) / sizeof(cands[0])); ++trial) {
+        const int cand = cands[trial / 2];
         b->seg_target = cand;
+        b->split = (trial & 1) != 0;
+        if (b->split && cand <= 2 * kBatchShortRows) continue;  // no short tiles to split off
         dugks_status st = batch_tables(b);
         if (st != DUGKS_OK) { release(); return st; }
         if ((e = batch_launch_steps(b, std::min(2, dugks_batch::kGraphSteps))) != cudaSuccess) break;  // warm-up
@@ -1758,7 +1778,7 @@ dugks_status dugks_batch_autotune(dugks_batch* b, int steps_per_trial, int* best
         if (e != cudaSuccess || (e = cudaEventSynchronize(ev1)) != cudaSuccess) break;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev0, ev1);
-        if (ms < best_ms) { best_ms = ms; best = cand; }
+        if (ms < best_ms) { best_ms = ms; best = cand; best_split = b->split; }
     }
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
@@ -1776,6 +1796,7 @@ dugks_status dugks_batch_autotune(dugks_batch* b, int steps_per_trial, int* best
     if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) { release(); return batch_fail(b, e, "sync"); }
     release();
     b->seg_target = best;
+    b->split = best_split;
     dugks_status st = batch_tables(b);
     if (st != DUGKS_OK) return st;
     if (best_rows_out) *best_rows_out = best;
