@@ -277,9 +277,10 @@ dugks_status dugks_set_adjoint_kernel(dugks_ctx *ctx, int kernel);
  * and the sweep reads less).  Runs the forward
  * sweep keeping one state every checkpoint_every steps, then for each segment
  * from the last recomputes its states and steps the adjoint back through it
- * (memory: ceil(nsteps/K) + K + 2 states of 9 nx ny elements, allocated for
- * the call and freed).  Synchronises the stream.  The context's own state is
- * left at an intermediate step: initialise it again before stepping. */
+ * (memory: ceil(nsteps/K) + K + 2 states of 9 nx ny elements in one workspace
+ * that the context keeps for later calls, grown when a call needs more and
+ * freed by dugks_destroy).  Synchronises the stream.  The context's own state
+ * is left at an intermediate step: initialise it again before stepping. */
 dugks_status dugks_adjoint(dugks_ctx *ctx, const void *phi0_dev, long long nsteps, int checkpoint_every,
                            const void *grad_phiN_dev, void *grad_phi0_dev, double *grad_alpha_out,
                            double *grad_u_out);

@@ -77,6 +77,8 @@ struct dugks_ctx {
     double* adj_partial = nullptr;  // 3 adj_partials(): dJ/dlambda, dJ/du_x, dJ/du_y per block
     double* adj_upart = nullptr;    // 3 x kInitBlocks: the initialisation's u partials
     int adj_used = 0;               // partial slots the last adjoint launch wrote (the sums read these)
+    void* adj_ws = nullptr;         // dugks_adjoint's states (checkpoints, a segment, two lambdas), kept
+    size_t adj_ws_bytes = 0;        //   for later calls and grown when a call needs more
     double* adj_dalpha = nullptr;
     // source terms (dugks_set_source)
     double ux = 0, uy = 0;
@@ -597,7 +599,7 @@ void free_ctx(dugks_ctx* ctx) {
                     ctx->adj_ax, ctx->adj_ay,
                     ctx->src_field, ctx->hist[0], ctx->hist[1], ctx->aux[0], ctx->aux[1],
                     static_cast<void*>(ctx->adj_partial), static_cast<void*>(ctx->adj_dalpha),
-                    static_cast<void*>(ctx->adj_upart)})
+                    static_cast<void*>(ctx->adj_upart), ctx->adj_ws})
         if (p) cudaFree(p);
     for (void* p : {static_cast<void*>(ctx->dxv), static_cast<void*>(ctx->dyv), static_cast<void*>(ctx->staging),
                     static_cast<void*>(ctx->partial), static_cast<void*>(ctx->mass_dev),
@@ -1525,36 +1527,39 @@ dugks_status dugks_adjoint(dugks_ctx* ctx, const void* phi0_dev, long long nstep
     if (st != DUGKS_OK) return st;
     const long long K = std::min<long long>(checkpoint_every, std::max<long long>(nsteps, 1));
     const long long nseg = nsteps == 0 ? 0 : (nsteps + K - 1) / K;
-    const size_t sbytes = size_t(Q) * ctx->nx * ctx->ny * ctx->elem;
-    std::vector<void*> bufs;
-    auto release = [&]() {
-        for (void* p : bufs) cudaFree(p);
-        bufs.clear();
-    };
-    auto take = [&](void** p) -> bool {
-        if (cudaMalloc(p, sbytes) != cudaSuccess) return false;
-        bufs.push_back(*p);
-        return true;
-    };
+    // states of 256-byte-aligned size in one workspace: nseg checkpoints, K segment states, two lambdas
+    const size_t sbytes = (size_t(Q) * ctx->nx * ctx->ny * ctx->elem + 255) / 256 * 256;
+    const size_t need = sbytes * size_t(nseg + K + 2);
+    if (need > ctx->adj_ws_bytes) {
+        if (ctx->adj_ws) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(ctx->adj_ws);
+            ctx->adj_ws = nullptr;
+            ctx->adj_ws_bytes = 0;
+        }
+        if (cudaMalloc(&ctx->adj_ws, need) != cudaSuccess) {
+            ctx->adj_ws = nullptr;
+            ctx->last_error = "adjoint workspace allocation failed";
+            return DUGKS_ERR_NOMEM;
+        }
+        ctx->adj_ws_bytes = need;
+    }
+    unsigned char* ws = static_cast<unsigned char*>(ctx->adj_ws);
     std::vector<void*> ckpt(size_t(nseg), nullptr), seg(size_t(K), nullptr);
-    void* lam[2] = {nullptr, nullptr};
-    for (auto& p : ckpt)
-        if (!take(&p)) { release(); ctx->last_error = "checkpoint allocation failed"; return DUGKS_ERR_NOMEM; }
-    for (auto& p : seg)
-        if (!take(&p)) { release(); ctx->last_error = "segment allocation failed"; return DUGKS_ERR_NOMEM; }
-    if (!take(&lam[0]) || !take(&lam[1])) { release(); ctx->last_error = "adjoint allocation failed"; return DUGKS_ERR_NOMEM; }
+    for (long long q = 0; q < nseg; ++q) ckpt[size_t(q)] = ws + size_t(q) * sbytes;
+    for (long long q = 0; q < K; ++q) seg[size_t(q)] = ws + size_t(nseg + q) * sbytes;
+    void* lam[2] = {ws + size_t(nseg + K) * sbytes, ws + size_t(nseg + K + 1) * sbytes};
     auto fail = [&](cudaError_t e, const char* what) {
         dugks_status s = cuda_fail(ctx, e, what);
         cudaStreamSynchronize(ctx->stream);
-        release();
         return s;
     };
     cudaError_t e;
     // forward sweep, keeping one state per segment
-    if ((st = dugks_init_phi(ctx, phi0_dev)) != DUGKS_OK) { release(); return st; }
+    if ((st = dugks_init_phi(ctx, phi0_dev)) != DUGKS_OK) return st;
     for (long long s = 0; s < nseg; ++s) {
-        if ((st = dugks_save_state(ctx, ckpt[s])) != DUGKS_OK) { release(); return st; }
-        if ((st = dugks_step(ctx, std::min(K, nsteps - s * K))) != DUGKS_OK) { release(); return st; }
+        if ((st = dugks_save_state(ctx, ckpt[s])) != DUGKS_OK) return st;
+        if ((st = dugks_step(ctx, std::min(K, nsteps - s * K))) != DUGKS_OK) return st;
     }
     if ((e = cudaMemsetAsync(ctx->adj_dalpha, 0, 3 * sizeof(double), ctx->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(ctx->adj_partial, 0, 3 * sizeof(double) * size_t(adj_partials(ctx)), ctx->stream)) !=
@@ -1575,10 +1580,10 @@ dugks_status dugks_adjoint(dugks_ctx* ctx, const void* phi0_dev, long long nstep
     // reverse sweep: recompute each segment from its checkpoint, then step the adjoint back through it
     for (long long s = nseg - 1; s >= 0; --s) {
         const long long ns = std::min(K, nsteps - s * K);
-        if ((st = dugks_load_state(ctx, ckpt[s])) != DUGKS_OK) { release(); return st; }
+        if ((st = dugks_load_state(ctx, ckpt[s])) != DUGKS_OK) return st;
         for (long long q = 0; q < ns; ++q) {
-            if ((st = dugks_save_state(ctx, seg[q])) != DUGKS_OK) { release(); return st; }
-            if (q + 1 < ns && (st = dugks_step(ctx, 1)) != DUGKS_OK) { release(); return st; }
+            if ((st = dugks_save_state(ctx, seg[q])) != DUGKS_OK) return st;
+            if (q + 1 < ns && (st = dugks_step(ctx, 1)) != DUGKS_OK) return st;
         }
         for (long long q = ns - 1; q >= 0; --q) {
             if ((e = launch_adjoint_step_any(ctx, seg[q], lam[cur], lam[1 - cur], nullptr, nullptr, want_u, true)) !=
@@ -1596,7 +1601,6 @@ dugks_status dugks_adjoint(dugks_ctx* ctx, const void* phi0_dev, long long nstep
         cudaSuccess)
         return fail(e, "cudaMemcpyAsync");
     if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return fail(e, "cudaStreamSynchronize");
-    release();
     if (grad_alpha_out) *grad_alpha_out = res[0];
     if (grad_u_out) {
         grad_u_out[0] = res[1];

@@ -203,6 +203,34 @@ def test_checkpointed_gradient_matches_oracle(prec, kind):
     assert np.abs(np.asarray(du) - duref).max() <= tol * float(np.abs(duref).max()), (du, duref)
 
 
+def test_gradient_workspace_reuse_and_growth():
+    """dugks_adjoint keeps its workspace in the context: a second call gives the
+    same gradient bit for bit, and a longer run (a larger workspace) after a
+    shorter one still matches the oracle."""
+    p, phi0 = I.burgers(40, 32, steps=30)
+    xc, yc = p.centres()
+    area = np.outer(np.diff(p.yf), np.diff(p.xf))
+    target = I.burgers_phi0(xc, yc, seed=5)
+    s = _solver(p, 64)
+    x0 = torch.tensor(phi0, dtype=torch.float64, device="cuda")
+
+    def grad(n, k):
+        s.init_phi(x0)
+        s.step(n)
+        gN = torch.tensor(area * (s.get_phi().cpu().numpy() - target), device="cuda")
+        return s.gradient(x0, n, gN, checkpoint_every=k, with_u=True)
+
+    a = grad(10, 5)
+    b = grad(10, 5)
+    assert torch.equal(a[0], b[0]) and a[1] == b[1] and a[2] == b[2]
+    g, da, du = grad(30, 4)
+    s.close()
+    gref, daref, duref, _ = Oracle(p).gradient(phi0, 30, lambda ph: area * (ph - target), checkpoint_every=4,
+                                               with_u=True)
+    assert _rel(g.cpu().numpy(), gref) <= 1e-10 and abs(da - daref) <= 1e-10 * abs(daref)
+    assert np.abs(np.asarray(du) - duref).max() <= 1e-10 * float(np.abs(duref).max())
+
+
 def test_autograd_function_and_checkpoint_length_invariance():
     """torch.autograd through the run; the gradient does not depend on the
     checkpoint spacing (recomputation is exact)."""
