@@ -411,6 +411,16 @@ dugks_status make_tensor_maps(dugks_ctx* ctx) {
 // the long ones as warps finish, and each warp pays the pipeline fill (two extra rows
 // and the latency of its first loads) over a long segment.  Grids without enough rows
 // for that keep the uniform plan.
+#ifndef DUGKS_PLAN_FIRST
+#define DUGKS_PLAN_FIRST 0.8
+#endif
+#ifndef DUGKS_PLAN_SHORT
+#define DUGKS_PLAN_SHORT 8
+#endif
+// 2048^2 (us per step): 0.8 / 8 rows 65.9, 0.85 / 8 65.6, 0.9 / 8 66.2, 0.8 / 6 66.6, 0.9 / 6 65.9,
+// 0.9 / 10 66.4, 0.95 / 8 68.0
+constexpr double kPlanFirst = DUGKS_PLAN_FIRST;  // share of the rows in the first wave of long segments
+constexpr int kPlanShort = DUGKS_PLAN_SHORT;      // rows of the short segments after them
 void plan_long_short(dugks_ctx* ctx, long long slots, double first, int seg_short) {
     const long long K = std::max<long long>(1, slots / ctx->nstrips);
     const int L = int(first * ctx->ny / double(K));
@@ -459,7 +469,7 @@ dugks_status plan_fused(dugks_ctx* ctx) {
     cut(3 * slots / ctx->nstrips, ctx->seg_rows, ctx->nseg);
     cut(3 * slots / ctx->nstrips, ctx->seg_rows_src, ctx->nseg_src);
     ctx->sp = SegPlan{ctx->seg_rows, ctx->nseg, ctx->seg_rows};
-    if (ctx->precision == 32 && ctx->nc != NC_LARGE) plan_long_short(ctx, slots, 0.8, 8);
+    if (ctx->precision == 32 && ctx->nc != NC_LARGE) plan_long_short(ctx, slots, kPlanFirst, kPlanShort);
     return DUGKS_OK;
 }
 
