@@ -576,11 +576,6 @@ __host__ __device__ constexpr int PB(int q) { return q == 0 ? 3 : q == 1 ? 4 : q
 __host__ __device__ constexpr int QX(int q) { return EX(PA(q)); }
 __host__ __device__ constexpr int QY(int q) { return EY(PA(q)); }
 
-// resident warps per SM the packed kernel is compiled for (sets its register budget)
-#ifndef DUGKS_VP_MIN_WARPS
-#define DUGKS_VP_MIN_WARPS 16
-#endif
-
 struct V9 {
     F2 p[4];
     float z;  // rest velocity
@@ -722,14 +717,9 @@ __device__ __forceinline__ void add_source_vp(const SrcArgs<float>& sa, const fl
     Fp.z = fmaf(sa.kU_f[0], Fa, Fp.z);
 }
 
-#ifndef DUGKS_VP_UNROLL
-#define DUGKS_VP_UNROLL 2
-#endif
 #ifndef DUGKS_VP_SRC_MIN_WARPS
 #define DUGKS_VP_SRC_MIN_WARPS 16
 #endif
-// rows per iteration of the row loop without the source terms
-constexpr int kVpUnroll = DUGKS_VP_UNROLL;
 
 template <int NC, bool EDGE, bool SRC = false>
 __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<float, NC>& a, const ConstsP<NC>& k,
@@ -892,7 +882,8 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
     F2 Pm[4], fS[4], Gx[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) { Pm[q] = fS[q] = Gx[q] = f2(0.f); }
-    if constexpr (SRC) {
+    static_assert(SRC, "the step without sources runs sv_rows (step_vp)");
+    {
         // one loop over rows y0-1 .. y1 whose first two passes skip the parts that need the
         // rows below: the source arithmetic is inlined once (instruction-cache footprint)
         P0 = Fp0 = Ly = V9{};
@@ -923,56 +914,6 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
             P0 = P;
             Fp0 = Fp;
         }
-    } else {
-    if (!load_row(y0 - 1, F)) failed = true;
-    // face metrics: fyB = face below the current row, fyA = face above it (index f+1 for face f)
-    FaceM<float> fyB = a.fy[y0], fyA = a.fy[y0 + 1];
-    if (!failed) {
-        vp_cell(k, F, P0, Fp0, ghost_of(y0 - 1), bv_of(y0 - 1));
-        cell_src(y0 - 1, F, P0, Fp0);
-        grad_x(y0 - 1, P0, Gx);
-        vp_lower(k, fyA, P0, Gx, Ly);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) Pm[q] = P0.p[q];
-        if (!load_row(y0, F)) failed = true;
-    }
-    if (!failed) {
-        fyB = fyA;
-        fyA = a.fy[y0 + 2];
-        vp_cell(k, F, P0, Fp0, ghost_of(y0), bv_of(y0));
-        cell_src(y0, F, P0, Fp0);
-        grad_x(y0, P0, Gx);
-        vp_yface(k, fyB, P0, Gx, Ly, fS);
-        vp_lower(k, fyA, P0, Gx, Ly);
-#pragma unroll(kVpUnroll)
-        for (int r = y0 + 1; r <= y1; ++r) {
-            V9 P, Fp;
-            F2 fN[4];
-            if (!load_row(r, F)) { failed = true; break; }
-            fyB = fyA;
-            fyA = a.fy[r + 2];
-            vp_cell(k, F, P, Fp, ghost_of(r), bv_of(r));
-            cell_src(r, F, P, Fp);
-            grad_x(r, P, Gx);
-            vp_yface(k, fyB, P, Gx, Ly, fN);
-            vp_lower(k, fyA, P, Gx, Ly);
-            {
-                const CellM<float> cyk = a.cy[r];  // row r - 1
-                V9 fb;
-                F2 dW[4];
-                x_fbar(cyk, P0, P, Pm, fb);
-                vp_xflux(k, fb, dW);
-                x_store(r - 1, cyk, Fp0, dW, fN, fS);
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                Pm[q] = P0.p[q];
-                fS[q] = fN[q];
-            }
-            P0 = P;
-            Fp0 = Fp;
-        }
-    }
     }
     if (failed && lane == 0) {
         atomicOr(a.err, 1);
@@ -983,30 +924,6 @@ __device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<f
     }
     ring += issued;
     __syncwarp();
-}
-
-template <int NC>
-__global__ void __launch_bounds__(32, DUGKS_VP_MIN_WARPS) fused_step_vp(const __grid_constant__ CUtensorMap tin,
-                                                        const StepArgs<float, NC> a, const ConstsP<NC> k,
-                                                        const int seg_rows, const int S) {
-    using L = WarpLayout<float>;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + size_t(S) * L::STAGE_BYTES);
-    const int lane = threadIdx.x;
-    const int xw = blockIdx.x * L::WI;
-    const int y0 = blockIdx.y * seg_rows;
-    const int y1 = min(y0 + seg_rows, a.ny);
-    if (y0 >= a.ny || xw >= a.nx) return;
-    if (lane == 0) {
-        for (int q = 0; q < S; ++q) mbar_init(&bars[q], 1);
-        fence_mbar_init();
-    }
-    __syncwarp();
-    const bool edge = xw - 1 < 0 || xw + L::WI >= a.nx;
-    int ring = 0;
-    if (edge) vp_rows<NC, true>(&tin, a, k, smem, bars, S, lane, xw, y0, y1, ring);
-    else vp_rows<NC, false>(&tin, a, k, smem, bars, S, lane, xw, y0, y1, ring);
 }
 
 // One warp waits, bounded, on an mbarrier that nothing completes: the wait expires and the
