@@ -35,6 +35,9 @@ namespace dugks {
 #ifndef DUGKS_ADJ_ROWS_MIN_WARPS
 #define DUGKS_ADJ_ROWS_MIN_WARPS 16
 #endif
+#ifndef DUGKS_ADJ_ROWS_WALL_MIN_WARPS
+#define DUGKS_ADJ_ROWS_WALL_MIN_WARPS 12  // the ghost folds need more registers than 16 warps leave
+#endif
 
 struct AdjRowLayout {
     static constexpr int WI = 28;                       // owned columns per warp
@@ -57,6 +60,7 @@ struct AdjConstsP {
     float a_bp, b_bp, a_tp, b_tp, a_f, b_f;
     float da_bp, db_bp, da_tp, db_tp, da_f, db_f;  // d/dlambda of the weights
     float hc;
+    float bcv[4];  // Dirichlet wall values W, E, S, N
 };
 
 template <int NC>
@@ -108,9 +112,66 @@ __device__ __forceinline__ void ap_add_du(const AdjConstsP<NC>& k, float phi, co
     }
 }
 
-// S: ring stages (a power of two keeps the stage index a mask); WU: also form the u-derivative
-template <int NC, int S, bool WU>
-__global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
+// Mirrored NEE ghost beyond a Dirichlet wall with value bv: P_g = feq(phi_g) + P_c - feq(phi_c),
+// phi_g = 2 bv - phi_c, of the interior cell c it mirrors (ftilde ft).  P (in) is P_c; returns
+// the ghost's zeroth moment phi_g.
+template <int NC>
+__device__ __forceinline__ float ap_ghost(const AdjConstsP<NC>& k, const float phc, const float bv, V9& P) {
+    const float phg = 2.f * bv - phc;
+    const F2 xc = f2(phc), xg = f2(phg);
+    F2 s = f2(0.f);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const F2 d = ap_feq(k, q, xg) - ap_feq(k, q, xc);
+        P.p[q] = P.p[q] + d;
+        s = s + d;
+    }
+    P.z += (phg - phc) - hsum(s);  // rest velocity: zeroth moment
+    return phg;
+}
+
+// The adjoint B of such a ghost folded back into its interior cell (ftilde ft): v = the
+// addition to lam of the cell (transposes of Eq. 2.21 and of phi = sum f through both
+// equilibria); its dJ/dlambda and dJ/du terms are added to rl, ru.
+template <int NC, bool WU>
+__device__ __forceinline__ void ap_ghost_fold(const AdjConstsP<NC>& k, const V9& B, const V9& ft, const float bv,
+                                              V9& v, float& rl, float (&ru)[2]) {
+    const float phc = vsum(ft), phg = 2.f * bv - phc;
+    const F2 xc = f2(phc), xg = f2(phg);
+    const F2 c1 = f2(k.b_bp - 1.f);
+    F2 pb = f2(0.f), dcs = f2(0.f), dgs = f2(0.f), fcs = f2(0.f), sp = f2(0.f);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const F2 dc = ap_dfeq(k, q, xc), dg = ap_dfeq(k, q, xg), fc = ap_feq(k, q, xc);
+        pb = fma2(B.p[q], fma2(c1, dc, f2(-1.f) * dg), pb);
+        dcs = dcs + dc;
+        dgs = dgs + dg;
+        fcs = fcs + fc;
+        sp = fma2(B.p[q], fma2(f2(k.da_bp), ft.p[q], f2(k.db_bp) * fc), sp);
+    }
+    // the rest velocity's derivatives and equilibrium follow the zeroth moment
+    const float dc0 = 1.f - hsum(dcs), dg0 = 1.f - hsum(dgs), fc0 = phc - hsum(fcs);
+    const float phibar = fmaf(B.z, fmaf(k.b_bp - 1.f, dc0, -dg0), hsum(pb));
+    const F2 ph2 = f2(phibar);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v.p[q] = fma2(f2(k.a_bp), B.p[q], ph2);
+    v.z = fmaf(k.a_bp, B.z, phibar);
+    rl += hsum(sp) + B.z * fmaf(k.da_bp, ft.z, k.db_bp * fc0);
+    if (WU) {  // (b_bp - 1) feq(phi_c) and feq(phi_g) in P_g
+        F2 w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = c1 * B.p[q];
+        ap_add_du(k, phc, w, 0xFu, (k.b_bp - 1.f) * B.z, ru);
+        F2 wg[4] = {B.p[0], B.p[1], B.p[2], B.p[3]};
+        ap_add_du(k, phg, wg, 0xFu, B.z, ru);
+    }
+}
+
+// S: ring stages (a power of two keeps the stage index a mask); WU: also form the u-derivative;
+// WALL: the grid has a Dirichlet wall on some axis (mirrored NEE ghosts, their adjoints folded
+// back into the cells they mirror; else both axes are periodic)
+template <int NC, int S, bool WU, bool WALL>
+__global__ void __launch_bounds__(32, WALL ? DUGKS_ADJ_ROWS_WALL_MIN_WARPS : DUGKS_ADJ_ROWS_MIN_WARPS)
     adj_rows_kernel(const __grid_constant__ CUtensorMap tf, const __grid_constant__ CUtensorMap tmu,
                     const StepArgs<float, NC> a, const AdjConstsP<NC> k, const AdjArgs<float> g,
                     const int seg_rows) {
@@ -129,14 +190,27 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
     const int j = xw - 2 + lane;                // this lane's column (periodic image when outside)
     const int jw = ((j % nx) + nx) % nx;
     const int xs = (xw - 2) & ~3;               // 16-byte aligned x of the box
-    const bool from_smem = j >= 0 && j < nx;    // else read the periodic image from global memory
+    const bool XW = WALL && !a.xper, YW = WALL && !a.yper;  // Dirichlet walls in x, in y
+    // with x-walls every lane reads the box: a ghost column (j = -1, nx) the ftilde of the cell it
+    // mirrors, a column beyond the ghosts the nearest cell's (zero weights only), and mu at its own
+    // column, which the TMA zero fill makes 0 outside the domain
+    const bool from_smem = XW || (j >= 0 && j < nx);  // else read the periodic image from global memory
+    const bool gcol = XW && (j == -1 || j == nx);
+    const int jf = XW ? min(max(j, 0), nx - 1) : j;   // column of this lane's ftilde
     const bool owner = lane >= 2 && lane <= 29 && j < nx;
+    const bool xedge = XW && (xw - 2 <= -1 || xw + 29 >= nx);  // the strip holds a ghost column
     const int R = y1 - y0 + 4;                  // rows y0-2 .. y1+1
-    auto wrow = [&](int r) { return r < 0 ? r + ny : (r >= ny ? r - ny : r); };  // r in [-2, ny + 1], ny >= 4
+    auto wrow = [&](int r) { return r < 0 ? r + ny : (r >= ny ? r - ny : r); };  // r in [-3, ny + 1], ny >= 4
+    // rows: ftilde (a ghost row the row it mirrors), mu (outside the domain: the TMA zero fill) and
+    // the cell-metric row (ghost rows carry zero metrics)
+    auto frow = [&](int r) { return YW ? min(max(r, 0), ny - 1) : wrow(r); };
+    auto mrow = [&](int r) { return YW ? r : wrow(r); };
+    auto crow = [&](int r) { return YW ? min(max(r, -1), ny) : wrow(r); };
 
     // this lane's cell: its east face (it is the left cell) and its west face (the right cell)
-    const FaceM<float> fE = a.fx[jw + 2], fW = a.fx[jw + 1];
-    const CellM<float> cxj = a.cx[jw + 1];
+    const int jm = XW ? min(max(j, -1), nx) : jw;
+    const FaceM<float> fE = a.fx[jm + 2], fW = a.fx[jm + 1];
+    const CellM<float> cxj = a.cx[jm + 1];
     const float hx_e = k.hc * fE.tl, hx_w = k.hc * fW.tr;  // weights of this cell's y-slope at the two faces
     const float mhig = -k.hc * cxj.ig;                     // x-slope factor of this cell at its y-faces
 
@@ -146,10 +220,10 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
     }
     __syncwarp();
     auto issue = [&](int t) {  // row y0 - 2 + t into stage t % S
-        const int st = t & (S - 1), row = wrow(y0 - 2 + t);
+        const int st = t & (S - 1), r = y0 - 2 + t;
         mbar_arrive_expect_tx(&bars[st], uint32_t(2 * L::BOX_BYTES));
-        tma_load_3d(stages + size_t(st) * L::STAGE_BYTES, &tf, &bars[st], xs, row, 0);
-        tma_load_3d(stages + size_t(st) * L::STAGE_BYTES + L::MU_OFF, &tmu, &bars[st], xs, row, 0);
+        tma_load_3d(stages + size_t(st) * L::STAGE_BYTES, &tf, &bars[st], xs, frow(r), 0);
+        tma_load_3d(stages + size_t(st) * L::STAGE_BYTES + L::MU_OFF, &tmu, &bars[st], xs, mrow(r), 0);
     };
     if (lane == 0)
         for (int t = 0; t < min(S, R); ++t) issue(t);
@@ -158,12 +232,16 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
         const int t = r - (y0 - 2);
         if (from_smem) {
             const float* st = reinterpret_cast<const float*>(stages + size_t(t & (S - 1)) * L::STAGE_BYTES +
-                                                             (which ? L::MU_OFF : 0)) + (j - xs);
+                                                             (which ? L::MU_OFF : 0)) + ((which ? j : jf) - xs);
             v.z = st[0];
 #pragma unroll
             for (int q = 0; q < 4; ++q) v.p[q] = f2(st[PA(q) * L::BOXW], st[PB(q) * L::BOXW]);
+        } else if (which && YW && (r < 0 || r >= ny)) {  // mu outside the domain
+            v.z = 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v.p[q] = f2(0.f);
         } else {
-            const float* src = (which ? g.mu : g.f) + (long long)wrow(r) * nx + jw;
+            const float* src = (which ? g.mu : g.f) + (long long)(which ? wrow(r) : frow(r)) * nx + jw;
             v.z = src[0];
 #pragma unroll
             for (int q = 0; q < 4; ++q) v.p[q] = f2(src[PA(q) * cplane], src[PB(q) * cplane]);
@@ -185,8 +263,8 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
         const int n = y0 - 2 + t;
         // row metrics, loaded before the wait: ig of row n - 1 (x-faces), r of rows n - 1, n and
         // the y-face below row n
-        const float igq = a.cy[wrow(n - 1) + 1].ig;
-        const float rL = a.cy[wrow(n - 1) + 1].r, rR = a.cy[wrow(n) + 1].r;
+        const float igq = a.cy[crow(n - 1) + 1].ig;
+        const float rL = a.cy[crow(n - 1) + 1].r, rR = a.cy[crow(n) + 1].r;
         const FaceM<float> m = a.fy[min(max(n, -1), ny + 1) + 1];
         float rl = 0.f, ru[2] = {0.f, 0.f};  // this row's dJ/dlambda and dJ/du terms (FP32), added in FP64
         const bool ok = mbar_wait_bounded(&bars[t & (S - 1)], uint32_t((t / S) & 1), 2000000000ull);
@@ -206,6 +284,17 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
                 hs = hs + h;
             }
             Pn.z = fmaf(k.a_bp, F.z, fmaf(k.b_bp, phn, -hsum(hs)));  // rest velocity: zeroth moment
+            if constexpr (WALL) {  // mirrored ghosts (corner ghosts, never used, kept at zero)
+                const bool grow = YW && (n == -1 || n == ny);
+                if (gcol && grow) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) Pn.p[q] = f2(0.f);
+                    Pn.z = 0.f;
+                    phn = 0.f;
+                } else if (gcol || grow) {
+                    phn = ap_ghost(k, phn, gcol ? (j < 0 ? k.bcv[0] : k.bcv[1]) : (n < 0 ? k.bcv[2] : k.bcv[3]), Pn);
+                }
+            }
         }
         const float d0 = Pn.p[0].v.x - Pn.p[0].v.y, d1 = Pn.p[1].v.x - Pn.p[1].v.y;
         const float d2 = Pn.p[2].v.x - Pn.p[2].v.y, d3 = Pn.p[3].v.x - Pn.p[3].v.y;
@@ -261,7 +350,8 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
                 sdp = fma2(gv[s], fma2(f2(k.da_f), fb[s], f2(k.db_f) * fe), sdp);
             }
             const float sg = hsum(sgp), bsg = k.b_f * sg;
-            if (owner && n - 1 >= y0 && n - 1 < y1) {
+            // (with an x-wall the ghost lane j = -1 counts the wall face west of column 0)
+            if ((owner || (XW && j == -1)) && n - 1 >= y0 && n - 1 < y1) {
                 rl += hsum(sdp);
                 if (WU) {  // Eq. 2.22: b_f feq(phi_b) of the crossing velocities
                     F2 w[4];
@@ -335,7 +425,7 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
             F2 A[3];
 #pragma unroll
             for (int s = 0; s < 3; ++s) A[s] = fma2(f2(k.a_f), gv[s], f2(bsg));
-            if (owner && n < y1) {
+            if (owner && (n < y1 || (YW && n == ny))) {  // (a y-wall's top face is its own face)
                 rl += hsum(sdp);
                 if (WU) {
                     F2 w[4];
@@ -375,6 +465,22 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
                 Bc.p[q] = fma2(f2(m.tr), d, Bc.p[q]);
             }
         }
+        if constexpr (WALL) {
+            // the south ghost row -1 is complete (in Ba) one pass before row 0 is: its fold waits
+            // in row 0 of lam, which this lane writes when row 0 is finished
+            if (YW && y0 == 0 && n == 1 && owner) {
+                V9 ft0, vs;
+                row_v9(0, 0, ft0);
+                ap_ghost_fold<NC, WU>(k, Ba, ft0, k.bcv[2], vs, rl, ru);
+                float* out = g.lam + j;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    out[PA(q) * cplane] = vs.p[q].v.x;
+                    out[PB(q) * cplane] = vs.p[q].v.y;
+                }
+                out[0] = vs.z;
+            }
+        }
         if (n >= y0 + 2) {
             // row n - 2 has every contribution: transpose Eqs. 2.21 and 2.13 and phi = sum f
             const int r = n - 2;
@@ -398,18 +504,65 @@ __global__ void __launch_bounds__(32, DUGKS_ADJ_ROWS_MIN_WARPS)
             const float de0 = 1.f - hsum(dsum), fe0 = phi - hsum(fsum);  // rest velocity: zeroth moment
             const float wz = fmaf(k.b_bp, Ba.z, k.b_tp * mu.z);
             const float phibar = fmaf(wz, de0, hsum(pb));
+            V9 addv;  // folds of the mirrored ghosts of this cell (walls)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) addv.p[q] = f2(0.f);
+            addv.z = 0.f;
+            float addl = 0.f, addu[2] = {0.f, 0.f};
+            float* out = g.lam + (long long)r * nx + j;
+            if constexpr (WALL) {
+                if (xedge) {
+                    // a ghost column's adjoint, folded by its lane, goes to the lane of the cell it
+                    // mirrors: column 0 takes it from lane - 1 (j = -1), column nx - 1 from lane + 1
+                    V9 vg;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) vg.p[q] = f2(0.f);
+                    vg.z = 0.f;
+                    float gl = 0.f, gu[2] = {0.f, 0.f};
+                    if (gcol) ap_ghost_fold<NC, WU>(k, Ba, ft, j < 0 ? k.bcv[0] : k.bcv[1], vg, gl, gu);
+                    const float fw = j == 0 ? 1.f : 0.f, fe = j == nx - 1 ? 1.f : 0.f;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        addv.p[q] = fma2(f2(fw), shfl_up2(vg.p[q]), f2(fe) * shfl_dn2(vg.p[q]));
+                    addv.z = fmaf(fw, __shfl_up_sync(0xffffffffu, vg.z, 1), fe * __shfl_down_sync(0xffffffffu, vg.z, 1));
+                    addl = fmaf(fw, __shfl_up_sync(0xffffffffu, gl, 1), fe * __shfl_down_sync(0xffffffffu, gl, 1));
+                    if (WU)
+#pragma unroll
+                        for (int a2 = 0; a2 < 2; ++a2)
+                            addu[a2] = fmaf(fw, __shfl_up_sync(0xffffffffu, gu[a2], 1),
+                                            fe * __shfl_down_sync(0xffffffffu, gu[a2], 1));
+                }
+                if (YW && y1 == ny && r == ny - 1) {  // the north ghost row ny, complete in Bb
+                    V9 vt;
+                    ap_ghost_fold<NC, WU>(k, Bb, ft, k.bcv[3], vt, addl, addu);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) addv.p[q] = addv.p[q] + vt.p[q];
+                    addv.z += vt.z;
+                }
+                if (YW && y0 == 0 && r == 0 && owner) {  // the south ghost row's fold, held in lam
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) addv.p[q] = addv.p[q] + f2(out[PA(q) * cplane], out[PB(q) * cplane]);
+                    addv.z += out[0];
+                }
+            }
             if (owner) {
                 rl += hsum(sp) + fmaf(Ba.z, fmaf(k.da_bp, ft.z, k.db_bp * fe0), mu.z * fmaf(k.da_tp, ft.z, k.db_tp * fe0));
                 if (WU) ap_add_du(k, phi, w, 0xFu, wz, ru);  // b_bp feq(phi) in P, b_tp feq(phi) in ftilde^+
-                float* out = g.lam + (long long)r * nx + j;
+                if constexpr (WALL) {
+                    rl += addl;
+                    if (WU) {
+                        ru[0] += addu[0];
+                        ru[1] += addu[1];
+                    }
+                }
                 const F2 ph2 = f2(phibar);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const F2 l = fma2(f2(k.a_bp), Ba.p[q], fma2(f2(k.a_tp), mu.p[q], ph2));
+                    const F2 l = fma2(f2(k.a_bp), Ba.p[q], fma2(f2(k.a_tp), mu.p[q], ph2)) + addv.p[q];
                     out[PA(q) * cplane] = l.v.x;
                     out[PB(q) * cplane] = l.v.y;
                 }
-                out[0] = fmaf(k.a_bp, Ba.z, fmaf(k.a_tp, mu.z, phibar));
+                out[0] = fmaf(k.a_bp, Ba.z, fmaf(k.a_tp, mu.z, phibar)) + addv.z;
             }
         }
         djdl += double(rl);

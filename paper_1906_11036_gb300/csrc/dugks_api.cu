@@ -697,6 +697,7 @@ AdjConstsP<NC> make_adj_consts_p(const dugks_ctx* ctx) {
     p.da_bp = ka.da_bp; p.db_bp = ka.db_bp; p.da_tp = ka.da_tp; p.db_tp = ka.db_tp;
     p.da_f = ka.da_f; p.db_f = ka.db_f;
     p.hc = k.hc;
+    for (int w = 0; w < 4; ++w) p.bcv[w] = k.bcv[w];
     return p;
 }
 
@@ -751,7 +752,7 @@ cudaError_t launch_adj_sum(dugks_ctx* ctx, double* dj_dalpha, double* dj_du) {
     return cudaGetLastError();
 }
 
-// The row-marching FP32 adjoint (adj_rows_kernel): grids periodic on both axes, equilibrium
+// The row-marching FP32 adjoint (adj_rows_kernel): periodic or Dirichlet walls, equilibrium
 // degree <= 3, f and mu rows that TMA can copy (nx a multiple of 4, 16-byte aligned buffers).
 #ifndef DUGKS_ADJ_ROW_STAGES
 #define DUGKS_ADJ_ROW_STAGES 4
@@ -772,7 +773,7 @@ constexpr int kAdjRowMinSeg = DUGKS_ADJ_ROW_MIN_SEG;           // rows per segme
 // 91 against 144 us; on 512^2, with too few warps in flight, the tiled kernel is faster), or
 // wherever it applies when dugks_set_adjoint_kernel asked for it.
 bool adj_rows_ok(const dugks_ctx* ctx, const void* f, const void* mu) {
-    const bool applies = ctx->precision == 32 && ctx->nc != NC_LARGE && ctx->xper && ctx->yper && ctx->nx % 4 == 0 &&
+    const bool applies = ctx->precision == 32 && ctx->nc != NC_LARGE && ctx->nx % 4 == 0 &&
                          ctx->nx >= 8 && ctx->ny >= 4 && (reinterpret_cast<uintptr_t>(f) % 16) == 0 &&
                          (reinterpret_cast<uintptr_t>(mu) % 16) == 0;
     if (!applies || ctx->adj_kernel == DUGKS_ADJ_TILED) return false;
@@ -812,12 +813,19 @@ cudaError_t launch_adjoint_rows(dugks_ctx* ctx, const StepArgs<float, NC>& a, co
     if ((long long)strips * nseg > cap) return cudaErrorInvalidConfiguration;
     ctx->adj_used = int(strips * nseg);  // the sums read the slots this launch writes
     const AdjConstsP<NC> kp = make_adj_consts_p<NC>(ctx);
-    if (g.want_u)
-        adj_rows_kernel<NC, kAdjRowStages, true><<<dim3(strips, unsigned(nseg)), 32, L::bytes(kAdjRowStages),
-                                                   ctx->stream>>>(tm[0], tm[1], a, kp, g, seg);
-    else
-        adj_rows_kernel<NC, kAdjRowStages, false><<<dim3(strips, unsigned(nseg)), 32, L::bytes(kAdjRowStages),
-                                                    ctx->stream>>>(tm[0], tm[1], a, kp, g, seg);
+    const dim3 grid(strips, unsigned(nseg));
+    const size_t smem = L::bytes(kAdjRowStages);
+    if (ctx->xper && ctx->yper) {
+        if (g.want_u)
+            adj_rows_kernel<NC, kAdjRowStages, true, false><<<grid, 32, smem, ctx->stream>>>(tm[0], tm[1], a, kp, g, seg);
+        else
+            adj_rows_kernel<NC, kAdjRowStages, false, false><<<grid, 32, smem, ctx->stream>>>(tm[0], tm[1], a, kp, g, seg);
+    } else {  // a Dirichlet wall on some axis
+        if (g.want_u)
+            adj_rows_kernel<NC, kAdjRowStages, true, true><<<grid, 32, smem, ctx->stream>>>(tm[0], tm[1], a, kp, g, seg);
+        else
+            adj_rows_kernel<NC, kAdjRowStages, false, true><<<grid, 32, smem, ctx->stream>>>(tm[0], tm[1], a, kp, g, seg);
+    }
     return cudaGetLastError();
 }
 

@@ -61,7 +61,19 @@ CASES = {
     "periodic_rows_124x50": lambda: I.burgers(124, 50)[0],
     "periodic_mixed_40x33": lambda: _mixed(False, False, 40, 33),
     "periodic_rows_8x5": lambda: I.burgers(8, 5)[0],
+    # Dirichlet walls with nx a multiple of 4: FP32 runs the row-marching adjoint with ghost folds
+    "wallrows_both_64x37": lambda: I.nonuniform(64, 37)[0],
+    "wallrows_x_40x33": lambda: _mixed(True, False, 40, 33),
+    "wallrows_y_44x30": lambda: _mixed(False, True, 44, 30),
+    "wallrows_both_8x5": lambda: I.nonuniform(8, 5)[0],
+    "wallrows_both_124x50": lambda: I.nonuniform(124, 50)[0],
+    "wallrows_both_poly_36x20": lambda: I.nonuniform(36, 20)[0].with_(b=(0.0, 0.6, 0.3, 0.1)),
 }
+
+
+def _kind(name):
+    """The adjoint kernel a case asks for: the row-marching one wherever it applies."""
+    return "rows" if name.startswith(("periodic_", "wallrows_")) else "auto"
 
 
 def _rel(a, b):
@@ -71,8 +83,8 @@ def _rel(a, b):
 @pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("name", list(CASES))
 def test_adjoint_step_matches_oracle(name, prec):
-    # periodic cases: the row-marching FP32 adjoint, whatever the size
-    adj = "rows" if name.startswith("periodic_") else "auto"
+    # periodic and wallrows cases: the row-marching FP32 adjoint, whatever the size
+    adj = _kind(name)
     p = CASES[name]()
     rng = np.random.default_rng(len(name))
     o = Oracle(p)
@@ -95,7 +107,7 @@ def test_adjoint_step_matches_oracle(name, prec):
 def test_adjoint_step_u_derivative_matches_oracle(name, prec):
     """The explicit u-derivative of one step (u of B = u b(phi)): cells, faces,
     ghosts; lam and dJ/dalpha are unchanged by asking for it."""
-    adj = "rows" if name.startswith("periodic_") else "auto"
+    adj = _kind(name)
     p = CASES[name]()
     rng = np.random.default_rng(len(name) + 100)
     o = Oracle(p)
@@ -172,6 +184,48 @@ def test_row_marching_and_tiled_fp32_adjoints_agree():
     (lr, dr), (lt, dtl) = out
     assert _rel(lr, lt) <= 1e-5 and abs(dr - dtl) <= 1e-4 * abs(dtl)
     assert _rel(lr, lam_ref) <= 2e-5 and abs(dr - da_ref) <= 2e-4 * abs(da_ref)
+
+
+def test_row_marching_and_tiled_fp32_adjoints_agree_with_walls():
+    """The same cross-check on a tanh mesh with Dirichlet walls on both axes (ghost folds)."""
+    p = I.nonuniform(256, 200)[0]
+    rng = np.random.default_rng(4)
+    o = Oracle(p)
+    f = o.init(1.0 + 0.2 * rng.standard_normal((p.ny, p.nx))) + 0.01 * rng.standard_normal((9, p.ny, p.nx))
+    mu = rng.standard_normal(f.shape)
+    lam_ref, da_ref, du_ref = o.adjoint_step_full(f, mu)
+    out = []
+    for kind in ("rows", "tiled"):
+        s = _solver(p, 32, kind)
+        lam, da, du = s.adjoint_step(torch.tensor(f, dtype=torch.float32, device="cuda"),
+                                     torch.tensor(mu, dtype=torch.float32, device="cuda"), with_u=True)
+        out.append((lam.double().cpu().numpy(), float(da.item()), du.cpu().numpy()))
+        s.close()
+    (lr, dr, ur), (lt, dtl, ut) = out
+    assert _rel(lr, lt) <= 1e-5 and abs(dr - dtl) <= 1e-4 * abs(dtl)
+    assert _rel(lr, lam_ref) <= 2e-5 and abs(dr - da_ref) <= 2e-4 * abs(da_ref)
+    assert np.abs(ur - du_ref).max() <= 2e-4 * float(np.abs(du_ref).max())
+
+
+@pytest.mark.parametrize("kind", ["tiled", "rows"])
+def test_checkpointed_gradient_with_walls_matches_oracle(kind):
+    """The checkpointed FP32 gradient (phi0, alpha, u) on the non-uniform mesh with walls."""
+    p, phi0 = I.nonuniform(48, 40, steps=40)
+    xc, yc = p.centres()
+    area = np.outer(np.diff(p.yf), np.diff(p.xf))
+    target = I.smooth_phi0(xc, yc, seed=9)
+    gref, daref, duref, _ = Oracle(p).gradient(phi0, p.steps, lambda ph: area * (ph - target), threads=8,
+                                               checkpoint_every=10, with_u=True)
+    s = _solver(p, 32, kind)
+    x0 = torch.tensor(phi0, dtype=torch.float32, device="cuda")
+    s.init_phi(x0)
+    s.step(p.steps)
+    gN = torch.tensor(area * (s.get_phi().double().cpu().numpy() - target), dtype=torch.float32, device="cuda")
+    g0, da, du = s.gradient(x0, p.steps, gN, checkpoint_every=10, with_u=True)
+    s.close()
+    assert _rel(g0.double().cpu().numpy(), gref) <= 1e-4
+    assert abs(da - daref) <= 1e-4 * abs(daref)
+    assert np.abs(np.asarray(du) - duref).max() <= 1e-4 * float(np.abs(duref).max())
 
 
 @pytest.mark.parametrize("prec,kind", [(64, "tiled"), (32, "tiled"), (32, "rows")])
