@@ -262,9 +262,9 @@ dugks_status dugks_adjoint_step(dugks_ctx *ctx, const void *f_dev, const void *m
 dugks_status dugks_set_feq_check(dugks_ctx *ctx, int on);
 
 /* Which kernel runs an FP32 adjoint step (a cross-check hook; results agree to
- * FP32 rounding).  DUGKS_ADJ_AUTO (the default): the row-marching kernel on
- * grids periodic in both directions with nx a multiple of 4 from 1 M cells
- * (1024^2), else the tiled kernel; DUGKS_ADJ_TILED: always the tiled kernel;
+ * FP32 rounding).  DUGKS_ADJ_AUTO (the default): the row-marching kernel
+ * (periodic or Dirichlet walls) on grids with nx a multiple of 4 from 1 M
+ * cells (1024^2), else the tiled kernel; DUGKS_ADJ_TILED: always the tiled kernel;
  * DUGKS_ADJ_ROWS: the row-marching kernel wherever it applies, whatever the
  * size.  DUGKS_ERR_ARG for a null ctx or an unknown value. */
 enum { DUGKS_ADJ_AUTO = 0, DUGKS_ADJ_TILED = 1, DUGKS_ADJ_ROWS = 2 };
