@@ -540,8 +540,8 @@ cudaError_t launch_step(dugks_ctx* ctx) {
     if (ctx->nsrc > 0) {  // the fused kernel with the source terms: velocity pairs in FP32, else scalar
         dim3 grid(ctx->nstrips, ctx->nseg_src);
         if constexpr (sizeof(T) == 4 && NC != NC_LARGE)
-            fused_step_vp_src<NC><<<grid, 32, src_vp_smem(ctx), ctx->stream>>>(
-                ctx->tmap[ctx->cur], a, make_constsp<NC>(ctx), ctx->seg_rows_src, ctx->stages,
+            step_vp_src<NC><<<grid, 32, src_vp_smem(ctx), ctx->stream>>>(
+                ctx->tmap[ctx->cur], a, make_constsp<NC>(ctx), ctx->rowy, ctx->seg_rows_src, ctx->stages,
                 make_src_args<float>(ctx), ctx->taux[ctx->cur]);
         else
             fused_step_src<T, NC><<<grid, 32, fused_smem(ctx), ctx->stream>>>(ctx->tmap[ctx->cur], a, k,

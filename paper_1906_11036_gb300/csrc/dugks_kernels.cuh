@@ -609,98 +609,29 @@ __device__ __forceinline__ float vsum(const V9& a) {
     return a.z + (s.v.x + s.v.y);
 }
 
-// Parts of a row that read the constants.  They are free functions (not
-// lambdas) so that the constants stay direct constant-bank operands.
-template <int NC>
-__device__ __forceinline__ void vp_cell(const ConstsP<NC>& k, const V9& F, V9& P, V9& Fp, const bool ghost,
-                                        const float bv) {
-    // P (Eq. 2.21, b_bp folded into the polynomials) and Fp = P + (P - ft)/3 (Eq. 2.23)
-    const float phi = vsum(F);
-    const F2 phi2 = f2(phi);
-    F2 hs = f2(0.f);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const F2 h = hbp2(k, q, phi2);
-        P.p[q] = fma2(F2{k.a_bp2}, F.p[q], h);
-        hs = hs + h;
-    }
-    P.z = fmaf(k.a_bp, F.z, fmaf(k.b_bp, phi, -(hs.v.x + hs.v.y)));  // rest velocity via the zeroth moment
-#pragma unroll
-    for (int q = 0; q < 4; ++q) Fp.p[q] = fma2(F2{k.third2}, P.p[q] - F.p[q], P.p[q]);
-    Fp.z = fmaf(k.third, P.z - F.z, P.z);
-    if (ghost) {  // mirrored NEE ghost: P_g = feq(2 bv - phi) + P - feq(phi)
-        float fe[Q], fg[Q];
-        feq_all(k.s, phi, fe);
-        feq_all(k.s, 2.f * bv - phi, fg);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) P.p[q] = P.p[q] + f2(fg[PA(q)] - fe[PA(q)], fg[PB(q)] - fe[PB(q)]);
-        P.z += fg[0] - fe[0];
-    }
-}
-// this row's half of the y-face above it (lower cell)
-template <int NC>
-__device__ __forceinline__ void vp_lower(const ConstsP<NC>& k, const FaceM<float>& f, const V9& P,
-                                         const F2 (&Gx)[4], V9& Ly) {
-    const F2 ayp = sgn2(1.f - f.w, f.hcd, 1), ay0 = f2(1.f - f.w);
-    const F2 gp = sgn2(0.f, -k.hc * f.tl, 1), gn = sgn2(0.f, -k.hc * f.tl, -1);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        F2 v = (QY(q) != 0 ? ayp : ay0) * P.p[q];
-        if (QX(q) != 0) v = fma2(QX(q) > 0 ? gp : gn, Gx[q], v);
-        Ly.p[q] = v;
-    }
-    Ly.z = (1.f - f.w) * P.z;
-}
-// y-face below this row: lower half Ly plus this row (upper cell); original f of the crossing pairs
-template <int NC>
-__device__ __forceinline__ void vp_yface(const ConstsP<NC>& k, const FaceM<float>& f, const V9& P,
-                                         const F2 (&Gx)[4], const V9& Ly, F2 (&fy)[4]) {
-    const F2 ayp = sgn2(f.w, -f.hcd, 1), ay0 = f2(f.w);
-    const F2 gp = sgn2(0.f, -k.hc * f.tr, 1), gn = sgn2(0.f, -k.hc * f.tr, -1);
-    V9 fb;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        F2 v = (QY(q) != 0 ? ayp : ay0) * P.p[q];
-        if (QX(q) != 0) v = fma2(QX(q) > 0 ? gp : gn, Gx[q], v);
-        fb.p[q] = Ly.p[q] + v;
-    }
-    fb.z = fmaf(f.w, P.z, Ly.z);
-    const F2 phib = f2(vsum(fb));
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (QY(q) != 0) fy[q] = fma2(F2{k.a_f2}, fb.p[q], hf2(k, q, phib));
-}
-// x-face east of this cell from its fbar: original f (Eq. 2.22) and east-minus-west differences
-template <int NC>
-__device__ __forceinline__ void vp_xflux(const ConstsP<NC>& k, const V9& fb, F2 (&dW)[4]) {
-    const F2 phib = f2(vsum(fb));
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (QX(q) != 0) {
-            const F2 fe = fma2(F2{k.a_f2}, fb.p[q], hf2(k, q, phib));
-            dW[q] = fe - shfl_up2(fe);  // the west face is lane - 1's east face
-        }
-}
-
 // Source terms of one cell added to the velocity pairs of P and Fp (the
 // arithmetic of add_source on the scalar path, with phi^n and phi^{n-1} carried
-// as one pair).  Av[0..nterms-1] are the cell's field values S_k, in ascending
-// order of power, and Av[8] its phi^{n-1}, staged with its ftilde.  Each pair
-// holds two opposite velocities, so their c_i.u terms differ only in sign and
-// their weights agree.
+// as one pair).  Av[0..7] are the cell's field values S_k, in ascending order of
+// power, and Av[8] its phi^{n-1}, staged with its ftilde.  Each pair holds two
+// opposite velocities, so their c_i.u terms differ only in sign and their
+// weights agree.  The loops run to fixed bounds: the host leaves en, ep and
+// dpow of the unused terms and the b' coefficients beyond its degree at zero
+// (an unused term reads a valid field and weighs it by zero), so no branch
+// depends on the number of terms.  b has degree <= NC - 1 wherever B = u b(phi)
+// enters the equilibrium; with u = 0 the R terms vanish whatever b' is.
+template <int NC>
 __device__ __forceinline__ void add_source_vp(const SrcArgs<float>& sa, const float (&Av)[9], float phi, V9& P,
                                               V9& Fp) {
     const F2 X = f2(phi, sa.first ? phi : Av[8]);  // (phi^n, phi^{n-1})
     F2 pw = f2(1.f), Fs = f2(0.f);                 // X^power[k]; (F^n, F^{n-1})
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        if (q < sa.nterms) {
-            for (int m = 0; m < sa.dpow[q]; ++m) pw = pw * X;
-            Fs = fma2(f2(sa.en[q], sa.ep[q]) * f2(Av[q]), pw, Fs);
-        }
+        for (int m = 0; m < sa.dpow[q]; ++m) pw = pw * X;
+        Fs = fma2(f2(sa.en[q], sa.ep[q]) * f2(Av[q]), pw, Fs);
     }
     F2 d = f2(0.f);  // (b'(phi^n), b'(phi^{n-1}))
-    for (int m = sa.ndb - 1; m >= 0; --m) d = fma2(d, X, f2(sa.db[m]));
+#pragma unroll
+    for (int m = NC - 2; m >= 0; --m) d = fma2(d, X, f2(sa.db[m]));
     const F2 G = d * Fs;  // (g^n, g^{n-1}) = b' F
     // F and g at the interface (backward difference over dt/2) and at the update
     const float Ft = fmaf(0.25f, Fs.v.x - Fs.v.y, Fs.v.x), gt = fmaf(0.25f, G.v.x - G.v.y, G.v.x);
@@ -717,215 +648,6 @@ __device__ __forceinline__ void add_source_vp(const SrcArgs<float>& sa, const fl
     Fp.z = fmaf(sa.kU_f[0], Fa, Fp.z);
 }
 
-#ifndef DUGKS_VP_SRC_MIN_WARPS
-#define DUGKS_VP_SRC_MIN_WARPS 16
-#endif
-
-template <int NC, bool EDGE, bool SRC = false>
-__device__ __forceinline__ void vp_rows(const CUtensorMap* tin, const StepArgs<float, NC>& a, const ConstsP<NC>& k,
-                                        unsigned char* stages, uint64_t* bars, const int S, const int lane,
-                                        const int xw, const int y0, const int y1, int& ring,
-                                        const SrcArgs<float>* sa = nullptr, const CUtensorMap* taux = nullptr) {
-    // `ring` counts the rows this warp has already passed through its stage ring (a warp may
-    // process several tiles); row t of the warp uses stage t % S in phase (t / S) & 1
-    using L = WarpLayout<float>;
-    const int nx = a.nx, ny = a.ny;
-    const int j = xw - 1 + lane;
-    const int xs = (xw - 1) & ~(L::ALIGN - 1);
-    const int R = y1 - y0 + 2;
-
-    int role = ROLE_IN, scol = j;
-    if (EDGE) {
-        if (j >= 0 && j < nx) { role = ROLE_IN; scol = j; }
-        else if (j == -1) { role = a.xper ? ROLE_WRAP_W : ROLE_GHOST_W; scol = a.xper ? nx - 1 : 0; }
-        else if (j == nx) { role = a.xper ? ROLE_WRAP_E : ROLE_GHOST_E; scol = a.xper ? 0 : nx - 1; }
-        else { role = ROLE_OUT; scol = 0; }
-    }
-    const bool from_smem = !EDGE || role == ROLE_IN || role == ROLE_GHOST_W || role == ROLE_GHOST_E;
-    const bool ghost_col = EDGE && (role == ROLE_GHOST_W || role == ROLE_GHOST_E);
-    const bool updates = (!EDGE || role == ROLE_IN) && lane >= 1 && lane <= L::WI;
-    const int jm = EDGE ? min(max(j, -1), nx) : j;
-    const FaceM<float> fW = a.fx[jm + 1], fE = a.fx[jm + 2];
-    const CellM<float> cxj = a.cx[jm + 1];
-    const float bvx = role == ROLE_GHOST_W ? k.s.bcv[0] : k.s.bcv[1];
-    const int soff = scol - xs;
-
-    // per-lane x-face weights for pairs with e_x sign +1 (q = 0, 2), -1 (q = 3), 0 (q = 1)
-    const F2 axLp = sgn2(1.f - fE.w, fE.hcd, 1), axLn = sgn2(1.f - fE.w, fE.hcd, -1), axL0 = f2(1.f - fE.w);
-    const F2 axRp = sgn2(fW.w, -fW.hcd, 1), axRn = sgn2(fW.w, -fW.hcd, -1), axR0 = f2(fW.w);
-    const F2 gxL = sgn2(0.f, -k.hc * fE.tl, 1), gxR = sgn2(0.f, -k.hc * fW.tr, 1);  // all y-crossing pairs have e_y sign +1
-    const F2 rxp = sgn2(0.f, -cxj.r, 1), rxn = sgn2(0.f, -cxj.r, -1);
-    auto axL = [&](int q) { return QX(q) > 0 ? axLp : (QX(q) < 0 ? axLn : axL0); };
-    auto axR = [&](int q) { return QX(q) > 0 ? axRp : (QX(q) < 0 ? axRn : axR0); };
-    const float igx_in = cxj.ig;
-
-    auto src_row = [&](int r) -> int {
-        if (r < 0) return a.yper ? r + ny : 0;
-        if (r >= ny) return a.yper ? r - ny : ny - 1;
-        return r;
-    };
-    const int stride = SRC ? sa->stage_bytes : L::STAGE_BYTES;  // bytes per ring stage
-    const uint32_t txb = uint32_t(SRC ? L::BOX_BYTES + sa->aux_box : L::BOX_BYTES);
-    auto issue = [&](int st, int row) {
-        mbar_arrive_expect_tx(&bars[st], txb);
-        tma_load_3d(stages + size_t(st) * stride, tin, &bars[st], xs, row, 0);
-        if (SRC) tma_load_3d(stages + size_t(st) * stride + L::STAGE_BYTES, taux, &bars[st], xs, row, 0);
-    };
-    if (lane == 0) {
-        for (int q = 0; q < min(S, R); ++q) issue((ring + q) % S, src_row(y0 - 1 + q));
-    }
-    float Av[9];  // source path: this lane's S_k (0..7) and phi^{n-1} (8) of the row just loaded
-#pragma unroll
-    for (int q = 0; q < 9; ++q) Av[q] = 0.f;
-    int s = ring % S, issued = min(S, R), consumed = 0;
-    uint32_t ph = uint32_t((ring / S) & 1);
-
-    auto load_row = [&](int r, V9& F) -> bool {
-        const bool ok = mbar_wait_bounded(&bars[s], ph, 2000000000ull);
-        if (__any_sync(0xffffffffu, !ok)) return false;
-        float ft[Q];
-        if (from_smem) {
-            const float* st = reinterpret_cast<const float*>(stages + size_t(s) * stride) + soff;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) ft[i] = st[i * L::BOXW];
-            if (SRC) {
-                const float* ax = reinterpret_cast<const float*>(stages + size_t(s) * stride + L::STAGE_BYTES) + soff;
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (q < sa->nterms) Av[q] = ax[q * L::BOXW];
-                Av[8] = ax[sa->nterms * L::BOXW];
-            }
-        } else if (role != ROLE_OUT) {
-            const long long base = (long long)src_row(r) * a.pitch + scol;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) ft[i] = a.fin[i * a.plane + base];
-            if (SRC) {
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (q < sa->nterms) Av[q] = sa->aux_in[q * sa->aux_plane + base];
-                Av[8] = sa->aux_in[sa->nterms * sa->aux_plane + base];
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) ft[i] = 0.f;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) F.p[q] = f2(ft[PA(q)], ft[PB(q)]);
-        F.z = ft[0];
-        __syncwarp();
-        if (issued < R) {
-            if (lane == 0) {
-                fence_proxy_async_smem();
-                issue(s, src_row(r + S));
-            }
-            ++issued;
-        }
-        if (++s == S) { s = 0; ph ^= 1u; }
-        ++consumed;
-        return true;
-    };
-    auto grad_x = [&](int r, const V9& P, F2 (&Gx)[4]) {
-        const F2 ig = f2((!a.yper && (r < 0 || r >= ny)) ? 0.f : igx_in);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (QX(q) != 0) Gx[q] = (shfl_dn2(P.p[q]) - shfl_up2(P.p[q])) * ig;
-    };
-    // fbar at this cell's east x-face: its own half plus the east neighbour's half
-    auto x_fbar = [&](const CellM<float>& cyk, const V9& P0, const V9& P, const F2 (&Pm)[4], V9& fb) {
-        const F2 igy = f2((ghost_col || (EDGE && role == ROLE_OUT)) ? 0.f : cyk.ig);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            F2 lx = axL(q) * P0.p[q], rxh = axR(q) * P0.p[q];
-            if (QY(q) != 0) {
-                const F2 gyv = (P.p[q] - Pm[q]) * igy;
-                lx = fma2(gxL, gyv, lx);
-                rxh = fma2(gxR, gyv, rxh);
-            }
-            fb.p[q] = lx + shfl_dn2(rxh);
-        }
-        fb.z = (1.f - fE.w) * P0.z + __shfl_down_sync(0xffffffffu, fW.w * P0.z, 1);
-    };
-    // cell update (Eq. 2.12) and store of row kr
-    auto x_store = [&](int kr, const CellM<float>& cyk, const V9& Fp0, const F2 (&dW)[4], const F2 (&fN)[4],
-                       const F2 (&fS)[4]) {
-        const F2 ryp = sgn2(0.f, -cyk.r, 1);
-        V9 v = Fp0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (QX(q) != 0) v.p[q] = fma2(QX(q) > 0 ? rxp : rxn, dW[q], v.p[q]);
-            if (QY(q) != 0) v.p[q] = fma2(ryp, fN[q] - fS[q], v.p[q]);
-        }
-        if (updates) {
-            float* out = a.fout + (long long)kr * a.pitch + j;
-            out[0] = v.z;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                out[PA(q) * a.plane] = v.p[q].v.x;
-                out[PB(q) * a.plane] = v.p[q].v.y;
-            }
-        }
-    };
-    auto ghost_of = [&](int r) { return ghost_col || (!a.yper && (r < 0 || r >= ny)); };
-    const float bv_s = k.s.bcv[2], bv_n = k.s.bcv[3];
-    auto bv_of = [&](int r) { return ghost_col ? bvx : (r < 0 ? bv_s : bv_n); };
-    // source terms of row r's cell (a ghost takes those of the interior cell it mirrors)
-    auto cell_src = [&](int r, const V9& Fr, V9& P, V9& Fp) {
-        if (SRC && !(EDGE && role == ROLE_OUT)) {
-            const float phi = vsum(Fr);
-            if (updates && r >= y0 && r < y1) sa->aux_out[sa->nterms * sa->aux_plane + (long long)r * a.pitch + j] = phi;
-            add_source_vp(*sa, Av, phi, P, Fp);
-        }
-    };
-
-    bool failed = false;
-    V9 F, P0, Fp0, Ly;
-    F2 Pm[4], fS[4], Gx[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) { Pm[q] = fS[q] = Gx[q] = f2(0.f); }
-    static_assert(SRC, "the step without sources runs sv_rows (step_vp)");
-    {
-        // one loop over rows y0-1 .. y1 whose first two passes skip the parts that need the
-        // rows below: the source arithmetic is inlined once (instruction-cache footprint)
-        P0 = Fp0 = Ly = V9{};
-#pragma unroll 1
-        for (int r = y0 - 1; r <= y1; ++r) {
-            V9 P, Fp;
-            F2 fN[4];
-            if (!load_row(r, F)) { failed = true; break; }
-            const FaceM<float> fyB = a.fy[r + 1], fyA = a.fy[r + 2];  // faces below / above row r
-            vp_cell(k, F, P, Fp, ghost_of(r), bv_of(r));
-            cell_src(r, F, P, Fp);
-            grad_x(r, P, Gx);
-            if (r >= y0) vp_yface(k, fyB, P, Gx, Ly, fN);
-            vp_lower(k, fyA, P, Gx, Ly);
-            if (r > y0) {
-                const CellM<float> cyk = a.cy[r];  // row r - 1
-                V9 fb;
-                F2 dW[4];
-                x_fbar(cyk, P0, P, Pm, fb);
-                vp_xflux(k, fb, dW);
-                x_store(r - 1, cyk, Fp0, dW, fN, fS);
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                Pm[q] = P0.p[q];
-                if (r >= y0) fS[q] = fN[q];
-            }
-            P0 = P;
-            Fp0 = Fp;
-        }
-    }
-    if (failed && lane == 0) {
-        atomicOr(a.err, 1);
-        for (int q = consumed; q < issued; ++q) {
-            mbar_wait_bounded(&bars[s], ph, 100000000ull);
-            if (++s == S) { s = 0; ph ^= 1u; }
-        }
-    }
-    ring += issued;
-    __syncwarp();
-}
-
 // One warp waits, bounded, on an mbarrier that nothing completes: the wait expires and the
 // error word is set, as after a stalled copy in a step kernel.
 __global__ void __launch_bounds__(32) wait_timeout_kernel(int* err, unsigned long long limit_ns) {
@@ -937,34 +659,6 @@ __global__ void __launch_bounds__(32) wait_timeout_kernel(int* err, unsigned lon
     __syncwarp();
     const bool ok = mbar_wait_bounded(&bar, 0u, limit_ns);
     if (__any_sync(0xffffffffu, !ok) && threadIdx.x == 0) atomicOr(err, 1);
-}
-
-// the velocity-pair step with the source terms F and R (16 resident warps per SM,
-// as the plain step; the source arithmetic fits in 128 registers without spills)
-template <int NC>
-__global__ void __launch_bounds__(32, DUGKS_VP_SRC_MIN_WARPS) fused_step_vp_src(const __grid_constant__ CUtensorMap tin,
-                                                            const StepArgs<float, NC> a, const ConstsP<NC> k,
-                                                            const int seg_rows, const int S,
-                                                            const __grid_constant__ SrcArgs<float> sa,
-                                                            const __grid_constant__ CUtensorMap taux) {
-    using L = WarpLayout<float>;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + size_t(S) * sa.stage_bytes);
-    const int lane = threadIdx.x;
-    const int xw = blockIdx.x * L::WI;
-    const int y0 = blockIdx.y * seg_rows;
-    const int y1 = min(y0 + seg_rows, a.ny);
-    if (y0 >= a.ny || xw >= a.nx) return;
-    if (lane == 0) {
-        for (int q = 0; q < S; ++q) mbar_init(&bars[q], 1);
-        fence_mbar_init();
-    }
-    __syncwarp();
-    const bool edge = xw - 1 < 0 || xw + L::WI >= a.nx;
-    int ring = 0;
-    if (edge) vp_rows<NC, true, true>(&tin, a, k, smem, bars, S, lane, xw, y0, y1, ring, &sa, &taux);
-    else vp_rows<NC, false, true>(&tin, a, k, smem, bars, S, lane, xw, y0, y1, ring, &sa, &taux);
 }
 
 // ---------------------------------------------------------------------------

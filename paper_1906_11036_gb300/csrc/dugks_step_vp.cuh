@@ -404,4 +404,268 @@ __global__ void __launch_bounds__(32, DUGKS_SV_MIN_WARPS)
     sv_rows<NC>(&tin, a, k, rw, smem, bars, S, lane, xw, y0, y1, edge, yg, ring);
 }
 
+
+// ---------------------------------------------------------------------------
+// the same row routine with the source terms F and R
+// ---------------------------------------------------------------------------
+//
+// The source distributions enter linearly (Eqs. 2.12 and 2.18; the reconstruction of
+// Eqs. 2.19, 2.20 is the same for fbar^+, R and F), so they are added to P = fbar^+ and to
+// ftilde^+ of each cell after Eq. 2.21 (add_source_vp); phi_b then takes the zeroth moment of
+// P with its sources, and a ghost mirrors the cell's own phi and carries its sources.  The
+// fields S_k and phi^{n-1} of a row arrive in a second TMA box in the same ring stage.  One
+// loop over the rows y0-1 .. y1 whose first two passes skip what needs the rows below keeps
+// one inlined copy of the source arithmetic (instruction-cache footprint).
+template <int NC>
+__device__ __forceinline__ void sv_rows_src(const CUtensorMap* tin, const CUtensorMap* taux,
+                                            const StepArgs<float, NC>& a, const ConstsP<NC>& k,
+                                            const RowY* __restrict__ rw, const SrcArgs<float>& sa,
+                                            unsigned char* stages, uint64_t* bars, const int S, const int lane,
+                                            const int xw, const int y0, const int y1, const bool EDGE,
+                                            const bool YG) {
+    using L = WarpLayout<float>;
+    const int nx = a.nx, ny = a.ny;
+    const int j = xw - 1 + lane;
+    const int xs = (xw - 1) & ~(L::ALIGN - 1);
+    const int R = y1 - y0 + 2;
+
+    int role = ROLE_IN, scol = j;
+    if (EDGE) {
+        if (j >= 0 && j < nx) { role = ROLE_IN; scol = j; }
+        else if (j == -1) { role = a.xper ? ROLE_WRAP_W : ROLE_GHOST_W; scol = a.xper ? nx - 1 : 0; }
+        else if (j == nx) { role = a.xper ? ROLE_WRAP_E : ROLE_GHOST_E; scol = a.xper ? 0 : nx - 1; }
+        else { role = ROLE_OUT; scol = 0; }
+    }
+    const bool from_smem = !EDGE || role == ROLE_IN || role == ROLE_GHOST_W || role == ROLE_GHOST_E;
+    const bool ghost_col = EDGE && (role == ROLE_GHOST_W || role == ROLE_GHOST_E);
+    const bool no_slope = EDGE && (ghost_col || role == ROLE_OUT);
+    const bool updates = (!EDGE || role == ROLE_IN) && lane >= 1 && lane <= L::WI;
+    const bool has_src = !(EDGE && role == ROLE_OUT);
+    const int jm = EDGE ? min(max(j, -1), nx) : j;
+    const FaceM<float> fW = a.fx[jm + 1], fE = a.fx[jm + 2];
+    const CellM<float> cxj = a.cx[jm + 1];
+    const float bvx = role == ROLE_GHOST_W ? k.s.bcv[0] : k.s.bcv[1];
+    const int soff = scol - xs;
+
+    const F2 axLp = sgn2(1.f - fE.w, fE.hcd, 1), axLn = sgn2(1.f - fE.w, fE.hcd, -1);
+    const F2 axRp = sgn2(fW.w, -fW.hcd, 1), axRn = sgn2(fW.w, -fW.hcd, -1);
+    const F2 gxL = sgn2(0.f, -k.hc * fE.tl, 1), gxR = sgn2(0.f, -k.hc * fW.tr, 1);
+    const F2 rxp = sgn2(0.f, -cxj.r, 1), rxn = sgn2(0.f, -cxj.r, -1);
+    const float eL0 = 1.f - fE.w, eLx = fE.hcd, eLy = -k.hc * fE.tl;
+    const float wR0 = fW.w, wRx = -fW.hcd, wRy = -k.hc * fW.tr;
+    const float igx = cxj.ig;
+    const float ymask = no_slope ? 0.f : 1.f;
+
+    auto src_row = [&](int r) -> int {
+        if (r < 0) return a.yper ? r + ny : 0;
+        if (r >= ny) return a.yper ? r - ny : ny - 1;
+        return r;
+    };
+    const int stride = sa.stage_bytes;  // ftilde box, then the box of the fields and phi^{n-1}
+    const uint32_t txb = uint32_t(L::BOX_BYTES + sa.aux_box);
+    auto issue = [&](int st, int row) {
+        mbar_arrive_expect_tx(&bars[st], txb);
+        tma_load_3d(stages + size_t(st) * stride, tin, &bars[st], xs, row, 0);
+        tma_load_3d(stages + size_t(st) * stride + L::STAGE_BYTES, taux, &bars[st], xs, row, 0);
+    };
+    if (lane == 0)
+        for (int q = 0; q < min(S, R); ++q) issue(q, src_row(y0 - 1 + q));
+    int s = 0, issued = min(S, R), consumed = 0;
+    uint32_t ph = 0u;
+    float Av[9];  // this lane's S_k (0..nterms-1) and phi^{n-1} (8) of the row just loaded
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Av[q] = 0.f;
+
+    auto load_row = [&](int r, V9& F) -> bool {
+        const bool ok = mbar_wait_bounded(&bars[s], ph, 2000000000ull);
+        if (__any_sync(0xffffffffu, !ok)) return false;
+        float ft[Q];
+        if (from_smem) {
+            const float* st = reinterpret_cast<const float*>(stages + size_t(s) * stride) + soff;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) ft[i] = st[i * L::BOXW];
+            // (a term beyond nterms reads the last field: its weights are zero)
+            const float* ax = reinterpret_cast<const float*>(stages + size_t(s) * stride + L::STAGE_BYTES) + soff;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) Av[q] = ax[min(q, sa.nterms - 1) * L::BOXW];
+            Av[8] = ax[sa.nterms * L::BOXW];
+        } else if (role != ROLE_OUT) {
+            const long long base = (long long)src_row(r) * a.pitch + scol;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) ft[i] = a.fin[i * a.plane + base];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) Av[q] = sa.aux_in[min(q, sa.nterms - 1) * sa.aux_plane + base];
+            Av[8] = sa.aux_in[sa.nterms * sa.aux_plane + base];
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) ft[i] = 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) F.p[q] = f2(ft[PA(q)], ft[PB(q)]);
+        F.z = ft[0];
+        __syncwarp();
+        if (issued < R) {
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                issue(s, src_row(r + S));
+            }
+            ++issued;
+        }
+        if (++s == S) { s = 0; ph ^= 1u; }
+        ++consumed;
+        return true;
+    };
+
+    // row r's cell: P and Fp with the source terms, the mirrored ghost, the moments of P
+    auto cell_row = [&](int r, const V9& F, SvCell& c, V9& Fp) {
+        sv_cell(k, F, c, Fp);  // c.phi = sum_i ftilde_i of the cell
+        if (has_src) {
+            if (updates && r >= y0 && r < y1) sa.aux_out[sa.nterms * sa.aux_plane + (long long)r * a.pitch + j] = c.phi;
+            add_source_vp<NC>(sa, Av, c.phi, c.P, Fp);
+        }
+        if (EDGE || YG) {
+            const bool grow = YG && (r < 0 || r >= ny);
+            if (ghost_col || grow) sv_ghost(k, c, ghost_col ? bvx : (r < 0 ? k.s.bcv[2] : k.s.bcv[3]));
+        }
+        c.phi = vsum(c.P);  // zeroth moment of P with its sources
+        sv_moments(c);
+    };
+    auto grad_x = [&](int r, const SvCell& c, F2& g2, F2& g3, float& gm) {
+        const float ig = (YG && (r < 0 || r >= ny)) ? 0.f : igx;
+        const F2 ig2 = f2(ig);
+        g2 = (shfl_dn2(c.P.p[2]) - shfl_up2(c.P.p[2])) * ig2;
+        g3 = (shfl_up2(c.P.p[3]) - shfl_dn2(c.P.p[3])) * ig2;
+        gm = (__shfl_down_sync(0xffffffffu, c.mx, 1) - __shfl_up_sync(0xffffffffu, c.mx, 1)) * ig;
+    };
+    struct Low {
+        F2 q1, q2, q3;
+        float ph;
+    };
+    auto lower = [&](const RowY& w, const SvCell& c, const F2 g2, const F2 g3, const float gm, Low& lo) {
+        const F2 gl = f2(-w.gl, w.gl);
+        lo.q1 = F2{w.lp} * c.P.p[1];
+        lo.q2 = fma2(gl, g2, F2{w.lp} * c.P.p[2]);
+        lo.q3 = fma2(gl, g3, F2{w.lp} * c.P.p[3]);
+        lo.ph = fmaf(w.l0, c.phi, fmaf(w.hlo, c.my, -w.gl * gm));
+    };
+    auto yface = [&](const RowY& w, const SvCell& c, const F2 g2, const F2 g3, const float gm, const Low& lo,
+                     F2& f1, F2& f2q, F2& f3) {
+        const F2 gu = f2(-w.gu, w.gu);
+        const F2 b1 = fma2(F2{w.up}, c.P.p[1], lo.q1);
+        const F2 b2 = fma2(gu, g2, fma2(F2{w.up}, c.P.p[2], lo.q2));
+        const F2 b3 = fma2(gu, g3, fma2(F2{w.up}, c.P.p[3], lo.q3));
+        const F2 pb = f2(lo.ph + fmaf(w.u0, c.phi, fmaf(-w.hup, c.my, -w.gu * gm)));
+        f1 = fma2(F2{k.a_f2}, b1, hf2(k, 1, pb));
+        f2q = fma2(F2{k.a_f2}, b2, hf2(k, 2, pb));
+        f3 = fma2(F2{k.a_f2}, b3, hf2(k, 3, pb));
+    };
+
+    bool failed = false;
+    SvCell c0;
+    V9 U0, F, Fp;
+    Low lo;
+    F2 pm2 = f2(0.f), pm3 = f2(0.f);
+    float mym = 0.f, ig0 = 0.f, ry0 = 0.f;
+#pragma unroll 1
+    for (int r = y0 - 1; r <= y1; ++r) {
+        const RowY w = rw[r + 1];
+        if (!load_row(r, F)) { failed = true; break; }
+        SvCell c;
+        F2 g2, g3, f1 = f2(0.f), fq2 = f2(0.f), f3 = f2(0.f);
+        float gm;
+        cell_row(r, F, c, Fp);
+        grad_x(r, c, g2, g3, gm);
+        if (r >= y0) yface(w, c, g2, g3, gm, lo, f1, fq2, f3);  // the face below row r
+        if (r > y0) {
+            // the x-face east of (j, r-1) and the update of row r - 1 (Eqs. 2.19, 2.20, 2.26, 2.22, 2.12)
+            const float igy = EDGE ? ig0 * ymask : ig0;
+            const F2 igy2 = f2(igy);
+            const F2 gy2 = (c.P.p[2] - pm2) * igy2, gy3 = (c.P.p[3] - pm3) * igy2;
+            const float gmy = (c.my - mym) * igy;
+            const F2 l0 = axLp * c0.P.p[0], r0 = axRp * c0.P.p[0];
+            const F2 l2 = fma2(gxL, gy2, axLp * c0.P.p[2]), r2 = fma2(gxR, gy2, axRp * c0.P.p[2]);
+            const F2 l3 = fma2(gxL, gy3, axLn * c0.P.p[3]), r3 = fma2(gxR, gy3, axRn * c0.P.p[3]);
+            const float pl = fmaf(eL0, c0.phi, fmaf(eLx, c0.mx, eLy * gmy));
+            const float pr = fmaf(wR0, c0.phi, fmaf(wRx, c0.mx, wRy * gmy));
+            const F2 b0 = l0 + shfl_dn2(r0), b2 = l2 + shfl_dn2(r2), b3 = l3 + shfl_dn2(r3);
+            const F2 pb = f2(pl + __shfl_down_sync(0xffffffffu, pr, 1));
+            const F2 e0 = fma2(F2{k.a_f2}, b0, hf2(k, 0, pb));
+            const F2 e2 = fma2(F2{k.a_f2}, b2, hf2(k, 2, pb));
+            const F2 e3 = fma2(F2{k.a_f2}, b3, hf2(k, 3, pb));
+            const F2 d0 = e0 - shfl_up2(e0), d2 = e2 - shfl_up2(e2), d3 = e3 - shfl_up2(e3);
+            const F2 ryn = sgn2(0.f, -ry0, 1);
+            V9 o;
+            o.z = U0.z;
+            o.p[0] = fma2(rxp, d0, U0.p[0]);
+            o.p[1] = fma2(ryn, f1, U0.p[1]);
+            o.p[2] = fma2(rxp, d2, fma2(ryn, fq2, U0.p[2]));
+            o.p[3] = fma2(rxn, d3, fma2(ryn, f3, U0.p[3]));
+            if (updates) {
+                float* out = a.fout + (long long)(r - 1) * a.pitch + j;
+                out[0] = o.z;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    out[PA(q) * a.plane] = o.p[q].v.x;
+                    out[PB(q) * a.plane] = o.p[q].v.y;
+                }
+            }
+            pm2 = c0.P.p[2];
+            pm3 = c0.P.p[3];
+            mym = c0.my;
+        } else if (r < y0) {
+            pm2 = c.P.p[2];
+            pm3 = c.P.p[3];
+            mym = c.my;
+        }
+        if (r >= y0) {  // row r: ftilde^+ plus the flux of the face below it
+            const F2 ryp = sgn2(0.f, w.ry, 1);
+            U0 = Fp;
+            U0.p[1] = fma2(ryp, f1, U0.p[1]);
+            U0.p[2] = fma2(ryp, fq2, U0.p[2]);
+            U0.p[3] = fma2(ryp, f3, U0.p[3]);
+        }
+        lower(w, c, g2, g3, gm, lo);  // the face above row r
+        c0 = c;
+        ig0 = w.igy;
+        ry0 = w.ry;
+    }
+    if (failed && lane == 0) {
+        atomicOr(a.err, 1);
+        for (int q = consumed; q < issued; ++q) {
+            mbar_wait_bounded(&bars[s], ph, 100000000ull);
+            if (++s == S) { s = 0; ph ^= 1u; }
+        }
+    }
+    __syncwarp();
+}
+
+#ifndef DUGKS_SV_SRC_MIN_WARPS
+#define DUGKS_SV_SRC_MIN_WARPS 16
+#endif
+
+// One one-warp CTA per (strip, row segment) with the source terms.
+template <int NC>
+__global__ void __launch_bounds__(32, DUGKS_SV_SRC_MIN_WARPS)
+    step_vp_src(const __grid_constant__ CUtensorMap tin, const StepArgs<float, NC> a, const ConstsP<NC> k,
+                const RowY* __restrict__ rw, const int seg_rows, const int S, const __grid_constant__ SrcArgs<float> sa,
+                const __grid_constant__ CUtensorMap taux) {
+    using L = WarpLayout<float>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + size_t(S) * sa.stage_bytes);
+    const int lane = threadIdx.x;
+    const int xw = blockIdx.x * L::WI;
+    const int y0 = blockIdx.y * seg_rows;
+    const int y1 = min(y0 + seg_rows, a.ny);
+    if (y0 >= a.ny || xw >= a.nx) return;
+    if (lane == 0) {
+        for (int q = 0; q < S; ++q) mbar_init(&bars[q], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const bool edge = xw - 1 < 0 || xw + L::WI >= a.nx;
+    const bool yg = !a.yper && (y0 == 0 || y1 == a.ny);
+    sv_rows_src<NC>(&tin, &taux, a, k, rw, sa, smem, bars, S, lane, xw, y0, y1, edge, yg);
+}
+
 }  // namespace dugks
