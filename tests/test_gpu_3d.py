@@ -43,6 +43,15 @@ CASES = {
     "d3q19_degree5_24x20x10": lambda: (lambda pp: (pp[0].with_(b=(0.0, 0.2, 0.1, 0.3)), pp[1]))(I.burgers3d(24, 20, 10)),
     "tiny_3x2x2_walls": lambda: _walls((3, 2, 2), 19, (1,) * 6, stretched=False),
     "tiny_1x3x2_periodic": lambda: I.burgers3d(1, 3, 2, lattice=15),
+    # nx a multiple of 4: the FP32 step runs the face-halves kernel (TMA-staged)
+    "d3q15_periodic_32x29x12": lambda: I.burgers3d(32, 29, 12, lattice=15),
+    "d3q19_walls_36x18x16": lambda: _walls((36, 18, 16), 19, (1,) * 6),
+    "d3q15_walls_28x16x9": lambda: _walls((28, 16, 9), 15, (1,) * 6),
+    "d3q15_mixed_uniform_40x23x11": lambda: _walls((40, 23, 11), 15, (0, 0, 1, 1, 1, 1), stretched=False),
+    "d3q19_mixed_60x21x13": lambda: _walls((60, 21, 13), 19, (1, 1, 0, 0, 1, 1)),
+    "d3q15_periodic_72x64x40": lambda: I.burgers3d(72, 64, 40, lattice=15),
+    "tiny_4x2x2_walls": lambda: _walls((4, 2, 2), 19, (1,) * 6, stretched=False),
+    "tiny_4x1x3_periodic": lambda: I.burgers3d(4, 1, 3, lattice=15),
 }
 
 
