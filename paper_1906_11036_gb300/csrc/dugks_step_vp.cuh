@@ -112,15 +112,17 @@ __device__ __forceinline__ void sv_ghost(const ConstsP<NC>& k, SvCell& c, const 
 // updated.  EDGE: the strip touches the first or last column (ghost, periodic-image or
 // idle lanes).  YG: the segment may meet a Dirichlet wall in y (ghost rows -1 and ny).
 // Both are warp-uniform run-time flags: a loop over segments then holds one copy of
-// the routine (several inlined copies in one loop exhaust the register budget).
+// the routine (several inlined copies in one loop exhaust the register budget).  PLAIN: a
+// warp that meets neither (known at compile time), so the flags and their branches fold away.
 // `ring` counts the rows this warp already passed through its ring (row t of the warp
 // uses stage t % S in phase (t / S) & 1), so a warp may run several segments.
-template <int NC>
+template <int NC, bool PLAIN = false>
 __device__ __forceinline__ void sv_rows(const CUtensorMap* tin, const StepArgs<float, NC>& a, const ConstsP<NC>& k,
                                         const RowY* __restrict__ rw, unsigned char* stages, uint64_t* bars,
                                         const int S, const int lane, const int xw, const int y0, const int y1,
-                                        const bool EDGE, const bool YG, int& ring) {
+                                        const bool edge_in, const bool yg_in, int& ring) {
     using L = WarpLayout<float>;
+    const bool EDGE = PLAIN ? false : edge_in, YG = PLAIN ? false : yg_in;
     const int nx = a.nx, ny = a.ny;
     const int j = xw - 1 + lane;
     const int xs = (xw - 1) & ~(L::ALIGN - 1);
@@ -401,7 +403,10 @@ __global__ void __launch_bounds__(32, DUGKS_SV_MIN_WARPS)
     const bool edge = xw - 1 < 0 || xw + L::WI >= a.nx;
     const bool yg = !a.yper && (y0 == 0 || y1 == a.ny);
     int ring = 0;
-    sv_rows<NC>(&tin, a, k, rw, smem, bars, S, lane, xw, y0, y1, edge, yg, ring);
+    if (!edge && !yg)
+        sv_rows<NC, true>(&tin, a, k, rw, smem, bars, S, lane, xw, y0, y1, false, false, ring);
+    else
+        sv_rows<NC>(&tin, a, k, rw, smem, bars, S, lane, xw, y0, y1, edge, yg, ring);
 }
 
 
@@ -416,13 +421,14 @@ __global__ void __launch_bounds__(32, DUGKS_SV_MIN_WARPS)
 // fields S_k and phi^{n-1} of a row arrive in a second TMA box in the same ring stage.  One
 // loop over the rows y0-1 .. y1 whose first two passes skip what needs the rows below keeps
 // one inlined copy of the source arithmetic (instruction-cache footprint).
-template <int NC>
+template <int NC, bool PLAIN = false>
 __device__ __forceinline__ void sv_rows_src(const CUtensorMap* tin, const CUtensorMap* taux,
                                             const StepArgs<float, NC>& a, const ConstsP<NC>& k,
                                             const RowY* __restrict__ rw, const SrcArgs<float>& sa,
                                             unsigned char* stages, uint64_t* bars, const int S, const int lane,
-                                            const int xw, const int y0, const int y1, const bool EDGE,
-                                            const bool YG) {
+                                            const int xw, const int y0, const int y1, const bool edge_in,
+                                            const bool yg_in) {
+    const bool EDGE = PLAIN ? false : edge_in, YG = PLAIN ? false : yg_in;
     using L = WarpLayout<float>;
     const int nx = a.nx, ny = a.ny;
     const int j = xw - 1 + lane;
@@ -665,7 +671,10 @@ __global__ void __launch_bounds__(32, DUGKS_SV_SRC_MIN_WARPS)
     __syncwarp();
     const bool edge = xw - 1 < 0 || xw + L::WI >= a.nx;
     const bool yg = !a.yper && (y0 == 0 || y1 == a.ny);
-    sv_rows_src<NC>(&tin, &taux, a, k, rw, sa, smem, bars, S, lane, xw, y0, y1, edge, yg);
+    if (!edge && !yg)
+        sv_rows_src<NC, true>(&tin, &taux, a, k, rw, sa, smem, bars, S, lane, xw, y0, y1, false, false);
+    else
+        sv_rows_src<NC>(&tin, &taux, a, k, rw, sa, smem, bars, S, lane, xw, y0, y1, edge, yg);
 }
 
 }  // namespace dugks
