@@ -68,7 +68,9 @@ struct dugks_ctx {
     int red_blocks = 0;
     CUtensorMap tmap[2];
     int nt = 32, stages = 8, seg_rows = 0, nstrips = 0, nseg = 0, occupancy = 0;
-    int seg_rows_src = 0, nseg_src = 0;  // row segments of the source-term kernel
+    int seg_rows_src = 0, nseg_src = 0;  // row segments of the source-term kernel (FP64: uniform)
+    SegPlan sp_src{0, 0, 0};              // the FP32 source-term kernel's segment plan
+    int nseg_sp_src = 0;
     SegPlan sp{1, 0, 1};  // step_vp: long segments first, then short ones
     long long steps_done = 0;
     // adjoint work buffers (allocated on first use)
@@ -421,16 +423,29 @@ dugks_status make_tensor_maps(dugks_ctx* ctx) {
 // 0.9 / 10 66.4, 0.95 / 8 68.0
 constexpr double kPlanFirst = DUGKS_PLAN_FIRST;  // share of the rows in the first wave of long segments
 constexpr int kPlanShort = DUGKS_PLAN_SHORT;      // rows of the short segments after them
-void plan_long_short(dugks_ctx* ctx, long long slots, double first, int seg_short) {
+#ifndef DUGKS_SRC_PLAN_FIRST
+#define DUGKS_SRC_PLAN_FIRST 0.7
+#endif
+#ifndef DUGKS_SRC_PLAN_SHORT
+#define DUGKS_SRC_PLAN_SHORT 8
+#endif
+// the same for the source-term kernel, from its own occupancy (Example 4.5 at 2048^2, us per
+// step: uniform 20-row segments 131.8; long share 0.9 141.0, 0.8 132.7, 0.7 121.8, 0.65 122.2,
+// 0.6 123.3, 0.5 125.4 with 8-row short segments; 0.8 with 12 or 16 rows 132.5, 131.7)
+constexpr double kSrcPlanFirst = DUGKS_SRC_PLAN_FIRST;
+constexpr int kSrcPlanShort = DUGKS_SRC_PLAN_SHORT;
+// Long segments over the first wave (share `first` of the rows), short ones after them;
+// false (and nothing set) where the grid has too few rows for it.
+bool plan_long_short(const dugks_ctx* ctx, long long slots, double first, int seg_short, SegPlan& sp, int& nseg) {
     const long long K = std::max<long long>(1, slots / ctx->nstrips);
     const int L = int(first * ctx->ny / double(K));
-    if (L < 2 * seg_short || L < 24) return;
+    if (L < 2 * seg_short || L < 24) return false;
     const int rest = ctx->ny - int(K) * L;
-    if (rest <= 0) return;
+    if (rest <= 0) return false;
     const int nshort = (rest + seg_short - 1) / seg_short;
-    ctx->sp = SegPlan{L, int(K), seg_short};
-    ctx->nseg = int(K) + nshort;
-    ctx->seg_rows = L;
+    sp = SegPlan{L, int(K), seg_short};
+    nseg = int(K) + nshort;
+    return true;
 }
 
 // Strip and segment counts of the fused kernels for this grid: one warp per
@@ -469,7 +484,10 @@ dugks_status plan_fused(dugks_ctx* ctx) {
     cut(3 * slots / ctx->nstrips, ctx->seg_rows, ctx->nseg);
     cut(3 * slots / ctx->nstrips, ctx->seg_rows_src, ctx->nseg_src);
     ctx->sp = SegPlan{ctx->seg_rows, ctx->nseg, ctx->seg_rows};
-    if (ctx->precision == 32 && ctx->nc != NC_LARGE) plan_long_short(ctx, slots, kPlanFirst, kPlanShort);
+    if (ctx->precision == 32 && ctx->nc != NC_LARGE && plan_long_short(ctx, slots, kPlanFirst, kPlanShort, ctx->sp, ctx->nseg))
+        ctx->seg_rows = ctx->sp.seg_long;
+    ctx->sp_src = SegPlan{ctx->seg_rows_src, ctx->nseg_src, ctx->seg_rows_src};
+    ctx->nseg_sp_src = ctx->nseg_src;
     return DUGKS_OK;
 }
 
@@ -540,8 +558,8 @@ cudaError_t launch_step(dugks_ctx* ctx) {
     if (ctx->nsrc > 0) {  // the fused kernel with the source terms: velocity pairs in FP32, else scalar
         dim3 grid(ctx->nstrips, ctx->nseg_src);
         if constexpr (sizeof(T) == 4 && NC != NC_LARGE)
-            step_vp_src<NC><<<grid, 32, src_vp_smem(ctx), ctx->stream>>>(
-                ctx->tmap[ctx->cur], a, make_constsp<NC>(ctx), ctx->rowy, ctx->seg_rows_src, ctx->stages,
+            step_vp_src<NC><<<dim3(ctx->nstrips, ctx->nseg_sp_src), 32, src_vp_smem(ctx), ctx->stream>>>(
+                ctx->tmap[ctx->cur], a, make_constsp<NC>(ctx), ctx->rowy, ctx->sp_src, ctx->stages,
                 make_src_args<float>(ctx), ctx->taux[ctx->cur]);
         else
             fused_step_src<T, NC><<<grid, 32, fused_smem(ctx), ctx->stream>>>(ctx->tmap[ctx->cur], a, k,
@@ -1491,6 +1509,19 @@ dugks_status dugks_set_source(dugks_ctx* ctx, int nterms, const double* rate, co
         }
         ctx->aux_box = int(planes) * L::BOXW * int(sizeof(float));
         ctx->src_stage = L::STAGE_BYTES + (ctx->aux_box + 127) / 128 * 128;
+        // the segment plan of the source-term kernel from its own occupancy (long segments over
+        // the first wave, short ones after them, as the plain step)
+        if (ctx->nc != NC_LARGE) {
+            int sms = 0, occ = 0;
+            CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+            const void* fn = ctx->nc == 3 ? reinterpret_cast<const void*>(&step_vp_src<3>)
+                                          : reinterpret_cast<const void*>(&step_vp_src<4>);
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32, src_vp_smem(ctx)));
+            ctx->sp_src = SegPlan{ctx->seg_rows_src, ctx->nseg_src, ctx->seg_rows_src};
+            ctx->nseg_sp_src = ctx->nseg_src;
+            if (occ > 0)
+                plan_long_short(ctx, (long long)sms * occ, kSrcPlanFirst, kSrcPlanShort, ctx->sp_src, ctx->nseg_sp_src);
+        }
     } else if (nterms > 0) {
         CK(cudaStreamSynchronize(ctx->stream));  // the old fields may still be read by queued steps
         if (ctx->src_field) { cudaFree(ctx->src_field); ctx->src_field = nullptr; }

@@ -653,7 +653,7 @@ __device__ __forceinline__ void sv_rows_src(const CUtensorMap* tin, const CUtens
 template <int NC>
 __global__ void __launch_bounds__(32, DUGKS_SV_SRC_MIN_WARPS)
     step_vp_src(const __grid_constant__ CUtensorMap tin, const StepArgs<float, NC> a, const ConstsP<NC> k,
-                const RowY* __restrict__ rw, const int seg_rows, const int S, const __grid_constant__ SrcArgs<float> sa,
+                const RowY* __restrict__ rw, const SegPlan sp, const int S, const __grid_constant__ SrcArgs<float> sa,
                 const __grid_constant__ CUtensorMap taux) {
     using L = WarpLayout<float>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -661,8 +661,8 @@ __global__ void __launch_bounds__(32, DUGKS_SV_SRC_MIN_WARPS)
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + size_t(S) * sa.stage_bytes);
     const int lane = threadIdx.x;
     const int xw = blockIdx.x * L::WI;
-    const int y0 = blockIdx.y * seg_rows;
-    const int y1 = min(y0 + seg_rows, a.ny);
+    int y0, y1;
+    seg_rows_of(sp, int(blockIdx.y), a.ny, y0, y1);
     if (y0 >= a.ny || xw >= a.nx) return;
     if (lane == 0) {
         for (int q = 0; q < S; ++q) mbar_init(&bars[q], 1);
