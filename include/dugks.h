@@ -312,9 +312,10 @@ dugks_status dugks_batch_save_state(dugks_batch *b, int i, void *f_dev_out);
 /* Synchronise; DUGKS_ERR_TIMEOUT if a bounded device wait expired. */
 dugks_status dugks_batch_sync(dugks_batch *b);
 /* Autotuner: times steps_per_trial steps for each candidate tile height (rows
- * per tile, 8 ... 128), each with and without the split of every instance's
- * last fifth of rows into 8-row tiles queued after all the others, on
- * snapshots of the current states; keeps the fastest and restores the states.
+ * per tile, 8 ... 128), each without and with the split of every instance's
+ * last rows (all but 0.8, 0.7 or 0.6 of them) into 8-row tiles queued after
+ * all the others, on snapshots of the current states; keeps the fastest and
+ * restores the states.
  * Outputs (nullable): the chosen rows per tile and milliseconds per step. */
 dugks_status dugks_batch_autotune(dugks_batch *b, int steps_per_trial, int *best_rows_out, float *best_ms_out);
 const char *dugks_batch_last_error(const dugks_batch *b);
@@ -341,12 +342,11 @@ const char *dugks_batch_last_error(const dugks_batch *b);
  * precision or nx, ny < 1, and DUGKS_ERR_UNSUPPORTED when nx*ny exceeds
  * DUGKS_NOALLOC_MAX_CELLS (one partial sum per 256 cells), DUGKS_ERR_CUDA if
  * a launch of this call fails (an error left pending by earlier work of the
- * caller is neither cleared nor reported).  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress) with that device
- * current and keeps it for the process; make that first call before any
- * stream capture, and do not call the entry point again on a device after
- * cudaDeviceReset there (the kept address would belong to the destroyed
- * context).  All calls share the one array: calls that overlap on the GPU
+ * caller is neither cleared nor reported).  Every call looks up the array's
+ * device address (cudaGetSymbolAddress, a host call) on the current device and
+ * keeps nothing, so a call after cudaDeviceReset finds the new context's array;
+ * make the first call on a device before any stream capture (that lookup may
+ * load the library's device code).  All calls share the one array: calls that overlap on the GPU
  * (concurrent streams, or several host threads) race and must be serialised
  * by the caller.  Every partial sum is overwritten before it is read, so
  * nothing from an earlier call leaks into a later one. */

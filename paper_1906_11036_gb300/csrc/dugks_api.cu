@@ -14,7 +14,6 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -107,7 +106,6 @@ struct dugks_ctx {
 };
 
 constexpr int kBatchShortRows = 8;       // rows of the short tiles at the end of the batched queue
-constexpr double kBatchLongFrac = 0.8;   // share of an instance's rows in long tiles
 
 struct dugks_batch {
     int n = 0, device = 0, nc = 3;
@@ -117,6 +115,7 @@ struct dugks_batch {
     void* d_insts = nullptr;   // BatchInst<nc>[n]
     BatchTile* d_tiles = nullptr;  // the tile queue
     bool split = true;             // long segments, then short tiles at the end of the queue
+    double long_frac = 0.8;        // with split: share of an instance's rows in long tiles
     int* d_counters = nullptr;  // one per launch of a graph (plus the remainder)
     int* d_err = nullptr;
     int ntiles = 0, seg_target = 48, blocks = 0, stages = 4;
@@ -940,7 +939,7 @@ dugks_status batch_build_tables(dugks_batch* b) {
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
         return (long long)b->ctx[x]->nx * b->ctx[x]->ny > (long long)b->ctx[y]->nx * b->ctx[y]->ny;
     });
-    // each instance: segments of seg_target rows over about kBatchLongFrac of its rows, then
+    // each instance: segments of seg_target rows over about long_frac of its rows, then
     // segments of kBatchShortRows; the short tiles of all instances follow all the long ones
     std::vector<BatchTile> tiles, shorts;
     for (int oi : order) {
@@ -957,7 +956,7 @@ dugks_status batch_build_tables(dugks_batch* b) {
         const int L = std::max(1, std::min(b->seg_target, c->ny));
         int nlong = (c->ny + L - 1) / L, ylong = c->ny;
         if (b->split && L > 2 * kBatchShortRows) {
-            nlong = int(kBatchLongFrac * c->ny / L);
+            nlong = int(b->long_frac * c->ny / L);
             ylong = nlong * L;
         }
         for (int sg = 0; sg < nlong; ++sg)
@@ -1808,18 +1807,23 @@ dugks_status dugks_batch_autotune(dugks_batch* b, int steps_per_trial, int* best
         if (st != DUGKS_OK) { release(); return st; }
     }
     const int p_saved = b->parity;
-    // tile heights, each with and without the short tiles at the end of the queue
+    // tile heights, each without the short tiles at the end of the queue and with them after
+    // long tiles over 0.8, 0.7 or 0.6 of every instance's rows
     const int cands[] = {8, 16, 24, 32, 48, 64, 96, 128};
+    const double fracs[] = {0.8, 0.7, 0.6};
+    constexpr int NV = 1 + int(sizeof(fracs) / sizeof(fracs[0]));
     int best = b->seg_target;
     bool best_split = b->split;
+    double best_frac = b->long_frac;
     float best_ms = 1e30f;
     cudaEvent_t ev0, ev1;
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);
-    for (int trial = 0; trial < 2 * int(sizeof(cands) / sizeof(cands[0])); ++trial) {
-        const int cand = cands[trial / 2];
+    for (int trial = 0; trial < NV * int(sizeof(cands) / sizeof(cands[0])); ++trial) {
+        const int cand = cands[trial / NV], v = trial % NV;
         b->seg_target = cand;
-        b->split = (trial & 1) != 0;
+        b->split = v != 0;
+        if (v) b->long_frac = fracs[v - 1];
         if (b->split && cand <= 2 * kBatchShortRows) continue;  // no short tiles to split off
         dugks_status st = batch_tables(b);
         if (st != DUGKS_OK) { release(); return st; }
@@ -1831,7 +1835,7 @@ dugks_status dugks_batch_autotune(dugks_batch* b, int steps_per_trial, int* best
         if (e != cudaSuccess || (e = cudaEventSynchronize(ev1)) != cudaSuccess) break;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev0, ev1);
-        if (ms < best_ms) { best_ms = ms; best = cand; best_split = b->split; }
+        if (ms < best_ms) { best_ms = ms; best = cand; best_split = b->split; best_frac = b->long_frac; }
     }
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
@@ -1850,6 +1854,7 @@ dugks_status dugks_batch_autotune(dugks_batch* b, int steps_per_trial, int* best
     release();
     b->seg_target = best;
     b->split = best_split;
+    b->long_frac = best_frac;
     dugks_status st = batch_tables(b);
     if (st != DUGKS_OK) return st;
     if (best_rows_out) *best_rows_out = best;
@@ -1864,24 +1869,19 @@ const char* dugks_batch_last_error(const dugks_batch* b) { return b ? b->last_er
 // ---- allocation-free phi / mass --------------------------------------------
 // Partial sums of the reduction live in this fixed device array instead of
 // a context's buffer.  Host code cannot use the symbol's address directly
-// (in host code it names a host-side shadow), so its device address is
-// looked up once per device with cudaGetSymbolAddress.
+// (in host code it names a host-side shadow), so every call looks up its
+// device address on the current device with cudaGetSymbolAddress (a host
+// call; nothing is cached that a device reset could leave stale).
 static __device__ __align__(256) double g_noalloc_partial[DUGKS_NOALLOC_MAX_BLOCKS];
 
 namespace {
 constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-double* g_noalloc_ptr[kMaxDevices] = {};
 
-cudaError_t noalloc_scratch(int dev, double** out) {
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partial);  // the current device is `dev`
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = static_cast<double*>(p);
-    }
-    *out = g_noalloc_ptr[dev];
+cudaError_t noalloc_scratch(double** out) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partial);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<double*>(p);
     return cudaSuccess;
 }
 }  // namespace
@@ -1898,7 +1898,7 @@ extern "C" dugks_status dugks_phi_mass_noalloc(const void* f_dev, int precision,
     if (cudaGetDevice(&dev) != cudaSuccess) return DUGKS_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return DUGKS_ERR_UNSUPPORTED;
     double* partial = nullptr;
-    if (noalloc_scratch(dev, &partial) != cudaSuccess) return DUGKS_ERR_CUDA;
+    if (noalloc_scratch(&partial) != cudaSuccess) return DUGKS_ERR_CUDA;
     const int blocks = int((n + 255) / 256);  // one partial per 256 cells, each written exactly once
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // an error the caller left pending is neither cleared nor reported as this call's
