@@ -69,6 +69,7 @@ struct dugks_ctx {
     int nt = 32, stages = 8, seg_rows = 0, nstrips = 0, nseg = 0, occupancy = 0;
     int seg_rows_src = 0, nseg_src = 0;  // row segments of the source-term kernel (FP64: uniform)
     SegPlan sp_src{0, 0, 0};              // the FP32 source-term kernel's segment plan
+    bool plain = false;                   // step_vp with the interior variant (long-segment plans)
     int nseg_sp_src = 0;
     SegPlan sp{1, 0, 1};  // step_vp: long segments first, then short ones
     long long steps_done = 0;
@@ -345,8 +346,8 @@ StepArgs<T, NC> make_args(const dugks_ctx* ctx, int from) {
 void* fused_fn(const dugks_ctx* ctx) {
     if (ctx->precision == 32) {
         switch (ctx->nc) {
-            case 3: return reinterpret_cast<void*>(&step_vp<3>);
-            case 4: return reinterpret_cast<void*>(&step_vp<4>);
+            case 3: return ctx->plain ? reinterpret_cast<void*>(&step_vp<3, true>) : reinterpret_cast<void*>(&step_vp<3, false>);
+            case 4: return ctx->plain ? reinterpret_cast<void*>(&step_vp<4, true>) : reinterpret_cast<void*>(&step_vp<4, false>);
             default: return reinterpret_cast<void*>(&fused_step<float, NC_LARGE>);  // high degree: scalar path
         }
     }
@@ -483,8 +484,13 @@ dugks_status plan_fused(dugks_ctx* ctx) {
     cut(3 * slots / ctx->nstrips, ctx->seg_rows, ctx->nseg);
     cut(3 * slots / ctx->nstrips, ctx->seg_rows_src, ctx->nseg_src);
     ctx->sp = SegPlan{ctx->seg_rows, ctx->nseg, ctx->seg_rows};
-    if (ctx->precision == 32 && ctx->nc != NC_LARGE && plan_long_short(ctx, slots, kPlanFirst, kPlanShort, ctx->sp, ctx->nseg))
+    ctx->plain = false;
+    if (ctx->precision == 32 && ctx->nc != NC_LARGE && plan_long_short(ctx, slots, kPlanFirst, kPlanShort, ctx->sp, ctx->nseg)) {
         ctx->seg_rows = ctx->sp.seg_long;
+        ctx->plain = true;  // the interior variant pays on long segments (step_vp)
+        e = cudaFuncSetAttribute(fused_fn(ctx), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
+    }
     ctx->sp_src = SegPlan{ctx->seg_rows_src, ctx->nseg_src, ctx->seg_rows_src};
     ctx->nseg_sp_src = ctx->nseg_src;
     return DUGKS_OK;
@@ -572,8 +578,12 @@ cudaError_t launch_step(dugks_ctx* ctx) {
     } else {
         dim3 grid(ctx->nstrips, ctx->nseg);
         if constexpr (sizeof(T) == 4 && NC != NC_LARGE)
-            step_vp<NC><<<grid, 32, fused_smem(ctx), ctx->stream>>>(ctx->tmap[ctx->cur], a, make_constsp<NC>(ctx),
-                                                                   ctx->rowy, ctx->sp, ctx->stages);
+            if (ctx->plain)
+                step_vp<NC, true><<<grid, 32, fused_smem(ctx), ctx->stream>>>(
+                    ctx->tmap[ctx->cur], a, make_constsp<NC>(ctx), ctx->rowy, ctx->sp, ctx->stages);
+            else
+                step_vp<NC, false><<<grid, 32, fused_smem(ctx), ctx->stream>>>(
+                    ctx->tmap[ctx->cur], a, make_constsp<NC>(ctx), ctx->rowy, ctx->sp, ctx->stages);
         else
             fused_step<T, NC><<<grid, 32, fused_smem(ctx), ctx->stream>>>(ctx->tmap[ctx->cur], a, k, ctx->seg_rows,
                                                                          ctx->stages);

@@ -381,7 +381,11 @@ __device__ __forceinline__ void seg_rows_of(const SegPlan& sp, const int k, cons
 }
 
 // One one-warp CTA per (strip, row segment): blockIdx.x = strip, blockIdx.y = segment.
-template <int NC>
+// IP: interior CTAs run the interior variant of the row routine.  The host takes it for plans
+// with long segments (2048^2 tanh mesh: 65.8 -> 63.75 us); without it for grids of short uniform
+// segments, where the second copy of the routine in the kernel costs more than it saves
+// (1024^2 periodic, 16-row segments: 25.05 us without, 25.71 us with).
+template <int NC, bool IP>
 __global__ void __launch_bounds__(32, DUGKS_SV_MIN_WARPS)
     step_vp(const __grid_constant__ CUtensorMap tin, const StepArgs<float, NC> a, const ConstsP<NC> k,
             const RowY* __restrict__ rw, const SegPlan sp, const int S) {
@@ -403,7 +407,7 @@ __global__ void __launch_bounds__(32, DUGKS_SV_MIN_WARPS)
     const bool edge = xw - 1 < 0 || xw + L::WI >= a.nx;
     const bool yg = !a.yper && (y0 == 0 || y1 == a.ny);
     int ring = 0;
-    if (!edge && !yg)
+    if (IP && !edge && !yg)
         sv_rows<NC, true>(&tin, a, k, rw, smem, bars, S, lane, xw, y0, y1, false, false, ring);
     else
         sv_rows<NC>(&tin, a, k, rw, smem, bars, S, lane, xw, y0, y1, edge, yg, ring);
