@@ -17,7 +17,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libdugks.so")
 SOURCES = [os.path.join(CSRC, "dugks_api.cu"), os.path.join(CSRC, "dugks3d_api.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("dugks_device.cuh", "dugks_kernels.cuh", "dugks_step_vp.cuh", "dugks_adjoint.cuh",
-                                                  "dugks_batch.cuh", "dugks3d_kernels.cuh", "dugks_adjoint_rows.cuh")] + [
+                                                  "dugks_batch.cuh", "dugks3d_kernels.cuh", "dugks3d_halves.cuh", "dugks_adjoint_rows.cuh")] + [
     os.path.join(ROOT, "include", "dugks.h"), os.path.join(ROOT, "include", "dugks3d.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

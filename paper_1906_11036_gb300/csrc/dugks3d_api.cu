@@ -13,7 +13,7 @@
 #include <vector>
 
 #include "../../include/dugks3d.h"
-#include "dugks3d_kernels.cuh"
+#include "dugks3d_halves.cuh"
 
 using namespace dugks3;
 
@@ -223,9 +223,14 @@ template <typename T, int QQ, int NC, int NW>
 cudaError_t launch3(dugks_3d_ctx* ctx) {
     const dim3 grid(ctx->grid[0], ctx->grid[1], ctx->grid[2]);
     if constexpr (std::is_same<T, float>::value) {
-        if (ctx->tma)
-            step3d_vp<QQ, NC, NW, true><<<grid, NW * 32, smem3_vp<QQ, NW, true>(), ctx->stream>>>(
-                ctx->tmap[ctx->cur], args3<float>(ctx), consts3p<QQ, NC>(ctx));
+        if (ctx->tma) {
+            if constexpr (QQ == 15)  // the face-halves kernel (D3Q15 256^3: 1186 us against 1214)
+                step3d_hv<QQ, NC, NW><<<grid, NW * 32, smem3_hv<QQ, NW>(), ctx->stream>>>(
+                    ctx->tmap[ctx->cur], args3<float>(ctx), consts3p<QQ, NC>(ctx));
+            else  // D3Q19: the face kernel on TMA boxes (256^3: 1144 us; the face-halves kernel 1188)
+                step3d_vp<QQ, NC, NW, true><<<grid, NW * 32, smem3_vp<QQ, NW, true>(), ctx->stream>>>(
+                    ctx->tmap[ctx->cur], args3<float>(ctx), consts3p<QQ, NC>(ctx));
+        }
         else
             step3d_vp<QQ, NC, NW, false><<<grid, NW * 32, smem3_vp<QQ, NW, false>(), ctx->stream>>>(
                 ctx->tmap[ctx->cur], args3<float>(ctx), consts3p<QQ, NC>(ctx));
@@ -255,9 +260,13 @@ struct AttrOp {
     template <typename T, int QQ, int NC, int NW>
     cudaError_t operator()() const {
         if constexpr (std::is_same<T, float>::value) {
-            cudaError_t e = cudaFuncSetAttribute(step3d_vp<QQ, NC, NW, true>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 int(smem3_vp<QQ, NW, true>()));
+            cudaError_t e;
+            if constexpr (QQ == 15)
+                e = cudaFuncSetAttribute(step3d_hv<QQ, NC, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem3_hv<QQ, NW>()));
+            else
+                e = cudaFuncSetAttribute(step3d_vp<QQ, NC, NW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem3_vp<QQ, NW, true>()));
             if (e != cudaSuccess) return e;
             return cudaFuncSetAttribute(step3d_vp<QQ, NC, NW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         int(smem3_vp<QQ, NW, false>()));
@@ -272,10 +281,17 @@ struct OccOp {
     template <typename T, int QQ, int NC, int NW>
     cudaError_t operator()() const {
         if constexpr (std::is_same<T, float>::value)
-            return tma ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, step3d_vp<QQ, NC, NW, true>, NW * 32,
-                                                                       smem3_vp<QQ, NW, true>())
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, step3d_vp<QQ, NC, NW, false>, NW * 32,
-                                                                       smem3_vp<QQ, NW, false>());
+        {
+            if (!tma)
+                return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, step3d_vp<QQ, NC, NW, false>, NW * 32,
+                                                                     smem3_vp<QQ, NW, false>());
+            if constexpr (QQ == 15)
+                return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, step3d_hv<QQ, NC, NW>, NW * 32,
+                                                                     smem3_hv<QQ, NW>());
+            else
+                return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, step3d_vp<QQ, NC, NW, true>, NW * 32,
+                                                                     smem3_vp<QQ, NW, true>());
+        }
         else
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, step3d<T, QQ, NC, NW>, NW * 32,
                                                                  smem3<T, QQ, NC, NW>());
@@ -458,9 +474,10 @@ dugks_status dugks_3d_create(const dugks_3d_mesh* mesh, const dugks_3d_vset* vse
         return st;
     }
     if ((e = dispatch3(ctx, AttrOp{})) != cudaSuccess) { st = fail3(ctx, e, "cudaFuncSetAttribute"); free3(ctx); return st; }
-    // TMA staging where it measured faster: D3Q19 on 256^3 1144 us against 1269 us with per-thread
-    // cp.async copies; D3Q15 1275 us against 1209 us, so D3Q15 keeps cp.async
-    ctx->tma = ctx->precision == 32 && ctx->q == 19 && ctx->nx % 4 == 0 && encode_tmaps3(ctx);
+    // FP32 with nx a multiple of 4 (the TMA box origin): ftilde staged by TMA boxes, D3Q19 in
+    // step3d_vp (256^3: 1144 us against 1269 us with per-thread cp.async copies), D3Q15 in the
+    // face-halves kernel step3d_hv (1186 us; step3d_vp 1214 with cp.async, 1275 with TMA)
+    ctx->tma = ctx->precision == 32 && ctx->nx % 4 == 0 && encode_tmaps3(ctx);
     // grid: 30-column strips x (NW-2)-row blocks x z segments.  The segment length
     // minimises (waves of resident CTAs) x (planes per CTA + about one plane of
     // pipeline fill), with segments of at least 8 planes where nz allows.

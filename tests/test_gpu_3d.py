@@ -52,6 +52,8 @@ CASES = {
     "d3q15_periodic_72x64x40": lambda: I.burgers3d(72, 64, 40, lattice=15),
     "tiny_4x2x2_walls": lambda: _walls((4, 2, 2), 19, (1,) * 6, stretched=False),
     "tiny_4x1x3_periodic": lambda: I.burgers3d(4, 1, 3, lattice=15),
+    "d3q15_degree5_32x20x10": lambda: (lambda pp: (pp[0].with_(b=(0.0, 0.2, 0.1, 0.3)), pp[1]))(
+        I.burgers3d(32, 20, 10, lattice=15)),
 }
 
 
