@@ -35,8 +35,9 @@
 // Every per-pair quantity (pair directions, crossing and slope indices) is a compile-time
 // constant of the code that uses it (sfor below): evaluated at run time, the velocity
 // tables cost more than the arithmetic.  The library runs this kernel for D3Q15 (256^3:
-// 1186 us per step against 1214 for the face kernel of dugks3d_kernels.cuh); for D3Q19 the
-// face kernel is faster (1144 us against 1188), with the live state here at 158 registers.
+// 1166 us per step against 1214 for the face kernel of dugks3d_kernels.cuh); for D3Q19 the
+// face kernel is faster (1144 us against 1188-1211), with the live state here at 158-164
+// registers.
 #pragma once
 #include <type_traits>
 #include <utility>
@@ -445,16 +446,19 @@ __global__ void __launch_bounds__(NW * 32, 1)
 
         // 7. the z fluxes complete the update of plane z (Eq. 2.12)
         if (upd && updates) {
-            const long long c = ((long long)z * ny + kk) * nx + j;
+            // velocity planes by 32-bit offsets: the host runs this kernel only where the Q planes
+            // hold fewer than 2^32 elements (D3Q15 256^3: 1166 us against 1186 with 64-bit ones)
+            float* o = a.fout + (((long long)z * ny + kk) * nx + j);
+            const uint32_t pl = uint32_t(a.plane);
             sfor<NP>([&](auto qc) {
                 constexpr int q = decltype(qc)::value;
                 F2 u = U[q];
                 if constexpr (QE3<QQ>(q, 2) != 0)
                     u = fma2(sgn2(0.f, -czl.r, QE3<QQ>(q, 2)), fT[XP3<QQ>(q, 2)] - fB[XP3<QQ>(q, 2)], u);
-                a.fout[PA3<QQ>(q) * a.plane + c] = u.v.x;
-                a.fout[PB3<QQ>(q) * a.plane + c] = u.v.y;
+                o[uint32_t(PA3<QQ>(q)) * pl] = u.v.x;
+                o[uint32_t(PB3<QQ>(q)) * pl] = u.v.y;
             });
-            a.fout[c] = U0;
+            o[0] = U0;
         }
 
         // plane pp becomes plane z of the next pass (its slope pairs stay in set cur)
