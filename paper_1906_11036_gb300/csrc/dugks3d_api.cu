@@ -227,7 +227,7 @@ cudaError_t launch3(dugks_3d_ctx* ctx) {
             if constexpr (QQ == 15)  // the face-halves kernel (D3Q15 256^3: 1166 us against 1214)
                 step3d_hv<QQ, NC, NW><<<grid, NW * 32, smem3_hv<QQ, NW>(), ctx->stream>>>(
                     ctx->tmap[ctx->cur], args3<float>(ctx), consts3p<QQ, NC>(ctx));
-            else  // D3Q19: the face kernel on TMA boxes (256^3: 1144 us; the face-halves kernel 1188)
+            else  // D3Q19: the face kernel on TMA boxes (256^3: 1132 us; the face-halves kernel 1188-1211)
                 step3d_vp<QQ, NC, NW, true><<<grid, NW * 32, smem3_vp<QQ, NW, true>(), ctx->stream>>>(
                     ctx->tmap[ctx->cur], args3<float>(ctx), consts3p<QQ, NC>(ctx));
         }
@@ -474,13 +474,13 @@ dugks_status dugks_3d_create(const dugks_3d_mesh* mesh, const dugks_3d_vset* vse
         return st;
     }
     if ((e = dispatch3(ctx, AttrOp{})) != cudaSuccess) { st = fail3(ctx, e, "cudaFuncSetAttribute"); free3(ctx); return st; }
-    // FP32 with nx a multiple of 4 (the TMA box origin): ftilde staged by TMA boxes, D3Q19 in
-    // step3d_vp (256^3: 1144 us against 1269 us with per-thread cp.async copies), D3Q15 in the
-    // face-halves kernel step3d_hv (1166 us; step3d_vp 1214 with cp.async, 1275 with TMA)
-    // (step3d_hv addresses the velocity planes by 32-bit offsets: D3Q15 takes it below 2^32 elements)
+    // FP32 with nx a multiple of 4 (the TMA box origin) and the Q planes below 2^32 elements (the
+    // TMA kernels address them by 32-bit offsets): ftilde staged by TMA boxes, D3Q19 in step3d_vp
+    // (256^3: 1132 us against 1269 us with per-thread cp.async copies), D3Q15 in the face-halves
+    // kernel step3d_hv (1166 us; step3d_vp 1214 with cp.async, 1275 with TMA); otherwise step3d_vp
+    // with cp.async copies and 64-bit offsets
     const long long elems = (long long)ctx->q * ctx->nx * ctx->ny * ctx->nz;
-    ctx->tma = ctx->precision == 32 && ctx->nx % 4 == 0 && (ctx->q == 19 || elems < (1ll << 32)) &&
-               encode_tmaps3(ctx);
+    ctx->tma = ctx->precision == 32 && ctx->nx % 4 == 0 && elems < (1ll << 32) && encode_tmaps3(ctx);
     // grid: 30-column strips x (NW-2)-row blocks x z segments.  The segment length
     // minimises (waves of resident CTAs) x (planes per CTA + about one plane of
     // pipeline fill), with segments of at least 8 planes where nz allows.

@@ -736,8 +736,15 @@ __global__ void __launch_bounds__(NW * 32, 1)
                              fNy[XP3<QQ>(q, 1)] - sY[((w - 1) * NCP + XP3<QQ>(q, 1)) * 32 + lane], v);
                 if (XP3<QQ>(q, 2) >= 0)
                     v = fma2(sgn2(0.f, -czl.r, QE3<QQ>(q, 2)), fTz[XP3<QQ>(q, 2)] - fB[XP3<QQ>(q, 2)], v);
-                a.fout[PA3<QQ>(q) * a.plane + c] = v.v.x;
-                a.fout[PB3<QQ>(q) * a.plane + c] = v.v.y;
+                if constexpr (TM) {  // 32-bit plane offsets: the host takes TM below 2^32 elements
+                    float* o = a.fout + c;
+                    const uint32_t pl = uint32_t(a.plane);
+                    o[uint32_t(PA3<QQ>(q)) * pl] = v.v.x;
+                    o[uint32_t(PB3<QQ>(q)) * pl] = v.v.y;
+                } else {
+                    a.fout[PA3<QQ>(q) * a.plane + c] = v.v.x;
+                    a.fout[PB3<QQ>(q) * a.plane + c] = v.v.y;
+                }
             }
             a.fout[c] = fmaf(k.third, P0 - (TM ? bx[0] : sF0[(so * NW + w) * 32 + lane]), P0);
         }
